@@ -1,0 +1,387 @@
+"""FP64 CPU oracle for differentiable microstructure reconstruction (arXiv 2103.09686).
+
+TEST INFRASTRUCTURE ONLY: the plain, slow, obviously correct restatement of what the
+method computes.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline /
+reference leg of ``bench.py`` may import it; the library never does, and this module
+imports nothing from the library.  Heavy loops live in ``dmcr_oracle.c`` (plain C,
+double precision); everything else is numpy float64 written in the paper's order.
+
+What each function follows (sections and equations of the paper):
+
+* ``soft_constants``, ``threshold`` -- Sec. 3.2.4, Eq. softthreshold and its three
+  defining conditions f(0)=0, f(1)=1, f''(0.75)=0, alpha = 10.
+* ``sbar`` -- Sec. 3.2.2/3.2.3: convolve (Eq. convdef) -> threshold -> reduce
+  (Eq. s3 with p=r, q=s; the linear reduction of Sec. 3.2.2 on request).
+* ``sbar_masks`` -- the same with the masks m_pqrs built explicitly (Sec. 3.2.3).
+* ``half_window`` / ``full_window`` -- the shift sets |r_a| <= P_a of Sec. 3.3, halved by
+  the point symmetry of App. B.
+* ``restrict`` / ``prolongate_adjoint`` / ``descriptor`` -- Sec. 3.3, Eq. mg: each level
+  summarises 2^d children (read: arithmetic mean), weights w_l = 2^{(d/2)(l-1)}
+  (= 2^{l-1} in 2-D as in the paper's footnote), all levels active at once.
+* ``loss`` -- Sec. 3.1, Eq. L_func_dMCR: E = ||D - D_des||_2, E_bc with H(0)=0,
+  lambda = lambda0 * E.
+* ``loss_grad`` / ``descriptor_vjp`` -- the exact gradient by the chain rule through all
+  levels simultaneously (Sec. 3.1, Sec. 3.3).
+* ``adam_step`` / ``reconstruct`` -- Eq. M-update with Adam at the TensorFlow defaults
+  (App. B): lr 1e-3, beta1 0.9, beta2 0.999; epsilon 1e-7 (Keras form; the paper does
+  not print epsilon).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dmcr_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+TH_SOFT, TH_IDENTITY, TH_HARD = 0, 1, 2
+_KIND = {"soft": TH_SOFT, "identity": TH_IDENTITY, "hard": TH_HARD}
+
+
+def build(force: bool = False) -> str:
+    """Compile the C part of the oracle (gcc, -O2, OpenMP) next to its source."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.POINTER
+            d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int
+            lib.oracle_soft_constants.argtypes = [d, P(d), P(d), P(d)]
+            lib.oracle_threshold.argtypes = [i32, d, P(d), i64, P(d), P(d)]
+            lib.oracle_threshold_custom.argtypes = [d, d, d, d, P(d), i64, P(d)]
+            lib.oracle_sbar.argtypes = [P(d), P(i64), P(i32), i64, i32, d, i32, P(d)]
+            lib.oracle_sbar_masks.argtypes = [P(d), P(i64), P(i32), P(i32), i64, i32, d, P(d)]
+            lib.oracle_vjp_level.argtypes = [P(d), P(i64), P(i32), i64, P(d), i32, d, P(i64), i64, P(d)]
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _i32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def set_threads(n: int | None) -> None:
+    """Number of OpenMP threads the C loops use (None: leave the runtime default)."""
+    if n is not None:
+        os.environ["OMP_NUM_THREADS"] = str(int(n))
+        try:
+            ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+        except OSError:
+            pass
+
+
+# ----------------------------------------------------------------------------- threshold
+
+def soft_constants(alpha: float = 10.0):
+    """(c1, c2, c3) of Eq. softthreshold from f(0)=0, f(1)=1, f''(0.75)=0."""
+    lib = _load()
+    c1, c2, c3 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib.oracle_soft_constants(alpha, ctypes.byref(c1), ctypes.byref(c2), ctypes.byref(c3))
+    return c1.value, c2.value, c3.value
+
+
+def threshold(x, kind: str = "soft", alpha: float = 10.0):
+    """f(x) and f'(x) elementwise."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    f = np.empty_like(x)
+    df = np.empty_like(x)
+    lib.oracle_threshold(_KIND[kind], alpha, _dp(x), x.size, _dp(f), _dp(df))
+    return f, df
+
+
+def threshold_custom(x, alpha, c1, c2, c3):
+    """The logistic of Eq. softthreshold with explicit constants."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    f = np.empty_like(x)
+    lib.oracle_threshold_custom(alpha, c1, c2, c3, _dp(x), x.size, _dp(f))
+    return f
+
+
+# ----------------------------------------------------------------------------- windows
+
+def half_window(ndim: int, P) -> np.ndarray:
+    """Unique shifts under r <-> -r, r = 0 once, as (K_half, ndim) int array.
+
+    Order: 2-D  (0, 0..P1), then (1..P0, -P1..P1) row-major;
+           3-D  (0, 0, 0..P2), (0, 1..P1, -P2..P2), (1..P0, -P1..P1, -P2..P2).
+    """
+    P = [int(p) for p in P][:ndim]
+    out = []
+    if ndim == 2:
+        for q in range(0, P[1] + 1):
+            out.append((0, q))
+        for p in range(1, P[0] + 1):
+            for q in range(-P[1], P[1] + 1):
+                out.append((p, q))
+    elif ndim == 3:
+        for s in range(0, P[2] + 1):
+            out.append((0, 0, s))
+        for q in range(1, P[1] + 1):
+            for s in range(-P[2], P[2] + 1):
+                out.append((0, q, s))
+        for p in range(1, P[0] + 1):
+            for q in range(-P[1], P[1] + 1):
+                for s in range(-P[2], P[2] + 1):
+                    out.append((p, q, s))
+    else:
+        raise ValueError("ndim must be 2 or 3")
+    return np.array(out, dtype=np.int64).reshape(-1, ndim)
+
+
+def full_window(ndim: int, P) -> np.ndarray:
+    """All shifts |r_a| <= P_a, row-major, as (K_full, ndim)."""
+    P = [int(p) for p in P][:ndim]
+    axes = [np.arange(-p, p + 1) for p in P]
+    grid = np.meshgrid(*axes, indexing="ij")
+    return np.stack([g.ravel() for g in grid], axis=1).astype(np.int64)
+
+
+def _as3(M: np.ndarray):
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    if M.ndim == 2:
+        n = np.array([1, M.shape[0], M.shape[1]], dtype=np.int64)
+    elif M.ndim == 3:
+        n = np.array(M.shape, dtype=np.int64)
+    else:
+        raise ValueError("field must be 2-D or 3-D")
+    return M, n
+
+
+def _shifts3(shifts: np.ndarray, ndim: int) -> np.ndarray:
+    shifts = np.asarray(shifts, dtype=np.int64).reshape(-1, ndim)
+    s3 = np.zeros((shifts.shape[0], 3), dtype=np.int32)
+    s3[:, 3 - ndim:] = shifts
+    return np.ascontiguousarray(s3)
+
+
+# ----------------------------------------------------------------------------- descriptor
+
+def sbar(M, shifts, kind: str = "soft", alpha: float = 10.0, linear: bool = False) -> np.ndarray:
+    """One level: S_bar(r) = mean_x f(a_x(r))^2 (or mean_x f(a_x(r)) if linear)."""
+    lib = _load()
+    M, n = _as3(M)
+    s3 = _shifts3(shifts, M.ndim)
+    out = np.empty(s3.shape[0], dtype=np.float64)
+    lib.oracle_sbar(_dp(M), _i64p(n), _i32p(s3), s3.shape[0], _KIND[kind], alpha, int(linear), _dp(out))
+    return out
+
+
+def sbar_masks(M, P, shifts, kind: str = "soft", alpha: float = 10.0) -> np.ndarray:
+    """Same as ``sbar`` but through explicitly built masks (small fields only)."""
+    lib = _load()
+    M, n = _as3(M)
+    s3 = _shifts3(shifts, M.ndim)
+    P3 = np.zeros(3, dtype=np.int32)
+    P3[3 - M.ndim:] = [int(p) for p in P][:M.ndim]
+    out = np.empty(s3.shape[0], dtype=np.float64)
+    lib.oracle_sbar_masks(_dp(M), _i64p(n), _i32p(P3), _i32p(s3), s3.shape[0], _KIND[kind], alpha, _dp(out))
+    return out
+
+
+def restrict(M: np.ndarray) -> np.ndarray:
+    """One multigrid coarsening: each coarse cell is the mean of its 2^d children."""
+    M = np.asarray(M, dtype=np.float64)
+    d = M.ndim
+    shape = []
+    for s in M.shape:
+        if s % 2:
+            raise ValueError("size not divisible by 2")
+        shape += [s // 2, 2]
+    return M.reshape(shape).mean(axis=tuple(range(1, 2 * d, 2)))
+
+
+def prolongate_adjoint(C: np.ndarray) -> np.ndarray:
+    """Transpose of ``restrict``: every child receives its parent's value / 2^d."""
+    C = np.asarray(C, dtype=np.float64)
+    d = C.ndim
+    F = C
+    for ax in range(d):
+        F = np.repeat(F, 2, axis=ax)
+    return F / float(2 ** d)
+
+
+@dataclasses.dataclass
+class Params:
+    """Problem statement (Sec. 3.3): window P_a per axis, number of levels, threshold."""
+    ndim: int
+    window: tuple
+    levels: int = 1
+    threshold: str = "soft"
+    alpha: float = 10.0
+    weight_exp: float | None = None   # w_l = 2^{weight_exp (l-1)}; None -> d/2
+
+    def weights(self) -> np.ndarray:
+        e = self.ndim / 2.0 if self.weight_exp is None else self.weight_exp
+        return np.array([2.0 ** (e * l) for l in range(self.levels)])
+
+
+def pyramid(M: np.ndarray, levels: int):
+    out = [np.asarray(M, dtype=np.float64)]
+    for _ in range(1, levels):
+        out.append(restrict(out[-1]))
+    return out
+
+
+def descriptor(M, p: Params, levels_out: bool = False):
+    """Eq. mg: D = [w_1 S_bar_1, w_2 S_bar_2, ...] on the half window of every level."""
+    H = half_window(p.ndim, p.window)
+    pyr = pyramid(M, p.levels)
+    w = p.weights()
+    blocks = [w[l] * sbar(pyr[l], H, p.threshold, p.alpha) for l in range(p.levels)]
+    D = np.concatenate(blocks)
+    return (D, blocks) if levels_out else D
+
+
+def descriptor_shifts(M, p: Params, level: int, shifts) -> np.ndarray:
+    """Sampled entries: w_l * S_bar_l(r) for an explicit shift list at one level."""
+    pyr = pyramid(M, level + 1)
+    return p.weights()[level] * sbar(pyr[level], shifts, p.threshold, p.alpha)
+
+
+# ----------------------------------------------------------------------------- loss
+
+def box_excess(M: np.ndarray) -> np.ndarray:
+    """(M-1) H(M-1) - M H(-M) with H(0) = 0 (Sec. 3.1)."""
+    M = np.asarray(M, dtype=np.float64)
+    return np.where(M - 1.0 > 0, M - 1.0, 0.0) - np.where(-M > 0, M, 0.0)
+
+
+def loss(M, D_des, p: Params, mode: str = "norm", lambda0: float | None = None, bc: bool = True,
+         D=None) -> dict:
+    """Eq. L_func_dMCR.  mode 'norm': L = E + lambda E_bc, lambda = lambda0 E (the paper);
+    mode 'squared': L = E^2 + lambda0 E^2 E_bc.  lambda0 defaults to the finest pixel count.
+    """
+    M = np.asarray(M, dtype=np.float64)
+    N = M.size
+    if lambda0 is None:
+        lambda0 = float(N)
+    if not bc:
+        lambda0 = 0.0
+    if D is None:
+        D = descriptor(M, p)
+    rho = D - np.asarray(D_des, dtype=np.float64)
+    E2 = float(np.sum(rho * rho))
+    E = float(np.sqrt(E2))
+    Ebc = float(np.sum((box_excess(M) / N) ** 2))
+    phi = E if mode == "norm" else E2
+    lam = lambda0 * phi
+    L = phi + lam * Ebc
+    ref = float(np.sqrt(np.sum(np.asarray(D_des, dtype=np.float64) ** 2)))
+    return {"E": E, "E2": E2, "Ebc": Ebc, "lambda": lam, "L": L,
+            "rel_err": E / ref if ref > 0 else float("inf"), "rho": rho, "lambda0": lambda0}
+
+
+def level_vjp(M_level, p: Params, G_half, positions=None) -> np.ndarray:
+    """g_y = sum_r G(r) dS_bar(r)/dM_y for one level (positions: flat indices or all)."""
+    lib = _load()
+    M3, n = _as3(M_level)
+    s3 = _shifts3(half_window(p.ndim, p.window), M_level.ndim)
+    G = np.ascontiguousarray(G_half, dtype=np.float64)
+    if positions is None:
+        npos = int(np.prod(n))
+        out = np.empty(npos, dtype=np.float64)
+        lib.oracle_vjp_level(_dp(M3), _i64p(n), _i32p(s3), s3.shape[0], _dp(G), _KIND[p.threshold],
+                             p.alpha, None, npos, _dp(out))
+        return out.reshape(M_level.shape)
+    pos = np.ascontiguousarray(positions, dtype=np.int64)
+    out = np.empty(pos.size, dtype=np.float64)
+    lib.oracle_vjp_level(_dp(M3), _i64p(n), _i32p(s3), s3.shape[0], _dp(G), _KIND[p.threshold],
+                         p.alpha, _i64p(pos), pos.size, _dp(out))
+    return out
+
+
+def descriptor_vjp(M, p: Params, grad_D) -> np.ndarray:
+    """Gradient of <grad_D, D(M)> w.r.t. the finest field, back-propagated through every
+    level at once (Sec. 3.3): per-level VJP, then the transpose of the pooling chain."""
+    M = np.asarray(M, dtype=np.float64)
+    K = half_window(p.ndim, p.window).shape[0]
+    pyr = pyramid(M, p.levels)
+    w = p.weights()
+    g = None
+    for l in reversed(range(p.levels)):
+        gl = level_vjp(pyr[l], p, w[l] * np.asarray(grad_D[l * K:(l + 1) * K], dtype=np.float64))
+        g = gl if g is None else gl + prolongate_adjoint(g)
+    return g
+
+
+def loss_grad(M, D_des, p: Params, mode: str = "norm", lambda0: float | None = None, bc: bool = True):
+    """Loss (as ``loss``) and dL/dM by the chain rule:
+    dL/dM = phi'(E) (1 + lambda0 E_bc) dE/dM + lambda0 phi(E) dE_bc/dM."""
+    M = np.asarray(M, dtype=np.float64)
+    N = M.size
+    out = loss(M, D_des, p, mode, lambda0, bc)
+    lam0 = out["lambda0"]
+    rho, E, Ebc = out["rho"], out["E"], out["Ebc"]
+    if mode == "norm":
+        dphi_dD = rho / E if E > 0 else np.zeros_like(rho)
+        phi = E
+    else:
+        dphi_dD = 2.0 * rho
+        phi = out["E2"]
+    g = descriptor_vjp(M, p, dphi_dD * (1.0 + lam0 * Ebc))
+    ex = box_excess(M)
+    dex = np.where(M - 1.0 > 0, 1.0, 0.0) - np.where(-M > 0, 1.0, 0.0)
+    g = g + lam0 * phi * 2.0 * (ex / N) * dex / N
+    return out, g
+
+
+# ----------------------------------------------------------------------------- optimiser
+
+def adam_step(M, g, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-7):
+    """One Adam step in the TensorFlow/Keras form; t is the 1-based step count."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    lr_t = lr * np.sqrt(1.0 - beta2 ** t) / (1.0 - beta1 ** t)
+    M = M - lr_t * m / (np.sqrt(v) + eps)
+    return M, m, v
+
+
+def reconstruct(M0, D_des, p: Params, iters: int, tol_rel: float = 0.0, lr=1e-3, beta1=0.9,
+                beta2=0.999, eps=1e-7, mode="norm", lambda0=None, bc=True, check_every=1):
+    """Flow chart of Sec. 3: evaluate L and dL/dM, stop when rel_err < tol_rel (tested every
+    ``check_every`` iterations), otherwise take one Adam step.  Returns the field and the
+    per-iteration loss records."""
+    M = np.array(M0, dtype=np.float64)
+    m = np.zeros_like(M)
+    v = np.zeros_like(M)
+    hist = []
+    for t in range(1, iters + 1):
+        out, g = loss_grad(M, D_des, p, mode, lambda0, bc)
+        hist.append({k: out[k] for k in ("E", "E2", "Ebc", "lambda", "L", "rel_err")})
+        if tol_rel > 0 and (t - 1) % check_every == 0 and out["rel_err"] < tol_rel:
+            break
+        M, m, v = adam_step(M, g, m, v, t, lr, beta1, beta2, eps)
+    return M, hist
+
+
+def round_field(M) -> np.ndarray:
+    """Rounding for evaluation (Sec. 4.1): values >= 0.5 become phase 1."""
+    return (np.asarray(M) >= 0.5).astype(np.float64)
