@@ -1,0 +1,196 @@
+/*
+ * dmcr.h -- C ABI of the GB300 (sm_103a) library for differentiable microstructure
+ * characterization and reconstruction (Seibert, Ambati, Rassloff, Kaestner,
+ * "Reconstructing random heterogeneous media through differentiable optimization",
+ * arXiv 2103.09686).
+ *
+ * The library evaluates, for a relaxed (real-valued) periodic 2-D or 3-D phase field M:
+ *   - the soft-thresholded two-point correlation descriptor
+ *       S_bar_l(r) = (1/N_l) sum_x f( a_x(r) )^2,
+ *       a_x(r) = (M_x + M_{x+r mod n}) / 2  (r != 0),  a_x(0) = M_x
+ *     (Sec. 3.2.2 Eq. s3 with p=r, q=s; Sec. 3.2.3 Eq. convdef; Sec. 3.2.4
+ *     Eq. softthreshold with f(0)=0, f(1)=1, f''(0.75)=0, alpha=10),
+ *     on every level l of the simultaneous multigrid pyramid and concatenated as
+ *     D = [w_1 S_bar_1, w_2 S_bar_2, ...] (Sec. 3.3 Eq. mg);
+ *   - the loss L = E + lambda E_bc, E = ||D - D_des||_2, lambda = lambda0 E
+ *     (Sec. 3.1 Eq. L_func_dMCR) and its exact gradient with respect to every pixel
+ *     or voxel, back-propagated through all levels at once (Sec. 3.3);
+ *   - Adam reconstructions driven by that gradient (Sec. 3, Eq. M-update; App. B).
+ *
+ * Conventions common to every call
+ *   - Every call returns a dmcr_status.  On failure dmcr_last_error() (thread local)
+ *     returns a one-line reason; nothing has been enqueued when argument validation
+ *     fails (DMCR_EINVAL).
+ *   - Fields are FP32, C order (n[0] slowest).  2-D fields use n[0], n[1]; 3-D fields
+ *     n[0], n[1], n[2].  Shift component r_a runs along array axis a.
+ *   - Every float pointer is CALLER-OWNED DEVICE memory unless stated otherwise; the
+ *     library never frees caller memory and never keeps a pointer after a call returns.
+ *   - Scratch memory: calls that need it take `ws`, a caller-owned device buffer of at
+ *     least dmcr_workspace_size() bytes, 256-byte aligned.  The library allocates no
+ *     device memory in those calls.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Work is enqueued asynchronously on it unless the call says otherwise.
+ *   - Half-window layout of one level (HALF, the canonical order), with P the window:
+ *       2-D: (0, 0..P1), then (1..P0, -P1..P1) row-major;
+ *       3-D: (0, 0, 0..P2), (0, 1..P1, -P2..P2), (1..P0, -P1..P1, -P2..P2).
+ *     K_half = (prod_a (2 P_a + 1) + 1) / 2 entries; the descriptor holds `levels`
+ *     such blocks, finest level first.
+ */
+#ifndef DMCR_H
+#define DMCR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DMCR_OK = 0,
+    DMCR_EINVAL = 1,      /* invalid argument (sizes, window, levels, null pointer) */
+    DMCR_ENOMEM = 2,      /* workspace too small */
+    DMCR_ECUDA = 3,       /* a CUDA runtime call failed */
+    DMCR_ENONFINITE = 4,  /* the loss became NaN or Inf */
+    DMCR_ETIMEOUT = 5,    /* a bounded device wait ran out */
+    DMCR_ENOTSUP = 6      /* combination not supported by this build */
+} dmcr_status;
+
+enum { DMCR_SOFT = 0, DMCR_IDENTITY = 1 };           /* threshold (Sec. 3.2.4; f(x)=x ablation of Sec. 4.1) */
+enum { DMCR_PATH_AUTO = 0, DMCR_PATH_DIRECT = 1 };   /* evaluation path */
+enum { DMCR_LOSS_NORM = 0, DMCR_LOSS_SQUARED = 1 };  /* L = E(1 + lambda0 E_bc)  |  E^2 (1 + lambda0 E_bc) */
+enum { DMCR_PROLONG_ADJOINT_ACCUMULATE = 0, DMCR_PROLONG_INJECT = 1 };
+enum { DMCR_INIT_CALLER = 0, DMCR_INIT_UNIFORM_SEEDED = 1 };
+
+/* Problem statement (Sec. 3.3): field size, window P_a per axis, multigrid levels. */
+typedef struct {
+    int ndim;                /* 2 or 3 */
+    int64_t n[3];            /* finest field sizes, C order; n[a] divisible by 2^(levels-1) */
+    int window[3];           /* P_a >= 0 per axis; at every level P_a <= n_a(level) / 2 */
+    int levels;              /* >= 1; level l has size n / 2^(l-1), mean of 2^d children */
+    int threshold;           /* DMCR_SOFT (default) or DMCR_IDENTITY */
+    float alpha;             /* soft-threshold slope; the paper uses 10 */
+    float level_weight_exp;  /* w_l = 2^(level_weight_exp (l-1)); <0 selects ndim/2 (2^(l-1) in 2-D) */
+    int path;                /* DMCR_PATH_AUTO or DMCR_PATH_DIRECT */
+} dmcr_params;
+
+/* Loss options (Sec. 3.1).  lambda = lambda0 * E (NORM) or lambda0 * E^2 (SQUARED). */
+typedef struct {
+    int mode;                /* DMCR_LOSS_NORM (the paper) or DMCR_LOSS_SQUARED */
+    float lambda0;           /* <0 selects the finest pixel count N */
+    int bc_on;               /* 0 disables the box penalty E_bc */
+} dmcr_loss_opts;
+
+/* loss_out layout written by dmcr_loss_grad / dmcr_reconstruct (6 floats) */
+enum { DMCR_OUT_E = 0, DMCR_OUT_E2 = 1, DMCR_OUT_EBC = 2, DMCR_OUT_LAMBDA = 3, DMCR_OUT_L = 4,
+       DMCR_OUT_REL_ERR = 5, DMCR_OUT_COUNT = 6 };
+
+/* Reconstruction options (flow chart of Sec. 3; Adam at the TensorFlow defaults, App. B). */
+typedef struct {
+    int max_iters;           /* iterations (loss + gradient + Adam step) at most */
+    float tol_rel;           /* stop when ||D - D_des|| / ||D_des|| < tol_rel (0: never) */
+    float lr, beta1, beta2, eps;   /* 1e-3, 0.9, 0.999, 1e-7 */
+    dmcr_loss_opts loss;
+    int init;                /* DMCR_INIT_CALLER or DMCR_INIT_UNIFORM_SEEDED */
+    uint64_t seed;           /* SplitMix64 seed for DMCR_INIT_UNIFORM_SEEDED */
+    int check_every;         /* stopping test every k iterations (>= 1) */
+} dmcr_recon_opts;
+
+/* Adam state of one job: caller-owned device buffers, kept between calls (resume). */
+typedef struct {
+    float* m;                /* N floats, zero for a fresh start */
+    float* v;                /* N floats, zero for a fresh start */
+    int64_t step;            /* Adam steps taken so far (host value, updated on return) */
+} dmcr_adam_state;
+
+typedef struct {
+    int iterations;          /* Adam steps taken in this call */
+    int converged;           /* 1 if tol_rel was reached */
+    float loss[DMCR_OUT_COUNT];   /* loss_out of the last evaluated iterate */
+    int status;              /* dmcr_status of the run */
+} dmcr_recon_report;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int dmcr_version(void);
+
+/* Reason for the last failing call on this host thread ("" if none). */
+const char* dmcr_last_error(void);
+
+/* Descriptor length sum_l K_half (all levels).  Returns DMCR_EINVAL on bad params. */
+dmcr_status dmcr_descriptor_length(const dmcr_params* p, int64_t* length);
+
+/* Bytes of scratch memory (`ws`) the calls below need for these params. */
+dmcr_status dmcr_workspace_size(const dmcr_params* p, size_t* bytes);
+
+/*
+ * dmcr_descriptor -- the multigrid descriptor D of `field` (Sec. 3.2, Sec. 3.3 Eq. mg).
+ *   field: N floats (device, read only).  desc: dmcr_descriptor_length floats (device,
+ *   written).  Also used to characterise a target: D_des = dmcr_descriptor(target).
+ *   Errors: DMCR_EINVAL (params), DMCR_ENOMEM (ws_bytes too small), DMCR_ECUDA.
+ */
+dmcr_status dmcr_descriptor(const dmcr_params* p, const float* field, float* desc,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * dmcr_loss_grad -- loss and exact gradient (Sec. 3.1 Eq. L_func_dMCR; Sec. 3.3).
+ *   field: N floats; target_desc: descriptor_length floats (device, read only).
+ *   loss_out: DMCR_OUT_COUNT floats (device, written: E, E^2, E_bc, lambda, L, rel_err).
+ *   grad: N floats (device, written) or NULL for the loss alone.
+ *   desc_out: descriptor_length floats (device, written) or NULL.
+ *   At E = 0 the NORM-mode gradient of E is defined as 0.
+ */
+dmcr_status dmcr_loss_grad(const dmcr_params* p, const dmcr_loss_opts* opts, const float* field,
+                           const float* target_desc, float* loss_out, float* grad, float* desc_out,
+                           void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * dmcr_descriptor_vjp -- grad_field = (dD/dM)^T grad_desc for an arbitrary upstream
+ *   gradient (the backward of a differentiable descriptor; Sec. 3.3: through every level).
+ *   grad_desc: descriptor_length floats; grad_field: N floats (device, written).
+ */
+dmcr_status dmcr_descriptor_vjp(const dmcr_params* p, const float* field, const float* grad_desc,
+                                float* grad_field, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * dmcr_restrict -- one multigrid coarsening (Sec. 3.3; read: each coarse cell is the mean
+ *   of its 2^d children).  n_fine: sizes of `fine` (each even).  coarse: N/2^d floats.
+ */
+dmcr_status dmcr_restrict(int ndim, const int64_t n_fine[3], const float* fine, float* coarse,
+                          void* stream);
+
+/*
+ * dmcr_prolongate -- coarse to fine (Sec. 3.3).  mode DMCR_PROLONG_ADJOINT_ACCUMULATE:
+ *   fine += R^T coarse, i.e. every child gains parent / 2^d (the transpose of
+ *   dmcr_restrict, used to back-propagate through the levels); DMCR_PROLONG_INJECT:
+ *   fine = parent value copied to every child (coarse-to-fine warm start).
+ *   n_coarse: sizes of `coarse`; fine has 2^d times as many cells.
+ */
+dmcr_status dmcr_prolongate(int ndim, const int64_t n_coarse[3], const float* coarse, float* fine,
+                            int mode, void* stream);
+
+/*
+ * dmcr_init_uniform -- field[i] = top 24 bits of SplitMix64(seed, i) * 2^-24, the
+ *   counter-based uniform[0,1) start of a reconstruction ("randomly initialized", Sec. 3).
+ */
+dmcr_status dmcr_init_uniform(float* field, int64_t count, uint64_t seed, void* stream);
+
+/*
+ * dmcr_reconstruct -- Adam reconstruction (flow chart of Sec. 3; Eq. M-update; App. B).
+ *   Iteration t: evaluate L and dL/dM at the current field; if (t-1) % check_every == 0
+ *   and rel_err < tol_rel, stop; otherwise take one Adam step.  The iteration runs as a
+ *   captured CUDA graph; the stopping test is taken on the device.
+ *   field_inout: N floats, the start (DMCR_INIT_CALLER) and the result.
+ *   state: Adam moments (device) and step count (host), updated for resume.
+ *   history: max_iters * 3 floats (device: E, L, rel_err per iteration) or NULL.
+ *   SYNCHRONOUS: returns after the run, with `report` (host) filled in.
+ */
+dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* opts,
+                             const float* target_desc, float* field_inout, dmcr_adam_state* state,
+                             float* history, dmcr_recon_report* report, void* ws, size_t ws_bytes,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMCR_H */

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libdmcr (include/dmcr.h): argument marshalling only.
+
+Every function named ``dmcr_*`` here calls the C entry point of the same name with the
+device pointers of CUDA tensors and the current PyTorch stream; all arithmetic runs in
+the library's kernels.  The library must be built (``__graft_entry__.build()`` or
+``python -m paper_2103_09686_gb300._build``); nothing here falls back to another
+implementation when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import torch
+
+from . import _build
+
+c_int, c_int64, c_float, c_void_p, c_uint64, c_size_t = (ctypes.c_int, ctypes.c_int64, ctypes.c_float,
+                                                        ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t)
+
+DMCR_OK, DMCR_EINVAL, DMCR_ENOMEM, DMCR_ECUDA, DMCR_ENONFINITE, DMCR_ETIMEOUT, DMCR_ENOTSUP = range(7)
+DMCR_SOFT, DMCR_IDENTITY = 0, 1
+DMCR_PATH_AUTO, DMCR_PATH_DIRECT = 0, 1
+DMCR_LOSS_NORM, DMCR_LOSS_SQUARED = 0, 1
+DMCR_PROLONG_ADJOINT_ACCUMULATE, DMCR_PROLONG_INJECT = 0, 1
+DMCR_INIT_CALLER, DMCR_INIT_UNIFORM_SEEDED = 0, 1
+OUT_NAMES = ("E", "E2", "Ebc", "lambda", "L", "rel_err")
+
+
+class dmcr_params(ctypes.Structure):
+    _fields_ = [("ndim", c_int), ("n", c_int64 * 3), ("window", c_int * 3), ("levels", c_int),
+                ("threshold", c_int), ("alpha", c_float), ("level_weight_exp", c_float), ("path", c_int)]
+
+
+class dmcr_loss_opts(ctypes.Structure):
+    _fields_ = [("mode", c_int), ("lambda0", c_float), ("bc_on", c_int)]
+
+
+class dmcr_recon_opts(ctypes.Structure):
+    _fields_ = [("max_iters", c_int), ("tol_rel", c_float), ("lr", c_float), ("beta1", c_float),
+                ("beta2", c_float), ("eps", c_float), ("loss", dmcr_loss_opts), ("init", c_int),
+                ("seed", c_uint64), ("check_every", c_int)]
+
+
+class dmcr_adam_state(ctypes.Structure):
+    _fields_ = [("m", c_void_p), ("v", c_void_p), ("step", c_int64)]
+
+
+class dmcr_recon_report(ctypes.Structure):
+    _fields_ = [("iterations", c_int), ("converged", c_int), ("loss", c_float * 6), ("status", c_int)]
+
+
+class DmcrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("dmcr status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(build_if_missing: bool = False):
+    """Load libdmcr.so from the package directory (raises when it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing or not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError("libdmcr.so is not built: run __graft_entry__.build() or "
+                                   "python -m paper_2103_09686_gb300._build")
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        P = ctypes.POINTER
+        lib.dmcr_version.restype = c_int
+        lib.dmcr_last_error.restype = ctypes.c_char_p
+        lib.dmcr_descriptor_length.argtypes = [P(dmcr_params), P(c_int64)]
+        lib.dmcr_workspace_size.argtypes = [P(dmcr_params), P(c_size_t)]
+        lib.dmcr_descriptor.argtypes = [P(dmcr_params), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+        lib.dmcr_loss_grad.argtypes = [P(dmcr_params), P(dmcr_loss_opts), c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_void_p, c_void_p, c_size_t, c_void_p]
+        lib.dmcr_descriptor_vjp.argtypes = [P(dmcr_params), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                                            c_void_p]
+        lib.dmcr_restrict.argtypes = [c_int, P(c_int64), c_void_p, c_void_p, c_void_p]
+        lib.dmcr_prolongate.argtypes = [c_int, P(c_int64), c_void_p, c_void_p, c_int, c_void_p]
+        lib.dmcr_init_uniform.argtypes = [c_void_p, c_int64, c_uint64, c_void_p]
+        lib.dmcr_reconstruct.argtypes = [P(dmcr_params), P(dmcr_recon_opts), c_void_p, c_void_p, P(dmcr_adam_state),
+                                         c_void_p, P(dmcr_recon_report), c_void_p, c_size_t, c_void_p]
+        for name in ("dmcr_descriptor_length", "dmcr_workspace_size", "dmcr_descriptor", "dmcr_loss_grad",
+                     "dmcr_descriptor_vjp", "dmcr_restrict", "dmcr_prolongate", "dmcr_init_uniform",
+                     "dmcr_reconstruct"):
+            getattr(lib, name).restype = c_int
+        _lib = lib
+        return lib
+
+
+def _check(st: int):
+    if st != DMCR_OK:
+        raise DmcrError(st, load().dmcr_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("tensor must be contiguous float32")
+    return t.data_ptr()
+
+
+# ----------------------------------------------------------------------------- params
+
+@dataclasses.dataclass(frozen=True)
+class Params:
+    """Problem statement (Sec. 3.3): field shape, window P_a per axis, multigrid levels."""
+    shape: tuple
+    window: tuple
+    levels: int = 1
+    threshold: int = DMCR_SOFT
+    alpha: float = 10.0
+    level_weight_exp: float = -1.0
+    path: int = DMCR_PATH_AUTO
+
+    @property
+    def ndim(self) -> int:
+        return len(self.shape)
+
+    def c(self) -> dmcr_params:
+        p = dmcr_params()
+        p.ndim = len(self.shape)
+        for a, s in enumerate(self.shape):
+            p.n[a] = int(s)
+        for a, w in enumerate(self.window):
+            p.window[a] = int(w)
+        p.levels = int(self.levels)
+        p.threshold = int(self.threshold)
+        p.alpha = float(self.alpha)
+        p.level_weight_exp = float(self.level_weight_exp)
+        p.path = int(self.path)
+        return p
+
+
+@dataclasses.dataclass(frozen=True)
+class LossOpts:
+    mode: int = DMCR_LOSS_NORM
+    lambda0: float = -1.0      # <0: finest pixel count
+    bc_on: bool = True
+
+    def c(self) -> dmcr_loss_opts:
+        return dmcr_loss_opts(int(self.mode), float(self.lambda0), int(bool(self.bc_on)))
+
+
+@dataclasses.dataclass(frozen=True)
+class ReconOpts:
+    max_iters: int = 200
+    tol_rel: float = 0.0
+    lr: float = 1e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-7
+    loss: LossOpts = LossOpts()
+    init: int = DMCR_INIT_CALLER
+    seed: int = 0
+    check_every: int = 1
+
+    def c(self) -> dmcr_recon_opts:
+        o = dmcr_recon_opts()
+        o.max_iters = int(self.max_iters)
+        o.tol_rel = float(self.tol_rel)
+        o.lr, o.beta1, o.beta2, o.eps = float(self.lr), float(self.beta1), float(self.beta2), float(self.eps)
+        o.loss = self.loss.c()
+        o.init = int(self.init)
+        o.seed = int(self.seed) & ((1 << 64) - 1)
+        o.check_every = int(self.check_every)
+        return o
+
+
+# ----------------------------------------------------------------------------- raw C entry points
+
+def dmcr_version() -> int:
+    return load().dmcr_version()
+
+
+def dmcr_descriptor_length(p: Params) -> int:
+    out = c_int64()
+    _check(load().dmcr_descriptor_length(ctypes.byref(p.c()), ctypes.byref(out)))
+    return out.value
+
+
+def dmcr_workspace_size(p: Params) -> int:
+    out = c_size_t()
+    _check(load().dmcr_workspace_size(ctypes.byref(p.c()), ctypes.byref(out)))
+    return out.value
+
+
+def workspace(p: Params, device=None) -> torch.Tensor:
+    n = dmcr_workspace_size(p)
+    return torch.empty(max(n, 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def dmcr_descriptor(p: Params, field, desc, ws=None, stream=None):
+    ws = workspace(p, field.device) if ws is None else ws
+    _check(load().dmcr_descriptor(ctypes.byref(p.c()), _ptr(field), _ptr(desc), ws.data_ptr(), ws.numel(),
+                                  _stream(stream)))
+    return desc
+
+
+def dmcr_loss_grad(p: Params, opts: LossOpts, field, target_desc, loss_out, grad=None, desc_out=None, ws=None,
+                   stream=None):
+    ws = workspace(p, field.device) if ws is None else ws
+    _check(load().dmcr_loss_grad(ctypes.byref(p.c()), ctypes.byref(opts.c()), _ptr(field), _ptr(target_desc),
+                                 _ptr(loss_out), _ptr(grad), _ptr(desc_out), ws.data_ptr(), ws.numel(),
+                                 _stream(stream)))
+
+
+def dmcr_descriptor_vjp(p: Params, field, grad_desc, grad_field, ws=None, stream=None):
+    ws = workspace(p, field.device) if ws is None else ws
+    _check(load().dmcr_descriptor_vjp(ctypes.byref(p.c()), _ptr(field), _ptr(grad_desc), _ptr(grad_field),
+                                      ws.data_ptr(), ws.numel(), _stream(stream)))
+    return grad_field
+
+
+def dmcr_restrict(fine, coarse, stream=None):
+    n = (c_int64 * 3)(*list(fine.shape) + [0] * (3 - fine.dim()))
+    _check(load().dmcr_restrict(fine.dim(), n, _ptr(fine), _ptr(coarse), _stream(stream)))
+    return coarse
+
+
+def dmcr_prolongate(coarse, fine, mode=DMCR_PROLONG_ADJOINT_ACCUMULATE, stream=None):
+    n = (c_int64 * 3)(*list(coarse.shape) + [0] * (3 - coarse.dim()))
+    _check(load().dmcr_prolongate(coarse.dim(), n, _ptr(coarse), _ptr(fine), int(mode), _stream(stream)))
+    return fine
+
+
+def dmcr_init_uniform(field, seed: int, stream=None):
+    _check(load().dmcr_init_uniform(_ptr(field), field.numel(), int(seed) & ((1 << 64) - 1), _stream(stream)))
+    return field
+
+
+def dmcr_reconstruct(p: Params, opts: ReconOpts, target_desc, field, m, v, step: int = 0, history=None, ws=None,
+                     stream=None):
+    """Runs the reconstruction (synchronous).  Returns (report dict, new Adam step)."""
+    ws = workspace(p, field.device) if ws is None else ws
+    st = dmcr_adam_state(_ptr(m), _ptr(v), int(step))
+    rep = dmcr_recon_report()
+    status = load().dmcr_reconstruct(ctypes.byref(p.c()), ctypes.byref(opts.c()), _ptr(target_desc), _ptr(field),
+                                     ctypes.byref(st), _ptr(history), ctypes.byref(rep), ws.data_ptr(), ws.numel(),
+                                     _stream(stream))
+    _check(status)
+    report = {"iterations": rep.iterations, "converged": bool(rep.converged), "status": rep.status}
+    report.update({k: float(rep.loss[i]) for i, k in enumerate(OUT_NAMES)})
+    return report, st.step
+
+
+# ----------------------------------------------------------------------------- conveniences
+
+def descriptor(field: torch.Tensor, p: Params, ws=None) -> torch.Tensor:
+    desc = torch.empty(dmcr_descriptor_length(p), dtype=torch.float32, device=field.device)
+    return dmcr_descriptor(p, field, desc, ws)
+
+
+def loss_grad(field: torch.Tensor, target_desc: torch.Tensor, p: Params, opts: LossOpts = LossOpts(),
+              want_grad: bool = True, ws=None):
+    loss = torch.empty(6, dtype=torch.float32, device=field.device)
+    grad = torch.empty_like(field) if want_grad else None
+    dmcr_loss_grad(p, opts, field, target_desc, loss, grad, None, ws)
+    return loss, grad
+
+
+def descriptor_vjp(field: torch.Tensor, grad_desc: torch.Tensor, p: Params, ws=None) -> torch.Tensor:
+    g = torch.empty_like(field)
+    return dmcr_descriptor_vjp(p, field, grad_desc, g, ws)

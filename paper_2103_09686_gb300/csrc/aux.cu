@@ -1,0 +1,227 @@
+// Memory-bound kernels around the correlation: multigrid restriction / prolongation
+// (Sec. 3.3), the box-penalty reduction and the loss (Sec. 3.1, Eq. L_func_dMCR), the
+// fused gradient assembly + Adam update (Eq. M-update, App. B) and the counter-based
+// uniform start field.  All reductions use fixed grids and fixed summation orders, so
+// every result is bitwise reproducible run to run.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace dmcr {
+
+// --------------------------------------------------------------------- multigrid
+
+// coarse[c] = mean of the 2^d children of c (children summed in a fixed order).
+__global__ void restrict_kernel(int ndim, int64_t c0, int64_t c1, int64_t c2, const float* __restrict__ fine,
+                                float* __restrict__ coarse, const int* __restrict__ done) {
+    if (done != nullptr && *done) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t Nc = c0 * c1 * c2;
+    if (i >= Nc) return;
+    const int64_t x = i % c2, y = (i / c2) % c1, z = i / (c1 * c2);
+    const int64_t f1 = 2 * c1, f2 = 2 * c2;
+    float s;
+    if (ndim == 2) {
+        const float* r0 = fine + (2 * y) * f2 + 2 * x;
+        const float* r1 = r0 + f2;
+        s = ((r0[0] + r0[1]) + (r1[0] + r1[1])) * 0.25f;
+    } else {
+        const float* p0 = fine + ((2 * z) * f1 + 2 * y) * f2 + 2 * x;
+        const float* p1 = p0 + f1 * f2;
+        s = (((p0[0] + p0[1]) + (p0[f2] + p0[f2 + 1])) + ((p1[0] + p1[1]) + (p1[f2] + p1[f2 + 1]))) * 0.125f;
+    }
+    coarse[i] = s;
+}
+
+void launch_restrict(int ndim, const int64_t nf[3], const float* fine, float* coarse, const int* done,
+                     cudaStream_t s) {
+    const int64_t c0 = (ndim == 2) ? 1 : nf[0] / 2;
+    const int64_t c1 = nf[1] / 2, c2 = nf[2] / 2;
+    const int64_t Nc = c0 * c1 * c2;
+    const int th = 256;
+    restrict_kernel<<<(unsigned)((Nc + th - 1) / th), th, 0, s>>>(ndim, c0, c1, c2, fine, coarse, done);
+}
+
+// fine[f] += coarse[parent(f)] / 2^d   (transpose of restrict)   or   fine[f] = coarse[parent(f)]
+__global__ void prolongate_kernel(int ndim, int64_t c0, int64_t c1, int64_t c2, const float* __restrict__ coarse,
+                                  float* __restrict__ fine, int mode) {
+    const int64_t f0 = (ndim == 2) ? 1 : 2 * c0, f1 = 2 * c1, f2 = 2 * c2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= f0 * f1 * f2) return;
+    const int64_t x = i % f2, y = (i / f2) % f1, z = i / (f1 * f2);
+    const int64_t pz = (ndim == 2) ? 0 : z / 2;
+    const float v = coarse[(pz * c1 + y / 2) * c2 + x / 2];
+    if (mode == 1) fine[i] = v;
+    else fine[i] += v * (ndim == 2 ? 0.25f : 0.125f);
+}
+
+void launch_prolongate(int ndim, const int64_t nc[3], const float* coarse, float* fine, int mode, cudaStream_t s) {
+    const int64_t c0 = (ndim == 2) ? 1 : nc[0];
+    const int64_t Nf = (ndim == 2 ? 4 : 8) * c0 * nc[1] * nc[2];
+    const int th = 256;
+    prolongate_kernel<<<(unsigned)((Nf + th - 1) / th), th, 0, s>>>(ndim, c0, nc[1], nc[2], coarse, fine, mode);
+}
+
+// --------------------------------------------------------------------- loss
+
+// Box excess of Sec. 3.1: (M-1) H(M-1) - M H(-M), H(0) = 0.
+__device__ __forceinline__ float box_excess(float M) {
+    return M > 1.f ? M - 1.f : (M < 0.f ? -M : 0.f);
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+    // fixed-order tree over the block (blockDim.x a power of two <= 1024)
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void penalty_kernel(const float* __restrict__ M, int64_t N, double* __restrict__ partials,
+                               const int* __restrict__ done) {
+    if (done != nullptr && *done) return;
+    __shared__ double sh[256];
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double e = (double)box_excess(M[i]);
+        acc += e * e;
+    }
+    const double t = block_sum_d(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+void launch_penalty(const float* field, int64_t N, double* partials, const int* done, cudaStream_t s) {
+    penalty_kernel<<<NPEN_BLOCKS, 256, 0, s>>>(field, N, partials, done);
+}
+
+// Single block: E, E^2, E_bc, lambda, L, rel_err and the gradient scalars; in a
+// reconstruction also the stopping test and the Adam step bookkeeping.
+__global__ void __launch_bounds__(1024) loss_kernel(LossParams lp, const float* __restrict__ desc,
+                                                    const float* __restrict__ target,
+                                                    const double* __restrict__ pen, Scalars* sc,
+                                                    float* __restrict__ loss_out, float* __restrict__ history) {
+    if (lp.recon && sc->done) return;
+    __shared__ double sh[1024];
+    double r2 = 0.0, t2 = 0.0;
+    for (int64_t k = threadIdx.x; k < lp.Ktot; k += blockDim.x) {
+        const double t = (double)target[k];
+        const double r = (double)desc[k] - t;
+        r2 += r * r;
+        t2 += t * t;
+    }
+    const double E2 = block_sum_d(r2, sh);
+    const double T2 = block_sum_d(t2, sh);
+    double pe = 0.0;
+    if (threadIdx.x < NPEN_BLOCKS && pen != nullptr) pe = pen[threadIdx.x];
+    const double ex2 = block_sum_d(pe, sh);
+    if (threadIdx.x != 0) return;
+    const double N = (double)lp.N;
+    const double lam0 = lp.bc_on ? (double)lp.lambda0 : 0.0;
+    const double E = sqrt(E2);
+    const double Ebc = ex2 / (N * N);
+    const double phi = lp.mode == 0 ? E : E2;
+    const double lam = lam0 * phi;
+    const double L = phi + lam * Ebc;
+    const double rel = T2 > 0 ? E / sqrt(T2) : INFINITY;
+    const float out[6] = {(float)E, (float)E2, (float)Ebc, (float)lam, (float)L, (float)rel};
+    for (int i = 0; i < 6; ++i) sc->loss[i] = out[i];
+    if (loss_out != nullptr)
+        for (int i = 0; i < 6; ++i) loss_out[i] = out[i];
+    // dL/dD = phi'(E) (1 + lam0 E_bc) dE/dD ;  dL/dM (penalty) = lam0 phi dE_bc/dM
+    double gs;
+    if (lp.mode == 0) gs = E > 0 ? (1.0 + lam0 * Ebc) / E : 0.0;
+    else gs = 2.0 * (1.0 + lam0 * Ebc);
+    sc->gscale = (float)gs;
+    sc->pen_coef = (float)(2.0 * lam0 * phi / (N * N));
+    if (!lp.recon) return;
+    const int it = sc->iter;
+    if (history != nullptr && it < lp.max_iters) {
+        history[3 * it + 0] = (float)E;
+        history[3 * it + 1] = (float)L;
+        history[3 * it + 2] = (float)rel;
+    }
+    sc->iter = it + 1;
+    if (!isfinite(L)) { sc->done = 2; return; }
+    if (lp.tol_rel > 0.f && (it % lp.check_every) == 0 && rel < (double)lp.tol_rel) { sc->done = 1; return; }
+    if (it + 1 > lp.max_iters) { sc->done = 3; return; }
+    const int64_t t = sc->adam_step + 1;
+    sc->adam_step = t;
+    sc->lr_t = (float)((double)lp.lr * sqrt(1.0 - pow((double)lp.beta2, (double)t)) /
+                       (1.0 - pow((double)lp.beta1, (double)t)));
+}
+
+void launch_loss(const LossParams& lp, const float* desc, const float* target, const double* pen, Scalars* sc,
+                 float* loss_out, float* history, cudaStream_t s) {
+    loss_kernel<<<1, 1024, 0, s>>>(lp, desc, target, pen, sc, loss_out, history);
+}
+
+// --------------------------------------------------------------------- gradient + Adam
+
+// g(y) = sum_l 2^{-d(l-1)} sum_chunks part_l[chunk][ancestor_l(y)]  (+ penalty gradient),
+// then either written out, or used for one Adam step (Keras form) on the field.
+__global__ void final_kernel(FinalArgs a, const int* __restrict__ done) {
+    if (done != nullptr && *done) return;
+    const int64_t N1 = a.n1[0] * a.n1[1] * a.n1[2];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N1) return;
+    const int64_t x = i % a.n1[2], y = (i / a.n1[2]) % a.n1[1], z = i / (a.n1[1] * a.n1[2]);
+    float g = 0.f;
+    float scale = 1.f;
+    const float step = a.ndim == 2 ? 0.25f : 0.125f;
+    for (int l = 0; l < a.levels; ++l) {
+        const int64_t lz = a.ndim == 2 ? 0 : (z >> l);
+        const int64_t li = (lz * a.nl[l][1] + (y >> l)) * a.nl[l][2] + (x >> l);
+        float s = 0.f;
+        const float* p = a.parts[l] + li;
+        for (int c = 0; c < a.nChunks[l]; ++c) s += p[(int64_t)c * a.Nl[l]];
+        g = fmaf(scale, s, g);
+        scale *= step;
+    }
+    if (a.sc != nullptr && a.field != nullptr) {
+        const float M = a.field[i];
+        const float ex = box_excess(M);
+        const float dex = M > 1.f ? 1.f : (M < 0.f ? -1.f : 0.f);
+        g = fmaf(a.sc->pen_coef * ex, dex, g);
+    }
+    if (a.grad_out != nullptr) a.grad_out[i] = g;
+    if (a.M != nullptr) {
+        const float m = fmaf(a.beta1, a.m[i], (1.f - a.beta1) * g);
+        const float v = fmaf(a.beta2, a.v[i], (1.f - a.beta2) * g * g);
+        a.m[i] = m;
+        a.v[i] = v;
+        a.M[i] = a.M[i] - a.sc->lr_t * m / (sqrtf(v) + a.eps);
+    }
+}
+
+void launch_final(const FinalArgs& a, const int* done, cudaStream_t s) {
+    const int64_t N1 = a.n1[0] * a.n1[1] * a.n1[2];
+    const int th = 256;
+    final_kernel<<<(unsigned)((N1 + th - 1) / th), th, 0, s>>>(a, done);
+}
+
+// --------------------------------------------------------------------- start field
+
+// SplitMix64 (Steele, Lea & Flood 2014): state seed + (i+1) * golden gamma, then the
+// published three-step mix; value = top 24 bits * 2^-24.
+__global__ void init_uniform_kernel(float* __restrict__ f, int64_t count, uint64_t seed) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    f[i] = (float)(z >> 40) * (1.0f / 16777216.0f);
+}
+
+void launch_init_uniform(float* field, int64_t count, uint64_t seed, cudaStream_t s) {
+    const int th = 256;
+    init_uniform_kernel<<<(unsigned)((count + th - 1) / th), th, 0, s>>>(field, count, seed);
+}
+
+}  // namespace dmcr

@@ -1,0 +1,532 @@
+// Direct correlation kernels of the soft-thresholded two-point descriptor and its adjoint
+// (sm_103a).  Paper: arXiv 2103.09686, Sec. 3.2.2-3.2.4 (convolve -> threshold ->
+// quadratic reduce) and the gradient of Sec. 3.1/3.3.
+//
+// Product form.  With kappa = (alpha/2) log2 e and cexp = 0.75 alpha log2 e, every pixel
+// is mapped once to E_y = 2^(-kappa M_y) (tip side) and E'_x = 2^(cexp - kappa M_x)
+// (tail side); a shifted pair then needs no exponential at all:
+//     P = E'_x E_y = exp(-alpha (a - 0.75)),  a = (M_x + M_y)/2,
+//     s = 1 / (1 + P) = sigma(alpha (a - 0.75)),   f(a) = c1 s + c3.
+// One FFMA and one MUFU reciprocal per pair.  The pair (x, x+0) gives a = M_x, so r = 0
+// needs no special case.  Blocks whose pixels leave |kappa M| <= lim take an exact slow
+// path (P = 2^(cexp - kappa M_x - kappa M_y) per pair), so arbitrary finite fields are
+// handled; the choice is block-uniform.
+//
+// Forward (half window).  A thread owns T = 8 consecutive rx shifts of one (rz, ry) and
+// walks the positions of its block's tile; per 8-position chunk it reads 8 tail values
+// (broadcast) and 16 tip values (4 x LDS.128) and evaluates 64 pairs.  Consecutive lanes
+// own consecutive ry, i.e. consecutive shared-memory rows whose stride is 4 mod 32 words,
+// so the LDS.128 reads are bank-conflict free.  Per-thread sums are hierarchical (row,
+// plane, block) in FP32, written per tile and reduced across tiles in FP64 in fixed order:
+// the result is deterministic.
+//
+// Adjoint (full window, gather form).  A thread owns 8 consecutive positions of one row;
+// lanes own consecutive rows.  For every shift of its block's chunk it accumulates
+//     g_y += G'(r) * h(a_y(r)),  h = f f' = c1 alpha s (1 - s) (c1 s + c3),
+// with G'(r) = dL/dS_bar(|r|) / N (2 dL/dS_bar(0) / N at r = 0), recomputing every pair
+// (the N x K ensemble is never stored).  No atomics; per-chunk partials are summed in a
+// fixed order by the final kernel.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace dmcr {
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ int64_t wrapi(int64_t i, int64_t n) {
+    int64_t m = i % n;
+    return m < 0 ? m + n : m;
+}
+
+__host__ __device__ inline int stride_4mod32(int cols) {
+    // smallest s >= cols with s % 32 == 4
+    int s = ((cols - 4 + 31) / 32) * 32 + 4;
+    return s < 4 ? 4 : s;
+}
+
+// Group gi of the half window -> (rz, ry, b); order: rz, then b, then ry fastest.
+__host__ __device__ inline void decode_group(const LevelGeom& g, int64_t gi, int& rz, int& ry, int& b) {
+    const int64_t n0 = (int64_t)(g.P[1] + 1) * g.NB;
+    if (gi < n0) {
+        rz = 0;
+        b = (int)(gi / (g.P[1] + 1));
+        ry = (int)(gi % (g.P[1] + 1));
+    } else {
+        const int64_t w = 2 * g.P[1] + 1;
+        const int64_t r = gi - n0;
+        const int64_t per = w * g.NB;
+        rz = 1 + (int)(r / per);
+        const int64_t rem = r % per;
+        b = (int)(rem / w);
+        ry = (int)(rem % w) - g.P[1];
+    }
+}
+
+// Canonical half-window index of (rz, ry, rx), -1 if (rz, ry, rx) is not in the half window.
+__host__ __device__ inline int64_t canon_index(const LevelGeom& g, int rz, int ry, int rx) {
+    const int Px = g.P[2], Py = g.P[1];
+    if (rx < -Px || rx > Px) return -1;
+    if (rz == 0 && ry == 0) return rx >= 0 ? rx : -1;
+    if (rz == 0) return ry > 0 ? (Px + 1) + (int64_t)(ry - 1) * (2 * Px + 1) + (rx + Px) : -1;
+    if (rz < 0) return -1;
+    return (Px + 1) + (int64_t)Py * (2 * Px + 1) +
+           ((int64_t)(rz - 1) * (2 * Py + 1) + (ry + Py)) * (2 * Px + 1) + (rx + Px);
+}
+
+// Block bounding box of the shift groups [gfirst, glast].
+struct GroupBox {
+    int rzA, rzB, rylo, ryhi, blo, bhi;
+};
+
+__host__ __device__ inline GroupBox group_box(const LevelGeom& g, int64_t gfirst, int64_t glast) {
+    int rzA, ryA, bA, rzB, ryB, bB;
+    decode_group(g, gfirst, rzA, ryA, bA);
+    decode_group(g, glast, rzB, ryB, bB);
+    GroupBox bx;
+    bx.rzA = rzA;
+    bx.rzB = rzB;
+    if (rzA == rzB && bA == bB) {
+        bx.rylo = ryA; bx.ryhi = ryB; bx.blo = bA; bx.bhi = bA;
+    } else if (rzA == rzB) {
+        bx.rylo = (rzA == 0) ? 0 : -g.P[1]; bx.ryhi = g.P[1]; bx.blo = bA; bx.bhi = bB;
+    } else {
+        bx.rylo = -g.P[1]; bx.ryhi = g.P[1]; bx.blo = 0; bx.bhi = g.NB - 1;
+    }
+    return bx;
+}
+
+struct FwdSmem {
+    int planesH, rowsH, colsH, strideH;
+};
+
+__host__ __device__ inline FwdSmem fwd_smem_shape(const LevelGeom& g, const GroupBox& bx) {
+    FwdSmem s;
+    s.planesH = bx.rzB - bx.rzA + 1;
+    s.rowsH = g.TY + bx.ryhi - bx.rylo;
+    s.colsH = T * (bx.bhi - bx.blo) + TX + T;
+    s.strideH = stride_4mod32(s.colsH);
+    return s;
+}
+
+// ------------------------------------------------------------------------- pair math
+
+enum { MODE_FAST = 0, MODE_SLOW = 1, MODE_IDENT = 2 };
+
+// 64 pairs of one chunk: tails x[0..8), tips y[0..16); pair (k, m) uses y[k+m].
+template <int MODE>
+__device__ __forceinline__ void fwd_chunk(const float (&x)[T], const float (&y)[2 * T], float (&r1)[T],
+                                          float (&r2)[T]) {
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+#pragma unroll
+        for (int m = 0; m < T; ++m) {
+            if (MODE == MODE_IDENT) {
+                const float a = x[k] + y[k + m];
+                r2[m] = fmaf(a, a, r2[m]);
+            } else {
+                float d;
+                if (MODE == MODE_FAST) d = fmaf(x[k], y[k + m], 1.0f);
+                else d = ex2_approx(x[k] - y[k + m]) + 1.0f;
+                const float s = rcp_approx(d);
+                r1[m] += s;
+                r2[m] = fmaf(s, s, r2[m]);
+            }
+        }
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void adj_chunk(const float (&x)[T], const float (&y)[2 * T], const float (&G)[T],
+                                          float (&acc)[T], float c1, float c1mc3, float c3) {
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+#pragma unroll
+        for (int m = 0; m < T; ++m) {
+            if (MODE == MODE_IDENT) {
+                acc[k] = fmaf(G[m], x[k] + y[k + m], acc[k]);
+            } else {
+                float d;
+                if (MODE == MODE_FAST) d = fmaf(x[k], y[k + m], 1.0f);
+                else d = ex2_approx(x[k] - y[k + m]) + 1.0f;
+                const float s = rcp_approx(d);
+                // H(s) = s (1 - s) (c1 s + c3) = s (c3 + s ((c1 - c3) - c1 s))
+                const float q = fmaf(-c1, s, c1mc3);
+                const float q2 = fmaf(s, q, c3);
+                acc[k] = fmaf(G[m] * s, q2, acc[k]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void load8(const float* p, float (&v)[T]) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    const float4 b = *reinterpret_cast<const float4*>(p + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+__device__ __forceinline__ void load16(const float* p, float (&v)[2 * T]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 a = *reinterpret_cast<const float4*>(p + 4 * i);
+        v[4 * i + 0] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = a.z; v[4 * i + 3] = a.w;
+    }
+}
+
+// ------------------------------------------------------------------------- forward
+
+template <int MODE>
+__device__ __forceinline__ void fwd_plane(const float* xs, const float* ybase, int strideH, int rowsValid,
+                                          int chunksValid, float (&p1)[T], float (&p2)[T]) {
+    for (int iy = 0; iy < rowsValid; ++iy) {
+        float r1[T], r2[T];
+#pragma unroll
+        for (int m = 0; m < T; ++m) { r1[m] = 0.f; r2[m] = 0.f; }
+        const float* xrow = xs + iy * TX;
+        const float* yrow = ybase + iy * strideH;
+#pragma unroll 1
+        for (int c = 0; c < chunksValid; ++c) {
+            float x[T], y[2 * T];
+            load8(xrow + c * T, x);
+            load16(yrow + c * T, y);
+            fwd_chunk<MODE>(x, y, r1, r2);
+        }
+#pragma unroll
+        for (int m = 0; m < T; ++m) { p1[m] += r1[m]; p2[m] += r2[m]; }
+    }
+}
+
+template <bool IDENT>
+__global__ void __launch_bounds__(FWD_THREADS)
+corr_fwd_kernel(const float* __restrict__ field, LevelGeom g, ThreshConst tc, float* __restrict__ partial,
+                const int* __restrict__ done) {
+    if (done != nullptr && *done) return;
+    extern __shared__ __align__(16) float smem[];
+    const int tid = threadIdx.x;
+    const int64_t ts = blockIdx.x;
+    const int tx = (int)(ts % g.tilesX);
+    const int ty = (int)((ts / g.tilesX) % g.tilesY);
+    const int pc = (int)(ts / ((int64_t)g.tilesX * g.tilesY));
+    const int64_t x0 = (int64_t)tx * TX, y0 = (int64_t)ty * g.TY;
+    const int64_t z0 = (int64_t)pc * g.PPB;
+    const int64_t z1 = min(z0 + (int64_t)g.PPB, g.n[0]);
+    const int64_t n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+
+    const int64_t gfirst = (int64_t)blockIdx.y * FWD_THREADS;
+    const int64_t glast = min(gfirst + FWD_THREADS, g.NG) - 1;
+    const GroupBox bx = group_box(g, gfirst, glast);
+    const FwdSmem sh = fwd_smem_shape(g, bx);
+
+    float* xs = smem;                       // TY x TX tails
+    float* ys = smem + g.TY * TX;           // planesH x rowsH x strideH tips
+
+    const int64_t gi = gfirst + tid;
+    const bool gvalid = gi < g.NG;
+    int rz = bx.rzA, ry = bx.rylo, b = bx.blo;
+    if (gvalid) decode_group(g, gi, rz, ry, b);
+    const float* ybase = ys + ((int64_t)(rz - bx.rzA) * sh.rowsH + (ry - bx.rylo)) * sh.strideH + T * (b - bx.blo);
+
+    const int rowsValid = (int)min((int64_t)g.TY, n1 - y0);
+    const int colsValid = (int)min((int64_t)TX, n2 - x0);
+    const int chunksValid = (colsValid + T - 1) / T;
+
+    float t1[T], t2[T];
+#pragma unroll
+    for (int m = 0; m < T; ++m) { t1[m] = 0.f; t2[m] = 0.f; }
+
+    const int nx = g.TY * TX;
+    const int ny = sh.planesH * sh.rowsH * sh.colsH;
+    const int64_t hx0 = x0 - g.P[2] + (int64_t)T * bx.blo;
+
+    for (int64_t z = z0; z < z1; ++z) {
+        __syncthreads();
+        bool bad = false;
+        for (int i = tid; i < nx; i += FWD_THREADS) {
+            const int iy = i / TX, ix = i % TX;
+            const bool valid = (y0 + iy < n1) && (x0 + ix < n2);
+            const float v = valid ? field[(z * n1 + y0 + iy) * n2 + x0 + ix] : 0.f;
+            xs[i] = v;
+            bad |= !(fabsf(tc.kappa * v) <= tc.lim) && valid && !isnan(v);
+        }
+        for (int i = tid; i < ny; i += FWD_THREADS) {
+            const int c = i % sh.colsH;
+            const int r = (i / sh.colsH) % sh.rowsH;
+            const int p = i / (sh.colsH * sh.rowsH);
+            const int64_t gz = wrapi(z + bx.rzA + p, n0);
+            const int64_t gy = wrapi(y0 + bx.rylo + r, n1);
+            const int64_t gx = wrapi(hx0 + c, n2);
+            const float v = field[(gz * n1 + gy) * n2 + gx];
+            ys[((int64_t)p * sh.rowsH + r) * sh.strideH + c] = v;
+            bad |= !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
+        }
+        const int slow = __syncthreads_or(bad);
+        // transform in place: each thread rewrites the elements it loaded
+        for (int i = tid; i < nx; i += FWD_THREADS) {
+            const int iy = i / TX, ix = i % TX;
+            const bool valid = (y0 + iy < n1) && (x0 + ix < n2);
+            const float v = xs[i];
+            float o;
+            if (IDENT) o = valid ? 0.5f * v : 0.f;
+            else if (!valid) o = __int_as_float(0x7f800000);            // +inf: s = 0
+            else o = slow ? fmaf(-tc.kappa, v, tc.cexp) : ex2_approx(fmaf(-tc.kappa, v, tc.cexp));
+            xs[i] = o;
+        }
+        for (int i = tid; i < ny; i += FWD_THREADS) {
+            const int c = i % sh.colsH;
+            const int r = (i / sh.colsH) % sh.rowsH;
+            const int p = i / (sh.colsH * sh.rowsH);
+            float* q = ys + ((int64_t)p * sh.rowsH + r) * sh.strideH + c;
+            const float v = *q;
+            float o;
+            if (IDENT) o = 0.5f * v;
+            else o = slow ? tc.kappa * v : ex2_approx(-tc.kappa * v);
+            *q = o;
+        }
+        __syncthreads();
+        float p1[T], p2[T];
+#pragma unroll
+        for (int m = 0; m < T; ++m) { p1[m] = 0.f; p2[m] = 0.f; }
+        if (IDENT) fwd_plane<MODE_IDENT>(xs, ybase, sh.strideH, rowsValid, chunksValid, p1, p2);
+        else if (slow) fwd_plane<MODE_SLOW>(xs, ybase, sh.strideH, rowsValid, chunksValid, p1, p2);
+        else fwd_plane<MODE_FAST>(xs, ybase, sh.strideH, rowsValid, chunksValid, p1, p2);
+#pragma unroll
+        for (int m = 0; m < T; ++m) { t1[m] += p1[m]; t2[m] += p2[m]; }
+    }
+
+    if (!gvalid) return;
+    // sum_x f^2 = c1^2 sum s^2 + 2 c1 c3 sum s + n c3^2 (identity: sum a^2 directly)
+    const float nvalid = (float)((z1 - z0) * (int64_t)rowsValid * colsValid);
+    float* out = partial + ts * g.Khalf;
+#pragma unroll
+    for (int m = 0; m < T; ++m) {
+        const int rx = -g.P[2] + T * b + m;
+        const int64_t k = canon_index(g, rz, ry, rx);
+        if (k < 0) continue;
+        float v;
+        if (IDENT) v = t2[m];
+        else v = fmaf(tc.c1 * tc.c1, t2[m], fmaf(2.f * tc.c1 * tc.c3, t1[m], nvalid * tc.c3 * tc.c3));
+        out[k] = v;
+    }
+}
+
+// Fixed-order FP64 sum over tiles, scaled by w_l / N_l.
+__global__ void fwd_reduce_kernel(LevelGeom g, const float* __restrict__ partial, float weight,
+                                  float* __restrict__ desc, const int* __restrict__ done) {
+    if (done != nullptr && *done) return;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.Khalf) return;
+    double s = 0.0;
+    for (int64_t t = 0; t < g.fwdTiles; ++t) s += (double)partial[t * g.Khalf + k];
+    desc[k] = (float)((double)weight * s / (double)g.N);
+}
+
+// ------------------------------------------------------------------------- adjoint
+
+template <int MODE>
+__device__ __forceinline__ void adj_rows(const float* ys, const float* Gs, int strideH, int WB, int NB, int ryN,
+                                         int lane, int strip, const float (&x)[T], float (&acc)[T], float c1,
+                                         float c1mc3, float c3) {
+    for (int r = 0; r < ryN; ++r) {
+        const float* yrow = ys + (lane + r) * strideH + T * strip;
+        const float* grow = Gs + r * WB;
+#pragma unroll 1
+        for (int bb = 0; bb < NB; ++bb) {
+            float y[2 * T], G[T];
+            load16(yrow + T * bb, y);
+            load8(grow + T * bb, G);
+            adj_chunk<MODE>(x, y, G, acc, c1, c1mc3, c3);
+        }
+    }
+}
+
+template <bool IDENT>
+__global__ void __launch_bounds__(ADJ_THREADS)
+corr_adj_kernel(const float* __restrict__ field, LevelGeom g, ThreshConst tc, const float* __restrict__ Gd,
+                float* __restrict__ part, const int* __restrict__ done) {
+    if (done != nullptr && *done) return;
+    extern __shared__ __align__(16) float smem[];
+    const int lane = threadIdx.x & 31, strip = threadIdx.x >> 5;
+    const int64_t tile = blockIdx.x;
+    const int tx = (int)(tile % g.adjTilesX);
+    const int ty = (int)((tile / g.adjTilesX) % g.adjTilesY);
+    const int64_t z = tile / ((int64_t)g.adjTilesX * g.adjTilesY);
+    const int64_t x0 = (int64_t)tx * TX, y0 = (int64_t)ty * 32;
+    const int64_t n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    const int chunk = blockIdx.y;
+    const int zc = chunk / g.nYc, yc = chunk % g.nYc;
+    const int rzA = -g.P[0] + zc * g.RZ;
+    const int rzB = min(rzA + g.RZ, g.P[0] + 1);
+    const int ryA = -g.P[1] + yc * g.RY;
+    const int ryB = min(ryA + g.RY, g.P[1] + 1);
+    const int ryN = ryB - ryA;
+    const int WB = g.NB * T;
+    const int rowsH = 32 + ryN - 1;
+    const int colsH = WB + 3 * T + 2 * T;   // 8 NB + 32 (see strip/bb read extents)
+    const int strideH = stride_4mod32(colsH);
+    float* ys = smem;
+    float* Gs = smem + rowsH * strideH;
+    const int64_t hx0 = x0 - g.P[2];
+
+    // own positions: row y0 + lane, columns x0 + 8 strip + k
+    const int64_t py = y0 + lane;
+    float mx[T];
+    bool xbad = false;
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        const int64_t px = x0 + T * strip + k;
+        const bool valid = py < n1 && px < n2;
+        mx[k] = valid ? field[(z * n1 + py) * n2 + px] : 0.f;
+        xbad |= !(fabsf(tc.kappa * mx[k]) <= tc.lim) && !isnan(mx[k]);
+    }
+    float acc[T];
+#pragma unroll
+    for (int k = 0; k < T; ++k) acc[k] = 0.f;
+    const float c1 = tc.c1, c3 = tc.c3, c1mc3 = tc.c1 - tc.c3;
+
+    const int ny = rowsH * colsH;
+    const int ng = ryN * WB;
+    for (int rz = rzA; rz < rzB; ++rz) {
+        __syncthreads();
+        const int64_t gz = wrapi(z + rz, n0);
+        bool bad = xbad;
+        for (int i = threadIdx.x; i < ny; i += ADJ_THREADS) {
+            const int c = i % colsH, r = i / colsH;
+            const int64_t gy = wrapi(y0 + ryA + r, n1);
+            const int64_t gx = wrapi(hx0 + c, n2);
+            const float v = field[(gz * n1 + gy) * n2 + gx];
+            ys[r * strideH + c] = v;
+            bad |= !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
+        }
+        const float* grow0 = Gd + ((int64_t)(rz + g.P[0]) * (2 * g.P[1] + 1) + (ryA + g.P[1])) * WB;
+        for (int i = threadIdx.x; i < ng; i += ADJ_THREADS) Gs[i] = grow0[i];
+        const int slow = __syncthreads_or(bad);
+        for (int i = threadIdx.x; i < ny; i += ADJ_THREADS) {
+            const int c = i % colsH, r = i / colsH;
+            float* q = ys + r * strideH + c;
+            const float v = *q;
+            *q = IDENT ? 0.5f * v : (slow ? tc.kappa * v : ex2_approx(-tc.kappa * v));
+        }
+        float x[T];
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            const float u = fmaf(-tc.kappa, mx[k], tc.cexp);
+            x[k] = IDENT ? 0.5f * mx[k] : (slow ? u : ex2_approx(u));
+        }
+        __syncthreads();
+        if (IDENT) adj_rows<MODE_IDENT>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc, c1, c1mc3, c3);
+        else if (slow) adj_rows<MODE_SLOW>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc, c1, c1mc3, c3);
+        else adj_rows<MODE_FAST>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc, c1, c1mc3, c3);
+    }
+
+    if (py >= n1) return;
+    float* out = part + (int64_t)chunk * g.N + (z * n1 + py) * n2;
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        const int64_t px = x0 + T * strip + k;
+        if (px < n2) out[px] = acc[k];
+    }
+}
+
+// Dense full-window coefficient grid of one level:
+//   Gd[rz][ry][col], rx = col - P2 (zero where rx > P2),
+//   value = scale * (src[k] - sub[k]) * (2 if r = 0),  k = canonical index of +-r,
+//   scale = weight * (gscale from the loss, or 1) * (c1 alpha / N_l, or 1 / N_l for f(x)=x).
+__global__ void gcoef_kernel(LevelGeom g, const float* __restrict__ src, const float* __restrict__ sub,
+                             const Scalars* __restrict__ sc, float scale, float* __restrict__ Gd,
+                             const int* __restrict__ done) {
+    if (done != nullptr && *done) return;
+    const int WB = g.NB * T;
+    const int64_t total = (int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * WB;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int col = (int)(i % WB);
+    const int ryi = (int)((i / WB) % (2 * g.P[1] + 1));
+    const int rzi = (int)(i / ((int64_t)WB * (2 * g.P[1] + 1)));
+    const int rz = rzi - g.P[0], ry = ryi - g.P[1], rx = col - g.P[2];
+    float v = 0.f;
+    if (rx <= g.P[2]) {
+        int64_t k = canon_index(g, rz, ry, rx);
+        if (k < 0) k = canon_index(g, -rz, -ry, -rx);
+        float d = src[k] - (sub != nullptr ? sub[k] : 0.f);
+        float s = scale * (sc != nullptr ? sc->gscale : 1.f);
+        if (rz == 0 && ry == 0 && rx == 0) s *= 2.f;
+        v = s * d;
+    }
+    Gd[i] = v;
+}
+
+// ------------------------------------------------------------------------- launchers
+
+size_t fwd_smem_bytes(const LevelGeom& g) {
+    int maxFloats = 0;
+    for (int gb = 0; gb < g.fwdGroupBlocks; ++gb) {
+        const int64_t gfirst = (int64_t)gb * FWD_THREADS;
+        const int64_t glast = std::min<int64_t>(gfirst + FWD_THREADS, g.NG) - 1;
+        const GroupBox bx = group_box(g, gfirst, glast);
+        const FwdSmem sh = fwd_smem_shape(g, bx);
+        const int f = g.TY * TX + sh.planesH * sh.rowsH * sh.strideH;
+        if (f > maxFloats) maxFloats = f;
+    }
+    return (size_t)maxFloats * sizeof(float);
+}
+
+void launch_corr_fwd(const LevelGeom& g, const ThreshConst& tc, const float* field, float* partial,
+                     const int* done, cudaStream_t s) {
+    const size_t smem = fwd_smem_bytes(g);
+    dim3 grid((unsigned)g.fwdTiles, (unsigned)g.fwdGroupBlocks);
+    if (tc.identity) corr_fwd_kernel<true><<<grid, FWD_THREADS, smem, s>>>(field, g, tc, partial, done);
+    else corr_fwd_kernel<false><<<grid, FWD_THREADS, smem, s>>>(field, g, tc, partial, done);
+}
+
+void launch_fwd_reduce(const LevelGeom& g, const ThreshConst& tc, const float* partial, float weight,
+                       float* desc, const int* done, cudaStream_t s) {
+    (void)tc;
+    const int th = 256;
+    fwd_reduce_kernel<<<(unsigned)((g.Khalf + th - 1) / th), th, 0, s>>>(g, partial, weight, desc, done);
+}
+
+size_t adj_smem_bytes(const LevelGeom& g) {
+    const int WB = g.NB * T;
+    const int rowsH = 32 + g.RY - 1;
+    const int colsH = WB + 5 * T;
+    return (size_t)(rowsH * stride_4mod32(colsH) + g.RY * WB) * sizeof(float);
+}
+
+void launch_corr_adj(const LevelGeom& g, const ThreshConst& tc, const float* field, const float* Gd, float* part,
+                     const int* done, cudaStream_t s) {
+    const size_t smem = adj_smem_bytes(g);
+    dim3 grid((unsigned)g.adjTiles, (unsigned)g.nChunks);
+    if (tc.identity) corr_adj_kernel<true><<<grid, ADJ_THREADS, smem, s>>>(field, g, tc, Gd, part, done);
+    else corr_adj_kernel<false><<<grid, ADJ_THREADS, smem, s>>>(field, g, tc, Gd, part, done);
+}
+
+void set_kernel_attributes() {
+    const int bytes = MAX_DYN_SMEM;
+    cudaFuncSetAttribute(corr_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(corr_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(corr_adj_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(corr_adj_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+void launch_gcoef(const LevelGeom& g, const ThreshConst& tc, const float* src, const float* sub, const Scalars* sc,
+                  float weight, float* Gd, const int* done, cudaStream_t s) {
+    const int WB = g.NB * T;
+    const int64_t total = (int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * WB;
+    const float scale = tc.identity ? weight / (float)g.N
+                                    : (float)((double)weight * (double)tc.c1 * (double)tc.alpha / (double)g.N);
+    const int th = 256;
+    gcoef_kernel<<<(unsigned)((total + th - 1) / th), th, 0, s>>>(g, src, sub, sc, scale, Gd, done);
+}
+
+}  // namespace dmcr
