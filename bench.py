@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark: one reconstruction iteration of differentiable MCR (arXiv 2103.09686) on GB300.
+
+A step is one pass of the whole hot path through the C ABI (``dmcr_adam_step``): multigrid
+restriction, the soft-thresholded S2 descriptor of every level, loss with box penalty,
+adjoint coefficients, the fused adjoint of every level, gradient assembly through the
+levels, and one Adam update.  Default workload: a 512x512 two-phase target (thresholded
+Gaussian random field, correlation length 12 px, volume fraction 0.40, plus periodic
+non-overlapping discs of radius 6-20 px), shift window +-64, three simultaneous levels
+(512, 256, 128), FP32, starting from a seeded uniform[0,1) field.
+
+Metric: S2+adjoint voxel-shifts/s = sum_l N_l K_full,l per step / step time, K_full =
+prod_a (2 P_a + 1).  Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64
+CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "S2+adjoint voxel-shifts/s"
+UNIT = "voxel-shifts/s"
+MUFU_RCP_PER_CLK_PER_SM = 16      # MUFU.RCP throughput per SM per clock (measured, sm_103a)
+
+WORKLOADS = {
+    "grf512": dict(shape=(512, 512), window=(64, 64), levels=3,
+                   desc="2D 512x512 GRF(l=12,vf=0.40)+discs r6-20, window +-64, 3 levels (512,256,128), "
+                        "one Adam iteration per step"),
+    "grf128_3d": dict(shape=(128, 128, 128), window=(24, 24, 24), levels=2,
+                      desc="3D 128^3 GRF(l=6/6/12, vf=0.25), window +-24, 2 levels (128,64), one Adam iteration"),
+    "grf64": dict(shape=(64, 64), window=(16, 16), levels=1,
+                  desc="2D 64x64 GRF(l=4, vf=0.30), window +-16, 1 level, one Adam iteration"),
+}
+
+
+def make_target(name: str, seed_base: int) -> np.ndarray:
+    if name == "grf512":
+        return synthetic.target_large_2d(2000 + seed_base)
+    if name == "grf128_3d":
+        return synthetic.target_3d(128, 3000 + seed_base)
+    return synthetic.target_small_2d(1000 + seed_base)
+
+
+def units_per_step(shape, window, levels) -> int:
+    kfull = int(np.prod([2 * p + 1 for p in window]))
+    n = int(np.prod(shape))
+    return sum((n >> (len(shape) * l)) * kfull for l in range(levels))
+
+
+def level_sizes(shape, levels):
+    return [int(np.prod([s >> l for s in shape])) for l in range(levels)]
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+
+def oracle_sample(shape, window, levels, target, field, budget_s: float, seed: int = 0):
+    """Time the FP64 oracle on a bounded sample of one descriptor+gradient evaluation and
+    extrapolate to voxel-shifts/s: forward on s half-window shifts of the finest level
+    (N_1 pair evaluations each), VJP at q positions (2 K_half pair evaluations each)."""
+    import oracle
+    op = oracle.Params(ndim=len(shape), window=tuple(window), levels=levels)
+    H = oracle.half_window(len(shape), window)
+    K = H.shape[0]
+    rng = np.random.default_rng(seed)
+    M = np.asarray(field, dtype=np.float32).astype(np.float64)
+    G = rng.standard_normal(K)
+    N1 = M.size
+
+    def run(s, q):
+        idx = rng.choice(K, size=min(s, K), replace=False)
+        t0 = time.perf_counter()
+        oracle.sbar(M, H[idx])
+        t1 = time.perf_counter()
+        pos = rng.choice(N1, size=q, replace=False)
+        oracle.level_vjp(M, op, G, pos)
+        t2 = time.perf_counter()
+        return (t1 - t0) / len(idx), (t2 - t1) / q
+
+    tf, ta = run(8, 16)          # calibrate
+    s = max(8, int(0.5 * budget_s / max(tf, 1e-9)))
+    q = max(16, min(N1, int(0.5 * budget_s / max(ta, 1e-9))))
+    tf, ta = run(s, q)
+    sizes = level_sizes(shape, levels)
+    t_full = sum(K * tf * (n / N1) + n * ta for n in sizes)
+    units = units_per_step(shape, window, levels)
+    return units / t_full, "%d forward shifts (of %d) on the %s level and the gradient at %d positions (of %d); " \
+        "full step extrapolated over %d levels" % (s, K, "x".join(map(str, shape)), q, N1, levels)
+
+
+def cores_used() -> int:
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS", "")) or os.cpu_count()
+    except ValueError:
+        return os.cpu_count()
+
+
+# ----------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="grf512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=16.0, help="seconds of oracle work for cpu_baseline")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+    shape, window, levels = wl["shape"], wl["window"], wl["levels"]
+    units = units_per_step(shape, window, levels)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        target = make_target(args.workload, 0)
+        field = synthetic.uniform_field(shape, seed=1)
+        per_step = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+        vals = []
+        sample = ""
+        for i in range(args.warmup + args.steps):
+            v, sample = oracle_sample(shape, window, levels, target, field, per_step, seed=i)
+            if i >= args.warmup:
+                vals.append(v)
+        value = float(np.mean(vals))
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": units / value * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": wl["desc"]},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    import paper_2103_09686_gb300 as dm
+    dm.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # inputs: one independent instance per rank (weak scaling, no data-path collective)
+    target = make_target(args.workload, rank)
+    p = dm.Params(shape=shape, window=window, levels=levels)
+    opts = dm.ReconOpts(lr=1e-2)
+    ws = dm.workspace(p, dev)
+    t_dev = torch.tensor(target, dtype=torch.float32, device=dev)
+    d_des = dm.descriptor(t_dev, p, ws)
+    field0 = torch.tensor(synthetic.uniform_field(shape, seed=7 + rank), dtype=torch.float32, device=dev)
+    field = field0.clone()
+    m = torch.zeros_like(field)
+    v = torch.zeros_like(field)
+    loss = torch.empty(6, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > 129 MB L2
+    step = 0
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step = dm.dmcr_adam_step(p, opts, d_des, field, m, v, step, loss, ws)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs, L2 flushed before every step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    dm.dmcr_profile_reset()
+    dm.dmcr_profile_enable(True)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step = dm.dmcr_adam_step(p, opts, d_des, field, m, v, step, loss, ws)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    dm.dmcr_profile_enable(False)
+    prof = dm.dmcr_profile_read()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = units * args.steps * world / total_s
+    loss_h = loss.cpu().numpy().tolist()
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the region
+    h_field = torch.tensor(synthetic.uniform_field(shape, seed=7 + rank), dtype=torch.float32).pin_memory()
+    h_target = d_des.cpu().pin_memory()
+    h_loss = torch.empty(6, dtype=torch.float32).pin_memory()
+    e2e_steps = max(20, args.steps // 4)
+    d_field = torch.empty_like(field)
+    d_t = torch.empty_like(d_des)
+    m.zero_(); v.zero_()
+    estep = 0
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        d_field.copy_(h_field, non_blocking=True)
+        d_t.copy_(h_target, non_blocking=True)
+        estep = dm.dmcr_adam_step(p, opts, d_t, d_field, m, v, estep, loss, ws)
+        h_loss.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = units * e2e_steps * world / e2e_s
+    h2d = h_field.numel() * 4 + h_target.numel() * 4
+    d2h = h_loss.numel() * 4
+
+    # ---- roofline of the dominant kernel (largest summed duration in the timed region)
+    name, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    sizes = level_sizes(shape, levels)
+    kfull = int(np.prod([2 * q + 1 for q in window]))
+    khalf = (kfull + 1) // 2
+    lvl = int(name.split("[L")[1].rstrip("]")) - 1 if "[L" in name else 0
+    if name.startswith("corr_adj"):
+        pairs = sizes[lvl] * kfull
+    elif name.startswith("corr_fwd"):
+        pairs = sizes[lvl] * khalf
+    else:
+        pairs = None
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = sm_count * MUFU_RCP_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9      # Gpair/s
+    avg_ms = kms / max(kcnt, 1)
+    roofline = None
+    if pairs is not None:
+        achieved = pairs / (avg_ms / 1e3) / 1e9
+        roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_basis": "%d SMs x %d MUFU.RCP/clk x %.0f MHz (one reciprocal per pair)" %
+                                  (sm_count, MUFU_RCP_PER_CLK_PER_SM, max_mhz),
+                    "avg_launch_ms": avg_ms, "launches": kcnt}
+    launches = int(sum(c for _, c in prof.values()))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v_cpu, sample = oracle_sample(shape, window, levels, target, field0.cpu().numpy(), args.cpu_budget)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["desc"], "units_per_step": units,
+                           "l2": "flushed before every timed step (256 MB write)",
+                           "parallelism": "independent instance per GPU" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
+                "gpu_launches": launches, "clocks": clocks,
+                "kernels": {k: {"ms": round(t, 4), "launches": c} for k, (t, c) in sorted(prof.items())},
+                "final_loss": loss_h}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -189,6 +189,29 @@ dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* opts,
                              float* history, dmcr_recon_report* report, void* ws, size_t ws_bytes,
                              void* stream);
 
+/*
+ * dmcr_adam_step -- ONE iteration of the reconstruction loop (flow chart of Sec. 3):
+ *   the loss at the current field (written to loss_out, DMCR_OUT_COUNT floats, device, or
+ *   NULL), its exact gradient and one Adam step (Keras form, bias correction with step
+ *   state->step + 1).  Uses opts->lr, beta1, beta2, eps and opts->loss; ignores the
+ *   stopping fields.  Asynchronous on `stream`; state->step is incremented on return.
+ *   A non-finite loss leaves the field unchanged (check loss_out).
+ */
+dmcr_status dmcr_adam_step(const dmcr_params* p, const dmcr_recon_opts* opts, const float* target_desc,
+                           float* field, dmcr_adam_state* state, float* loss_out, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the launching stream (host side).
+ *   dmcr_profile_enable(1) starts recording every kernel the library launches outside a
+ *   graph capture; dmcr_profile_reset() clears the records; dmcr_profile_read(i, ...)
+ *   waits for the recorded events and returns the i-th kernel name, its summed duration
+ *   in milliseconds and its launch count (DMCR_EINVAL once i is past the last entry).
+ */
+dmcr_status dmcr_profile_enable(int on);
+dmcr_status dmcr_profile_reset(void);
+dmcr_status dmcr_profile_read(int index, char* name, int name_len, double* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,9 +89,15 @@ def load(build_if_missing: bool = False):
         lib.dmcr_init_uniform.argtypes = [c_void_p, c_int64, c_uint64, c_void_p]
         lib.dmcr_reconstruct.argtypes = [P(dmcr_params), P(dmcr_recon_opts), c_void_p, c_void_p, P(dmcr_adam_state),
                                          c_void_p, P(dmcr_recon_report), c_void_p, c_size_t, c_void_p]
+        lib.dmcr_adam_step.argtypes = [P(dmcr_params), P(dmcr_recon_opts), c_void_p, c_void_p, P(dmcr_adam_state),
+                                       c_void_p, c_void_p, c_size_t, c_void_p]
+        lib.dmcr_profile_enable.argtypes = [c_int]
+        lib.dmcr_profile_reset.argtypes = []
+        lib.dmcr_profile_read.argtypes = [c_int, ctypes.c_char_p, c_int, P(ctypes.c_double), P(c_int64)]
         for name in ("dmcr_descriptor_length", "dmcr_workspace_size", "dmcr_descriptor", "dmcr_loss_grad",
                      "dmcr_descriptor_vjp", "dmcr_restrict", "dmcr_prolongate", "dmcr_init_uniform",
-                     "dmcr_reconstruct"):
+                     "dmcr_reconstruct", "dmcr_adam_step", "dmcr_profile_enable", "dmcr_profile_reset",
+                     "dmcr_profile_read"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib
@@ -260,6 +266,38 @@ def dmcr_reconstruct(p: Params, opts: ReconOpts, target_desc, field, m, v, step:
     report = {"iterations": rep.iterations, "converged": bool(rep.converged), "status": rep.status}
     report.update({k: float(rep.loss[i]) for i, k in enumerate(OUT_NAMES)})
     return report, st.step
+
+
+def dmcr_adam_step(p: Params, opts: ReconOpts, target_desc, field, m, v, step: int, loss_out=None, ws=None,
+                   stream=None) -> int:
+    """One asynchronous iteration (loss, gradient, Adam step).  Returns the new step count."""
+    ws = workspace(p, field.device) if ws is None else ws
+    st = dmcr_adam_state(_ptr(m), _ptr(v), int(step))
+    _check(load().dmcr_adam_step(ctypes.byref(p.c()), ctypes.byref(opts.c()), _ptr(target_desc), _ptr(field),
+                                 ctypes.byref(st), _ptr(loss_out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return st.step
+
+
+def dmcr_profile_enable(on: bool = True):
+    _check(load().dmcr_profile_enable(int(bool(on))))
+
+
+def dmcr_profile_reset():
+    _check(load().dmcr_profile_reset())
+
+
+def dmcr_profile_read() -> dict:
+    """{kernel name: (total ms, launches)} of the launches recorded since the last reset."""
+    lib = load()
+    out = {}
+    i = 0
+    buf = ctypes.create_string_buffer(64)
+    ms = ctypes.c_double()
+    cnt = c_int64()
+    while lib.dmcr_profile_read(i, buf, 64, ctypes.byref(ms), ctypes.byref(cnt)) == DMCR_OK:
+        out[buf.value.decode()] = (ms.value, cnt.value)
+        i += 1
+    return out
 
 
 # ----------------------------------------------------------------------------- conveniences

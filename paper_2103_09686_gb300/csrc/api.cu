@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -31,6 +32,83 @@ dmcr_status cuda_check(cudaError_t e, const char* what) {
     if (e != cudaSuccess) return fail(DMCR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
     return DMCR_OK;
 }
+
+// ---------------------------------------------------------------- per-kernel event timing
+struct ProfPending {
+    std::string name;
+    cudaEvent_t a, b;
+};
+struct ProfState {
+    std::mutex mu;
+    bool on = false;
+    std::vector<ProfPending> pending;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<int64_t> count;
+};
+ProfState& prof() {
+    static ProfState p;
+    return p;
+}
+cudaEvent_t prof_event(ProfState& p) {
+    if (!p.pool.empty()) {
+        cudaEvent_t e = p.pool.back();
+        p.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+void prof_collect(ProfState& p) {
+    for (auto& r : p.pending) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        size_t i = 0;
+        while (i < p.names.size() && p.names[i] != r.name) ++i;
+        if (i == p.names.size()) { p.names.push_back(r.name); p.ms.push_back(0.0); p.count.push_back(0); }
+        p.ms[i] += ms;
+        p.count[i] += 1;
+        p.pool.push_back(r.a);
+        p.pool.push_back(r.b);
+    }
+    p.pending.clear();
+}
+// Records an event pair around the launches of its scope when profiling is on and the
+// stream is not being captured into a graph.
+class ProfScope {
+  public:
+    ProfScope(const char* name, int level, cudaStream_t s) : s_(s) {
+        ProfState& p = prof();
+        if (!p.on) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return;
+        }
+        std::lock_guard<std::mutex> lk(p.mu);
+        name_ = level >= 0 ? std::string(name) + "[L" + std::to_string(level + 1) + "]" : std::string(name);
+        a_ = prof_event(p);
+        b_ = prof_event(p);
+        cudaEventRecord(a_, s);
+        active_ = true;
+    }
+    ~ProfScope() {
+        if (!active_) return;
+        ProfState& p = prof();
+        std::lock_guard<std::mutex> lk(p.mu);
+        cudaEventRecord(b_, s_);
+        p.pending.push_back({name_, a_, b_});
+    }
+
+  private:
+    cudaStream_t s_;
+    bool active_ = false;
+    std::string name_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
 
 #define DMCR_TRY(expr)                         \
     do {                                       \
@@ -223,6 +301,7 @@ void pyramid(const Plan& pl, const Ws& w, const float* field, const float* lv[MA
         float* dst = reinterpret_cast<float*>(w.base + pl.o_pyr[l]);
         const LevelGeom& gf = pl.g[l - 1];
         int64_t nf[3] = {gf.n[0], gf.n[1], gf.n[2]};
+        ProfScope ps("restrict", l, s);
         launch_restrict(pl.ndim, nf, lv[l - 1], dst, done, s);
         lv[l] = dst;
     }
@@ -231,7 +310,11 @@ void pyramid(const Plan& pl, const Ws& w, const float* field, const float* lv[MA
 void forward(const Plan& pl, const Ws& w, const float* const lv[MAX_LEVELS], float* desc, const int* done,
              cudaStream_t s) {
     for (int l = 0; l < pl.levels; ++l) {
-        launch_corr_fwd(pl.g[l], pl.tc, lv[l], w.fwd(l), done, s);
+        {
+            ProfScope ps("corr_fwd", l, s);
+            launch_corr_fwd(pl.g[l], pl.tc, lv[l], w.fwd(l), done, s);
+        }
+        ProfScope ps("fwd_reduce", l, s);
         launch_fwd_reduce(pl.g[l], pl.tc, w.fwd(l), pl.w[l], desc + pl.off[l], done, s);
     }
 }
@@ -248,9 +331,15 @@ void backward(const Plan& pl, const Ws& w, const float* const lv[MAX_LEVELS], co
     for (int a = 0; a < 3; ++a) fa.n1[a] = pl.g[0].n[a];
     for (int l = 0; l < pl.levels; ++l) {
         const LevelGeom& g = pl.g[l];
-        launch_gcoef(g, pl.tc, src + pl.off[l], sub != nullptr ? sub + pl.off[l] : nullptr, gsc, pl.w[l], w.gd(l),
-                     done, s);
-        launch_corr_adj(g, pl.tc, lv[l], w.gd(l), w.adj(l), done, s);
+        {
+            ProfScope ps("gcoef", l, s);
+            launch_gcoef(g, pl.tc, src + pl.off[l], sub != nullptr ? sub + pl.off[l] : nullptr, gsc, pl.w[l],
+                         w.gd(l), done, s);
+        }
+        {
+            ProfScope ps("corr_adj", l, s);
+            launch_corr_adj(g, pl.tc, lv[l], w.gd(l), w.adj(l), done, s);
+        }
         fa.parts[l] = w.adj(l);
         fa.nChunks[l] = g.nChunks;
         fa.Nl[l] = g.N;
@@ -265,7 +354,18 @@ void backward(const Plan& pl, const Ws& w, const float* const lv[MAX_LEVELS], co
     fa.beta1 = b1;
     fa.beta2 = b2;
     fa.eps = eps;
+    ProfScope ps(M != nullptr ? "grad_adam" : "grad_assemble", -1, s);
     launch_final(fa, done, s);
+}
+
+void penalty_and_loss(const Plan& pl, const Ws& w, const LossParams& lp, const float* field, const float* desc,
+                      const float* target, float* loss_out, float* history, const int* done, cudaStream_t s) {
+    if (lp.bc_on) {
+        ProfScope ps("penalty", -1, s);
+        launch_penalty(field, pl.N1, w.pen(), done, s);
+    }
+    ProfScope ps("loss", -1, s);
+    launch_loss(lp, desc, target, lp.bc_on ? w.pen() : nullptr, w.scal(), loss_out, history, s);
 }
 
 LossParams make_lp(const Plan& pl, const dmcr_loss_opts* o) {
@@ -337,8 +437,7 @@ dmcr_status dmcr_loss_grad(const dmcr_params* p, const dmcr_loss_opts* opts, con
     const LossParams lp = make_lp(pl, opts);
     pyramid(pl, w, field, lv, nullptr, s);
     forward(pl, w, lv, desc, nullptr, s);
-    if (lp.bc_on) launch_penalty(field, pl.N1, w.pen(), nullptr, s);
-    launch_loss(lp, desc, target_desc, lp.bc_on ? w.pen() : nullptr, w.scal(), loss_out, nullptr, s);
+    penalty_and_loss(pl, w, lp, field, desc, target_desc, loss_out, nullptr, nullptr, s);
     if (grad != nullptr)
         backward(pl, w, lv, desc, target_desc, w.scal(), field, lp.bc_on ? w.scal() : nullptr, grad, nullptr, nullptr,
                  nullptr, 0.f, 0.f, 0.f, nullptr, s);
@@ -429,9 +528,6 @@ dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* o, con
     lp.beta2 = o->beta2;
     lp.max_iters = o->max_iters;
     lp.recon = 1;
-    Scalars init;
-    memset(&init, 0, sizeof(init));
-    init.adam_step = state->step;
     const float* lv[MAX_LEVELS];
 
     do {
@@ -440,14 +536,12 @@ dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* o, con
         if ((st = cuda_check(cudaEventRecord(ev, caller), "cudaEventRecord"))) break;
         if ((st = cuda_check(cudaStreamWaitEvent(s, ev, 0), "cudaStreamWaitEvent"))) break;
         if (o->init == DMCR_INIT_UNIFORM_SEEDED) launch_init_uniform(field, pl.N1, o->seed, s);
-        if ((st = cuda_check(cudaMemcpyAsync(dsc, &init, sizeof(init), cudaMemcpyHostToDevice, s), "scalars"))) break;
-        if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
+        launch_scalars_init(dsc, state->step, s);
         // one iteration, captured once
         if ((st = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "BeginCapture"))) break;
         pyramid(pl, w, field, lv, done, s);
         forward(pl, w, lv, w.desc(), done, s);
-        if (lp.bc_on) launch_penalty(field, pl.N1, w.pen(), done, s);
-        launch_loss(lp, w.desc(), target_desc, lp.bc_on ? w.pen() : nullptr, dsc, nullptr, history, s);
+        penalty_and_loss(pl, w, lp, field, w.desc(), target_desc, nullptr, history, done, s);
         backward(pl, w, lv, w.desc(), target_desc, dsc, field, lp.bc_on ? dsc : nullptr, nullptr, field, state->m,
                  state->v, o->beta1, o->beta2, o->eps, done, s);
         cudaError_t ce = cudaStreamEndCapture(s, &graph);
@@ -480,8 +574,7 @@ dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* o, con
         LossParams lq = make_lp(pl, &o->loss);
         pyramid(pl, w, field, lv, nullptr, s);
         forward(pl, w, lv, w.desc(), nullptr, s);
-        if (lq.bc_on) launch_penalty(field, pl.N1, w.pen(), nullptr, s);
-        launch_loss(lq, w.desc(), target_desc, lq.bc_on ? w.pen() : nullptr, dsc, nullptr, nullptr, s);
+        penalty_and_loss(pl, w, lq, field, w.desc(), target_desc, nullptr, nullptr, nullptr, s);
         if ((st = cuda_check(cudaMemcpyAsync(&hs, dsc, sizeof(hs), cudaMemcpyDeviceToHost, s), "scalars D2H"))) break;
         if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
         for (int i = 0; i < DMCR_OUT_COUNT; ++i) report->loss[i] = hs.loss[i];
@@ -496,6 +589,75 @@ dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* o, con
     if (ev) cudaEventDestroy(ev);
     report->status = st;
     return st;
+}
+
+dmcr_status dmcr_adam_step(const dmcr_params* p, const dmcr_recon_opts* o, const float* target_desc, float* field,
+                           dmcr_adam_state* state, float* loss_out, void* ws, size_t ws_bytes, void* stream) {
+    Plan pl;
+    DMCR_TRY(validate_and_plan(p, pl));
+    if (o == nullptr || target_desc == nullptr || field == nullptr || state == nullptr || state->m == nullptr ||
+        state->v == nullptr)
+        return fail(DMCR_EINVAL, "NULL argument");
+    if (o->loss.mode != DMCR_LOSS_NORM && o->loss.mode != DMCR_LOSS_SQUARED)
+        return fail(DMCR_EINVAL, "unknown loss mode %d", o->loss.mode);
+    DMCR_TRY(check_ws(pl, ws, ws_bytes));
+    DMCR_TRY(prepare_device());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Ws w{static_cast<char*>(ws), &pl};
+    Scalars* dsc = w.scal();
+    const int* done = &dsc->done;
+    LossParams lp = make_lp(pl, &o->loss);
+    lp.tol_rel = 0.f;
+    lp.check_every = 1;
+    lp.lr = o->lr;
+    lp.beta1 = o->beta1;
+    lp.beta2 = o->beta2;
+    lp.max_iters = 1;
+    lp.recon = 1;
+    const float* lv[MAX_LEVELS];
+    {
+        ProfScope ps("scalars_init", -1, s);
+        launch_scalars_init(dsc, state->step, s);
+    }
+    pyramid(pl, w, field, lv, nullptr, s);
+    forward(pl, w, lv, w.desc(), nullptr, s);
+    penalty_and_loss(pl, w, lp, field, w.desc(), target_desc, loss_out, nullptr, nullptr, s);
+    backward(pl, w, lv, w.desc(), target_desc, dsc, field, lp.bc_on ? dsc : nullptr, nullptr, field, state->m,
+             state->v, o->beta1, o->beta2, o->eps, done, s);
+    DMCR_TRY(cuda_check(cudaGetLastError(), "dmcr_adam_step launch"));
+    state->step += 1;
+    return DMCR_OK;
+}
+
+dmcr_status dmcr_profile_enable(int on) {
+    ProfState& p = prof();
+    std::lock_guard<std::mutex> lk(p.mu);
+    p.on = on != 0;
+    return DMCR_OK;
+}
+
+dmcr_status dmcr_profile_reset(void) {
+    ProfState& p = prof();
+    std::lock_guard<std::mutex> lk(p.mu);
+    prof_collect(p);
+    p.names.clear();
+    p.ms.clear();
+    p.count.clear();
+    return DMCR_OK;
+}
+
+dmcr_status dmcr_profile_read(int index, char* name, int name_len, double* total_ms, int64_t* launches) {
+    ProfState& p = prof();
+    std::lock_guard<std::mutex> lk(p.mu);
+    prof_collect(p);
+    if (index < 0 || index >= (int)p.names.size()) return fail(DMCR_EINVAL, "no profile entry %d", index);
+    if (name != nullptr && name_len > 0) {
+        strncpy(name, p.names[index].c_str(), (size_t)name_len - 1);
+        name[name_len - 1] = 0;
+    }
+    if (total_ms != nullptr) *total_ms = p.ms[index];
+    if (launches != nullptr) *launches = p.count[index];
+    return DMCR_OK;
 }
 
 }  // extern "C"

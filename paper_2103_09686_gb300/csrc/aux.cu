@@ -205,6 +205,20 @@ void launch_final(const FinalArgs& a, const int* done, cudaStream_t s) {
     final_kernel<<<(unsigned)((N1 + th - 1) / th), th, 0, s>>>(a, done);
 }
 
+__global__ void scalars_init_kernel(Scalars* sc, int64_t adam_step) {
+    for (int i = 0; i < 6; ++i) sc->loss[i] = 0.f;
+    sc->gscale = 0.f;
+    sc->pen_coef = 0.f;
+    sc->lr_t = 0.f;
+    sc->done = 0;
+    sc->iter = 0;
+    sc->adam_step = adam_step;
+}
+
+void launch_scalars_init(Scalars* sc, int64_t adam_step, cudaStream_t s) {
+    scalars_init_kernel<<<1, 1, 0, s>>>(sc, adam_step);
+}
+
 // --------------------------------------------------------------------- start field
 
 // SplitMix64 (Steele, Lea & Flood 2014): state seed + (i+1) * golden gamma, then the

@@ -104,6 +104,7 @@ struct FinalArgs {
 };
 void launch_final(const FinalArgs& a, const int* done, cudaStream_t s);
 void launch_init_uniform(float* field, int64_t count, uint64_t seed, cudaStream_t s);
+void launch_scalars_init(Scalars* sc, int64_t adam_step, cudaStream_t s);
 void set_kernel_attributes();
 size_t fwd_smem_bytes(const LevelGeom& g);
 size_t adj_smem_bytes(const LevelGeom& g);

@@ -66,8 +66,8 @@ def test_descriptor_parity(cuda_lib, shape, window, levels, kind):
     np.testing.assert_allclose(got, want, rtol=RTOL, atol=1e-9)
 
 
-@pytest.mark.parametrize("shape,window,levels", [((64, 64), (16, 16), 1), ((32, 40), (4, 6), 2),
-                                                 ((8, 16, 24), (2, 3, 3), 2)])
+@pytest.mark.parametrize("shape,window,levels", [((64, 64), (16, 16), 1), ((32, 48), (4, 6), 2),
+                                                 ((8, 16, 32), (2, 3, 3), 2)])
 def test_identity_threshold_parity(cuda_lib, shape, window, levels):
     dm = cuda_lib
     M = _field("relaxed", shape, 7)
