@@ -212,6 +212,26 @@ dmcr_status dmcr_profile_enable(int on);
 dmcr_status dmcr_profile_reset(void);
 dmcr_status dmcr_profile_read(int index, char* name, int name_len, double* total_ms, int64_t* launches);
 
+/*
+ * dmcr_descriptor_noalloc -- the same descriptor as dmcr_descriptor, for callers that
+ *   cannot allocate device memory (no cudaMalloc, no caching allocator) at the point of
+ *   the call: code running under a runtime that forbids allocation during execution, or
+ *   deployments that reserve all device memory up front.  The paper has no counterpart;
+ *   this is a deployment convenience of this library.
+ *   Scratch comes from one fixed device array of DMCR_NOALLOC_SCRATCH_BYTES (16 MiB) in
+ *   the library, held by every GPU that loads it until the process exits.  Problems whose
+ *   scratch (pyramid levels plus per-tile partial sums) exceeds it are rejected with
+ *   DMCR_ENOMEM and a message; use dmcr_descriptor with a workspace for those.
+ *   The call allocates nothing.  Its first call on a device looks up the array's device
+ *   address (cudaGetSymbolAddress) with that device current; make that first call before
+ *   any stream capture.  All calls share the one array and every call overwrites what the
+ *   previous one left there, so calls that can overlap on the GPU (different streams,
+ *   threads or graphs without ordering between them) race: serialise them.
+ *   field: N floats, desc: dmcr_descriptor_length floats (device).  Asynchronous on `stream`.
+ */
+#define DMCR_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+dmcr_status dmcr_descriptor_noalloc(const dmcr_params* p, const float* field, float* desc, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,13 +91,14 @@ def load(build_if_missing: bool = False):
                                          c_void_p, P(dmcr_recon_report), c_void_p, c_size_t, c_void_p]
         lib.dmcr_adam_step.argtypes = [P(dmcr_params), P(dmcr_recon_opts), c_void_p, c_void_p, P(dmcr_adam_state),
                                        c_void_p, c_void_p, c_size_t, c_void_p]
+        lib.dmcr_descriptor_noalloc.argtypes = [P(dmcr_params), c_void_p, c_void_p, c_void_p]
         lib.dmcr_profile_enable.argtypes = [c_int]
         lib.dmcr_profile_reset.argtypes = []
         lib.dmcr_profile_read.argtypes = [c_int, ctypes.c_char_p, c_int, P(ctypes.c_double), P(c_int64)]
         for name in ("dmcr_descriptor_length", "dmcr_workspace_size", "dmcr_descriptor", "dmcr_loss_grad",
                      "dmcr_descriptor_vjp", "dmcr_restrict", "dmcr_prolongate", "dmcr_init_uniform",
                      "dmcr_reconstruct", "dmcr_adam_step", "dmcr_profile_enable", "dmcr_profile_reset",
-                     "dmcr_profile_read"):
+                     "dmcr_profile_read", "dmcr_descriptor_noalloc"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib
@@ -276,6 +277,12 @@ def dmcr_adam_step(p: Params, opts: ReconOpts, target_desc, field, m, v, step: i
     _check(load().dmcr_adam_step(ctypes.byref(p.c()), ctypes.byref(opts.c()), _ptr(target_desc), _ptr(field),
                                  ctypes.byref(st), _ptr(loss_out), ws.data_ptr(), ws.numel(), _stream(stream)))
     return st.step
+
+
+def dmcr_descriptor_noalloc(p: Params, field, desc, stream=None):
+    """dmcr_descriptor without a workspace: scratch from the library's fixed device array."""
+    _check(load().dmcr_descriptor_noalloc(ctypes.byref(p.c()), _ptr(field), _ptr(desc), _stream(stream)))
+    return desc
 
 
 def dmcr_profile_enable(on: bool = True):

@@ -661,3 +661,67 @@ dmcr_status dmcr_profile_read(int index, char* name, int name_len, double* total
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------- allocation-free descriptor
+//
+// Some callers cannot allocate device memory while they run: code called from a host
+// callback or a real-time loop in which cudaMalloc (or any allocating library) is not
+// allowed, and deployments that reserve all device memory at start-up.  For them, dmcr_descriptor_noalloc evaluates the same descriptor as dmcr_descriptor with its
+// scratch memory taken from one file-scope device array of fixed size, DMCR_NOALLOC_SCRATCH_BYTES,
+// that every GPU loading this library holds until the process exits.
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[DMCR_NOALLOC_SCRATCH_BYTES];
+
+struct NoallocDev {
+    int dev;
+    void* ptr;
+};
+
+// Host-side lookup of the array's device address, once per device with that device current.
+dmcr_status noalloc_scratch(void** out) {
+    static std::mutex mu;
+    static std::vector<NoallocDev> table;
+    int dev = 0;
+    DMCR_TRY(cuda_check(cudaGetDevice(&dev), "cudaGetDevice"));
+    std::lock_guard<std::mutex> lk(mu);
+    for (const NoallocDev& d : table)
+        if (d.dev == dev) {
+            *out = d.ptr;
+            return DMCR_OK;
+        }
+    void* ptr = nullptr;
+    DMCR_TRY(cuda_check(cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)"));
+    table.push_back({dev, ptr});
+    *out = ptr;
+    return DMCR_OK;
+}
+
+}  // namespace
+
+extern "C" dmcr_status dmcr_descriptor_noalloc(const dmcr_params* p, const float* field, float* desc, void* stream) {
+    Plan pl;
+    DMCR_TRY(validate_and_plan(p, pl));
+    if (field == nullptr || desc == nullptr) return fail(DMCR_EINVAL, "field/desc is NULL");
+    // compact layout: pyramid levels 2.. and the forward partials of every level
+    Plan cp = pl;
+    size_t o = 0;
+    for (int l = 0; l < cp.levels; ++l) {
+        const LevelGeom& g = cp.g[l];
+        if (l > 0) { cp.o_pyr[l] = o; o = align_up(o + (size_t)g.N * sizeof(float)); }
+        cp.o_fwd[l] = o; o = align_up(o + (size_t)g.fwdTiles * g.Khalf * sizeof(float));
+    }
+    if (o > (size_t)DMCR_NOALLOC_SCRATCH_BYTES)
+        return fail(DMCR_ENOMEM, "dmcr_descriptor_noalloc needs %zu bytes of scratch, more than its fixed %zu bytes; "
+                    "use dmcr_descriptor with a caller workspace", o, (size_t)DMCR_NOALLOC_SCRATCH_BYTES);
+    void* scratch = nullptr;
+    DMCR_TRY(noalloc_scratch(&scratch));
+    DMCR_TRY(prepare_device());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Ws w{static_cast<char*>(scratch), &cp};
+    const float* lv[MAX_LEVELS];
+    // every scratch entry read below is written first in the same call: nothing to clear
+    pyramid(cp, w, field, lv, nullptr, s);
+    forward(cp, w, lv, desc, nullptr, s);
+    return cuda_check(cudaGetLastError(), "dmcr_descriptor_noalloc launch");
+}
