@@ -292,16 +292,16 @@ def main():
     h2d = h_field.numel() * 4 + h_target.numel() * 4
     d2h = h_loss.numel() * 4
 
-    # ---- roofline of the dominant kernel (largest summed duration in the timed region)
+    # ---- roofline of the dominant kernel (largest summed duration in the timed region);
+    # the correlation kernels are one fused launch over all levels
     name, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
     sizes = level_sizes(shape, levels)
     kfull = int(np.prod([2 * q + 1 for q in window]))
     khalf = (kfull + 1) // 2
-    lvl = int(name.split("[L")[1].rstrip("]")) - 1 if "[L" in name else 0
     if name.startswith("corr_adj"):
-        pairs = sizes[lvl] * kfull
+        pairs = sum(sizes) * kfull
     elif name.startswith("corr_fwd"):
-        pairs = sizes[lvl] * khalf
+        pairs = sum(sizes) * khalf
     else:
         pairs = None
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -313,9 +313,9 @@ def main():
         achieved = pairs / (avg_ms / 1e3) / 1e9
         roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
                     "frac": achieved / peak, "traffic": None,
-                    "peak_basis": "%d SMs x %d MUFU.RCP/clk x %.0f MHz (one reciprocal per pair)" %
+                    "peak_basis": "%d SMs x %d MUFU.RCP/clk x %.0f MHz (one reciprocal per pair), of measured" %
                                   (sm_count, MUFU_RCP_PER_CLK_PER_SM, max_mhz),
-                    "avg_launch_ms": avg_ms, "launches": kcnt}
+                    "pairs_per_launch": pairs, "avg_launch_ms": avg_ms, "launches": kcnt}
     launches = int(sum(c for _, c in prof.values()))
 
     cpu = None

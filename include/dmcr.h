@@ -182,7 +182,8 @@ dmcr_status dmcr_init_uniform(float* field, int64_t count, uint64_t seed, void* 
  *   field_inout: N floats, the start (DMCR_INIT_CALLER) and the result.
  *   state: Adam moments (device) and step count (host), updated for resume.
  *   history: max_iters * 3 floats (device: E, L, rel_err per iteration) or NULL.
- *   SYNCHRONOUS: returns after the run, with `report` (host) filled in.
+ *   SYNCHRONOUS: returns after the run, with `report` (host) filled in; report.loss is the
+ *   loss of the returned field.
  */
 dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* opts,
                              const float* target_desc, float* field_inout, dmcr_adam_state* state,
@@ -200,6 +201,39 @@ dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* opts,
 dmcr_status dmcr_adam_step(const dmcr_params* p, const dmcr_recon_opts* opts, const float* target_desc,
                            float* field, dmcr_adam_state* state, float* loss_out, void* ws, size_t ws_bytes,
                            void* stream);
+
+/*
+ * Batched calls: `count` independent instances of any sizes, windows and levels (they must
+ * share the threshold and alpha), evaluated by ONE fused launch per phase -- every
+ * (instance, level) is a segment of the same grid, heaviest blocks first.  Pointer
+ * arguments are HOST arrays of `count` device pointers; loss_out holds count x
+ * DMCR_OUT_COUNT floats (device).  Each instance gives exactly the result of the
+ * corresponding single-instance call (same tiles, same summation order).
+ * The workspace is dmcr_batch_workspace_size() bytes, 256-byte aligned.
+ */
+dmcr_status dmcr_batch_workspace_size(int count, const dmcr_params* params, size_t* bytes);
+dmcr_status dmcr_descriptor_batched(int count, const dmcr_params* params, const float* const* fields,
+                                    float* const* descs, void* ws, size_t ws_bytes, void* stream);
+dmcr_status dmcr_loss_grad_batched(int count, const dmcr_params* params, const dmcr_loss_opts* opts,
+                                   const float* const* fields, const float* const* targets, float* loss_out,
+                                   float* const* grads /* NULL: loss only */, void* ws, size_t ws_bytes,
+                                   void* stream);
+dmcr_status dmcr_descriptor_vjp_batched(int count, const dmcr_params* params, const float* const* fields,
+                                        const float* const* grad_descs, float* const* grad_fields, void* ws,
+                                        size_t ws_bytes, void* stream);
+/* One Adam iteration of every instance (one opts for all; states: host array of count). */
+dmcr_status dmcr_adam_step_batched(int count, const dmcr_params* params, const dmcr_recon_opts* opts,
+                                   const float* const* targets, float* const* fields, dmcr_adam_state* states,
+                                   float* loss_out, void* ws, size_t ws_bytes, void* stream);
+/*
+ * Graph-captured reconstruction of every instance (opts, states, reports: host arrays of
+ * count).  Instances stop independently on their own device flags (converged instances
+ * cost nothing in later launches); the call returns when all have stopped.  SYNCHRONOUS.
+ * report.loss is the loss of the returned field of that instance.
+ */
+dmcr_status dmcr_reconstruct_batched(int count, const dmcr_params* params, const dmcr_recon_opts* opts,
+                                     const float* const* targets, float* const* fields, dmcr_adam_state* states,
+                                     dmcr_recon_report* reports, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Per-kernel timing with CUDA events recorded on the launching stream (host side).

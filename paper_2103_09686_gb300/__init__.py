@@ -10,4 +10,6 @@ from ._lib import (  # noqa: F401
     dmcr_adam_step, dmcr_descriptor_length, dmcr_descriptor_noalloc, dmcr_descriptor_vjp,
     dmcr_profile_enable, dmcr_profile_read, dmcr_profile_reset, dmcr_init_uniform, dmcr_loss_grad, dmcr_prolongate,
     dmcr_reconstruct, dmcr_restrict, dmcr_version, dmcr_workspace_size, load, loss_grad, workspace,
+    batch_workspace, dmcr_adam_step_batched, dmcr_batch_workspace_size, dmcr_descriptor_batched,
+    dmcr_descriptor_vjp_batched, dmcr_loss_grad_batched, dmcr_reconstruct_batched,
 )

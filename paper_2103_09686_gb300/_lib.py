@@ -92,13 +92,26 @@ def load(build_if_missing: bool = False):
         lib.dmcr_adam_step.argtypes = [P(dmcr_params), P(dmcr_recon_opts), c_void_p, c_void_p, P(dmcr_adam_state),
                                        c_void_p, c_void_p, c_size_t, c_void_p]
         lib.dmcr_descriptor_noalloc.argtypes = [P(dmcr_params), c_void_p, c_void_p, c_void_p]
+        PP = P(c_void_p)
+        lib.dmcr_batch_workspace_size.argtypes = [c_int, P(dmcr_params), P(c_size_t)]
+        lib.dmcr_descriptor_batched.argtypes = [c_int, P(dmcr_params), PP, PP, c_void_p, c_size_t, c_void_p]
+        lib.dmcr_loss_grad_batched.argtypes = [c_int, P(dmcr_params), P(dmcr_loss_opts), PP, PP, c_void_p, PP,
+                                               c_void_p, c_size_t, c_void_p]
+        lib.dmcr_descriptor_vjp_batched.argtypes = [c_int, P(dmcr_params), PP, PP, PP, c_void_p, c_size_t, c_void_p]
+        lib.dmcr_adam_step_batched.argtypes = [c_int, P(dmcr_params), P(dmcr_recon_opts), PP, PP, P(dmcr_adam_state),
+                                               c_void_p, c_void_p, c_size_t, c_void_p]
+        lib.dmcr_reconstruct_batched.argtypes = [c_int, P(dmcr_params), P(dmcr_recon_opts), PP, PP,
+                                                 P(dmcr_adam_state), P(dmcr_recon_report), c_void_p, c_size_t,
+                                                 c_void_p]
         lib.dmcr_profile_enable.argtypes = [c_int]
         lib.dmcr_profile_reset.argtypes = []
         lib.dmcr_profile_read.argtypes = [c_int, ctypes.c_char_p, c_int, P(ctypes.c_double), P(c_int64)]
         for name in ("dmcr_descriptor_length", "dmcr_workspace_size", "dmcr_descriptor", "dmcr_loss_grad",
                      "dmcr_descriptor_vjp", "dmcr_restrict", "dmcr_prolongate", "dmcr_init_uniform",
                      "dmcr_reconstruct", "dmcr_adam_step", "dmcr_profile_enable", "dmcr_profile_reset",
-                     "dmcr_profile_read", "dmcr_descriptor_noalloc"):
+                     "dmcr_profile_read", "dmcr_descriptor_noalloc", "dmcr_batch_workspace_size",
+                     "dmcr_descriptor_batched", "dmcr_loss_grad_batched", "dmcr_descriptor_vjp_batched",
+                     "dmcr_adam_step_batched", "dmcr_reconstruct_batched"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib
@@ -283,6 +296,91 @@ def dmcr_descriptor_noalloc(p: Params, field, desc, stream=None):
     """dmcr_descriptor without a workspace: scratch from the library's fixed device array."""
     _check(load().dmcr_descriptor_noalloc(ctypes.byref(p.c()), _ptr(field), _ptr(desc), _stream(stream)))
     return desc
+
+
+# ----------------------------------------------------------------------------- batched calls
+
+def _params_array(params):
+    arr = (dmcr_params * len(params))()
+    for i, p in enumerate(params):
+        arr[i] = p.c()
+    return arr
+
+
+def _ptr_array(tensors, allow_none=False):
+    if tensors is None:
+        return None
+    return (c_void_p * len(tensors))(*[(_ptr(t) if t is not None else None) for t in tensors])
+
+
+def dmcr_batch_workspace_size(params) -> int:
+    out = c_size_t()
+    _check(load().dmcr_batch_workspace_size(len(params), _params_array(params), ctypes.byref(out)))
+    return out.value
+
+
+def batch_workspace(params, device=None) -> torch.Tensor:
+    return torch.empty(max(dmcr_batch_workspace_size(params), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def dmcr_descriptor_batched(params, fields, descs, ws=None, stream=None):
+    ws = batch_workspace(params, fields[0].device) if ws is None else ws
+    _check(load().dmcr_descriptor_batched(len(params), _params_array(params), _ptr_array(fields), _ptr_array(descs),
+                                          ws.data_ptr(), ws.numel(), _stream(stream)))
+    return descs
+
+
+def dmcr_loss_grad_batched(params, opts: LossOpts, fields, targets, loss_out, grads=None, ws=None, stream=None):
+    ws = batch_workspace(params, fields[0].device) if ws is None else ws
+    _check(load().dmcr_loss_grad_batched(len(params), _params_array(params), ctypes.byref(opts.c()),
+                                         _ptr_array(fields), _ptr_array(targets), _ptr(loss_out), _ptr_array(grads),
+                                         ws.data_ptr(), ws.numel(), _stream(stream)))
+
+
+def dmcr_descriptor_vjp_batched(params, fields, grad_descs, grad_fields, ws=None, stream=None):
+    ws = batch_workspace(params, fields[0].device) if ws is None else ws
+    _check(load().dmcr_descriptor_vjp_batched(len(params), _params_array(params), _ptr_array(fields),
+                                              _ptr_array(grad_descs), _ptr_array(grad_fields), ws.data_ptr(),
+                                              ws.numel(), _stream(stream)))
+    return grad_fields
+
+
+def dmcr_adam_step_batched(params, opts: ReconOpts, targets, fields, ms, vs, steps, loss_out=None, ws=None,
+                           stream=None):
+    """One Adam iteration of every instance; returns the new step counts."""
+    ws = batch_workspace(params, fields[0].device) if ws is None else ws
+    n = len(params)
+    st = (dmcr_adam_state * n)()
+    for i in range(n):
+        st[i] = dmcr_adam_state(_ptr(ms[i]), _ptr(vs[i]), int(steps[i]))
+    _check(load().dmcr_adam_step_batched(n, _params_array(params), ctypes.byref(opts.c()), _ptr_array(targets),
+                                         _ptr_array(fields), st, _ptr(loss_out), ws.data_ptr(), ws.numel(),
+                                         _stream(stream)))
+    return [st[i].step for i in range(n)]
+
+
+def dmcr_reconstruct_batched(params, opts, targets, fields, ms, vs, steps, ws=None, stream=None):
+    """Graph-captured reconstruction of every instance (synchronous).  ``opts`` is one
+    ReconOpts or a list.  Returns (list of report dicts, list of new step counts)."""
+    ws = batch_workspace(params, fields[0].device) if ws is None else ws
+    n = len(params)
+    if isinstance(opts, ReconOpts):
+        opts = [opts] * n
+    oa = (dmcr_recon_opts * n)()
+    st = (dmcr_adam_state * n)()
+    for i in range(n):
+        oa[i] = opts[i].c()
+        st[i] = dmcr_adam_state(_ptr(ms[i]), _ptr(vs[i]), int(steps[i]))
+    reps = (dmcr_recon_report * n)()
+    status = load().dmcr_reconstruct_batched(n, _params_array(params), oa, _ptr_array(targets), _ptr_array(fields),
+                                             st, reps, ws.data_ptr(), ws.numel(), _stream(stream))
+    _check(status)
+    out = []
+    for i in range(n):
+        r = {"iterations": reps[i].iterations, "converged": bool(reps[i].converged), "status": reps[i].status}
+        r.update({k: float(reps[i].loss[j]) for j, k in enumerate(OUT_NAMES)})
+        out.append(r)
+    return out, [st[i].step for i in range(n)]
 
 
 def dmcr_profile_enable(on: bool = True):

@@ -131,10 +131,17 @@ struct Plan {
     int64_t N1 = 0;
     ThreshConst tc;
     // workspace offsets (bytes)
-    size_t o_scal = 0, o_pen = 0, o_desc = 0, o_pyr[MAX_LEVELS] = {}, o_fwd[MAX_LEVELS] = {},
-           o_gd[MAX_LEVELS] = {}, o_adj[MAX_LEVELS] = {};
+    size_t o_tab = 0, tab_bytes = 0, o_scal = 0, o_pen = 0, o_desc = 0, o_pyr[MAX_LEVELS] = {},
+           o_fwd[MAX_LEVELS] = {}, o_gd[MAX_LEVELS] = {}, o_adj[MAX_LEVELS] = {};
     size_t bytes = 0;
 };
+
+// Upper bound of the segment-table bytes of one instance (every phase, 16-B aligned arrays).
+size_t table_bound(int levels) {
+    return (size_t)levels * (sizeof(FwdSeg) + sizeof(RedSeg) + sizeof(GSeg) + sizeof(AdjSeg) + sizeof(RestrictSeg)) +
+           sizeof(PenSeg) + sizeof(LossSeg) + sizeof(FinalSeg) + sizeof(InitSeg);
+}
+size_t table_slack() { return (size_t)(16 + MAX_LEVELS) * 16 + 256; }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -242,10 +249,14 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         tc.alpha = (float)a;
         tc.kappa = (float)(0.5 * a * log2e);
         tc.cexp = (float)(0.75 * a * log2e);
-        tc.lim = (float)std::max(0.0, 100.0 - 0.75 * a * log2e);
+        // fast path: every pair factor d = 1 + E'_x E_y stays <= 2^62, so the product of two
+        // factors that share one reciprocal is finite
+        tc.lim = (float)std::max(0.0, 0.5 * (61.0 - 0.75 * a * log2e));
     }
     // workspace layout
     size_t o = 0;
+    pl.tab_bytes = align_up(table_bound(pl.levels) + table_slack());
+    pl.o_tab = o; o += pl.tab_bytes;
     pl.o_scal = o; o = align_up(o + sizeof(Scalars));
     pl.o_pen = o; o = align_up(o + NPEN_BLOCKS * sizeof(double));
     pl.o_desc = o; o = align_up(o + (size_t)pl.Ktot * sizeof(float));
@@ -253,7 +264,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         const LevelGeom& g = pl.g[l];
         if (l > 0) { pl.o_pyr[l] = o; o = align_up(o + (size_t)g.N * sizeof(float)); }
         pl.o_fwd[l] = o; o = align_up(o + (size_t)g.fwdTiles * g.Khalf * sizeof(float));
-        pl.o_gd[l] = o; o = align_up(o + (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T * sizeof(float));
+        pl.o_gd[l] = o; o = align_up(o + 3 * (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T * sizeof(float));
         pl.o_adj[l] = o; o = align_up(o + (size_t)g.nChunks * g.N * sizeof(float));
     }
     pl.bytes = o;
@@ -274,17 +285,6 @@ dmcr_status prepare_device() {
     return DMCR_OK;
 }
 
-struct Ws {
-    char* base;
-    const Plan* pl;
-    Scalars* scal() const { return reinterpret_cast<Scalars*>(base + pl->o_scal); }
-    double* pen() const { return reinterpret_cast<double*>(base + pl->o_pen); }
-    float* desc() const { return reinterpret_cast<float*>(base + pl->o_desc); }
-    float* fwd(int l) const { return reinterpret_cast<float*>(base + pl->o_fwd[l]); }
-    float* gd(int l) const { return reinterpret_cast<float*>(base + pl->o_gd[l]); }
-    float* adj(int l) const { return reinterpret_cast<float*>(base + pl->o_adj[l]); }
-};
-
 dmcr_status check_ws(const Plan& pl, void* ws, size_t ws_bytes) {
     if (ws == nullptr) return fail(DMCR_EINVAL, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0) return fail(DMCR_EINVAL, "workspace must be 256-byte aligned");
@@ -293,79 +293,304 @@ dmcr_status check_ws(const Plan& pl, void* ws, size_t ws_bytes) {
     return DMCR_OK;
 }
 
-// Pyramid level pointers: level 0 is the caller's field.
-void pyramid(const Plan& pl, const Ws& w, const float* field, const float* lv[MAX_LEVELS], const int* done,
-             cudaStream_t s) {
-    lv[0] = field;
-    for (int l = 1; l < pl.levels; ++l) {
-        float* dst = reinterpret_cast<float*>(w.base + pl.o_pyr[l]);
-        const LevelGeom& gf = pl.g[l - 1];
-        int64_t nf[3] = {gf.n[0], gf.n[1], gf.n[2]};
-        ProfScope ps("restrict", l, s);
-        launch_restrict(pl.ndim, nf, lv[l - 1], dst, done, s);
-        lv[l] = dst;
+// ---------------------------------------------------------------------------- execution engine
+//
+// Every entry point runs the same fused phases over a set of instances (one for the plain
+// calls, many for the batched ones).  The host fills one table buffer with the segment
+// arrays of every phase, writes it to the table region with blob_kernel (stream ordered,
+// no host synchronisation), then launches one kernel per phase:
+//   init -> restrict (per level index) -> corr_fwd -> fwd_reduce -> penalty -> loss
+//        -> gcoef -> corr_adj -> final (gradient assembly, optional Adam step).
+enum : unsigned {
+    F_INIT = 1u,     // reset the per-instance scalars (Adam step counters)
+    F_FWD = 2u,      // pyramid + descriptor
+    F_LOSS = 4u,     // penalty + loss
+    F_BACK = 8u,     // adjoint coefficients + adjoint + gradient assembly
+    F_ADAM = 16u     // the assembly applies one Adam step instead of writing the gradient
+};
+
+struct Inst {
+    const Plan* pl = nullptr;
+    char* ws = nullptr;            // this instance's workspace (Plan layout)
+    Scalars* sc = nullptr;         // this instance's scalars
+    const float* field = nullptr;  // finest field
+    float* M = nullptr;            // F_ADAM: the field updated in place
+    const float* target = nullptr; // F_LOSS/F_BACK: target descriptor; VJP: upstream gradient
+    float* desc = nullptr;         // descriptor output (workspace scratch if the caller gives none)
+    float* loss_out = nullptr;
+    float* grad = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-7f;
+    LossParams lp{};
+    float* history = nullptr;
+    bool use_done = false;         // kernels skip the instance once its done flag is set
+    int64_t step = 0;              // F_INIT: Adam steps taken before this call
+    const float* lv[MAX_LEVELS] = {};
+};
+
+struct TableBuf {
+    std::vector<unsigned char> h;
+    size_t add(const void* p, size_t n) {
+        const size_t off = (h.size() + 15) & ~size_t(15);
+        h.resize(off + n);
+        memcpy(h.data() + off, p, n);
+        return off;
     }
+};
+
+struct Prepared {
+    char* tab = nullptr;
+    TableBuf tb;
+    ThreshConst tc{};
+    unsigned flags = 0;
+    struct R {
+        size_t off;
+        int nseg;
+        int64_t blocks;
+    };
+    std::vector<R> restricts;
+    R fwd{0, 0, 0}, red{0, 0, 0}, pen{0, 0, 0}, loss{0, 0, 0}, gco{0, 0, 0}, adj{0, 0, 0}, fin{0, 0, 0},
+        init{0, 0, 0};
+    size_t smem_fwd = 0, smem_adj = 0;
+    template <typename S>
+    const S* at(size_t off) const { return reinterpret_cast<const S*>(tab + off); }
+};
+
+template <typename S>
+size_t push(TableBuf& tb, const std::vector<S>& v) {
+    return v.empty() ? 0 : tb.add(v.data(), v.size() * sizeof(S));
 }
 
-void forward(const Plan& pl, const Ws& w, const float* const lv[MAX_LEVELS], float* desc, const int* done,
-             cudaStream_t s) {
-    for (int l = 0; l < pl.levels; ++l) {
-        {
-            ProfScope ps("corr_fwd", l, s);
-            launch_corr_fwd(pl.g[l], pl.tc, lv[l], w.fwd(l), done, s);
-        }
-        ProfScope ps("fwd_reduce", l, s);
-        launch_fwd_reduce(pl.g[l], pl.tc, w.fwd(l), pl.w[l], desc + pl.off[l], done, s);
-    }
+bool same_thresh(const ThreshConst& a, const ThreshConst& b) {
+    return a.identity == b.identity && a.kappa == b.kappa && a.cexp == b.cexp && a.c1 == b.c1 && a.c3 == b.c3;
 }
 
-// Adjoint of every level for coefficients built from src (- sub), then the fused gradient
-// assembly (and Adam step when M != nullptr).
-void backward(const Plan& pl, const Ws& w, const float* const lv[MAX_LEVELS], const float* src, const float* sub,
-              const Scalars* gsc, const float* field_pen, const Scalars* pensc, float* grad_out, float* M, float* m,
-              float* v, float b1, float b2, float eps, const int* done, cudaStream_t s) {
-    FinalArgs fa;
-    memset(&fa, 0, sizeof(fa));
-    fa.ndim = pl.ndim;
-    fa.levels = pl.levels;
-    for (int a = 0; a < 3; ++a) fa.n1[a] = pl.g[0].n[a];
-    for (int l = 0; l < pl.levels; ++l) {
-        const LevelGeom& g = pl.g[l];
-        {
-            ProfScope ps("gcoef", l, s);
-            launch_gcoef(g, pl.tc, src + pl.off[l], sub != nullptr ? sub + pl.off[l] : nullptr, gsc, pl.w[l],
-                         w.gd(l), done, s);
-        }
-        {
-            ProfScope ps("corr_adj", l, s);
-            launch_corr_adj(g, pl.tc, lv[l], w.gd(l), w.adj(l), done, s);
-        }
-        fa.parts[l] = w.adj(l);
-        fa.nChunks[l] = g.nChunks;
-        fa.Nl[l] = g.N;
-        for (int a = 0; a < 3; ++a) fa.nl[l][a] = g.n[a];
+// Build every table of the requested phases; `tab`/`cap` is the device table region.
+dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap, Prepared& P) {
+    P.tab = tab;
+    P.flags = flags;
+    P.tc = in[0].pl->tc;
+    int maxL = 0;
+    for (Inst& x : in) {
+        if (!same_thresh(x.pl->tc, P.tc)) return fail(DMCR_ENOTSUP, "batched instances must share threshold and alpha");
+        maxL = std::max(maxL, x.pl->levels);
+        x.lv[0] = x.field;
+        for (int l = 1; l < x.pl->levels; ++l) x.lv[l] = reinterpret_cast<const float*>(x.ws + x.pl->o_pyr[l]);
     }
-    fa.field = field_pen;
-    fa.sc = pensc;
-    fa.grad_out = grad_out;
-    fa.M = M;
-    fa.m = m;
-    fa.v = v;
-    fa.beta1 = b1;
-    fa.beta2 = b2;
-    fa.eps = eps;
-    ProfScope ps(M != nullptr ? "grad_adam" : "grad_assemble", -1, s);
-    launch_final(fa, done, s);
+    const bool need_pyr = (flags & (F_FWD | F_BACK)) != 0;
+    if (flags & F_INIT) {
+        std::vector<InitSeg> v;
+        for (const Inst& x : in)
+            v.push_back({x.sc, x.step, pow((double)x.beta1, (double)x.step), pow((double)x.beta2, (double)x.step)});
+        P.init = {push(P.tb, v), (int)v.size(), (int64_t)v.size()};
+    }
+    if (need_pyr) {
+        for (int l = 1; l < maxL; ++l) {
+            std::vector<RestrictSeg> v;
+            int64_t b = 0;
+            for (const Inst& x : in) {
+                if (x.pl->levels <= l) continue;
+                const LevelGeom& g = x.pl->g[l];
+                RestrictSeg r{};
+                r.ndim = x.pl->ndim;
+                for (int a = 0; a < 3; ++a) r.c[a] = g.n[a];
+                r.fine = x.lv[l - 1];
+                r.coarse = const_cast<float*>(x.lv[l]);
+                r.done = x.use_done ? &x.sc->done : nullptr;
+                r.blockStart = b;
+                b += ceil_div(g.N, ELEM_TH);
+                v.push_back(r);
+            }
+            P.restricts.push_back({push(P.tb, v), (int)v.size(), b});
+        }
+    }
+    if (flags & F_FWD) {
+        struct Item {
+            FwdSeg f;
+            int64_t work, blocks;
+        };
+        std::vector<Item> items;
+        std::vector<RedSeg> rv;
+        int64_t rb = 0;
+        for (const Inst& x : in)
+            for (int l = 0; l < x.pl->levels; ++l) {
+                const LevelGeom& g = x.pl->g[l];
+                Item it{};
+                it.f.g = g;
+                it.f.field = x.lv[l];
+                it.f.partial = reinterpret_cast<float*>(x.ws + x.pl->o_fwd[l]);
+                it.f.done = x.use_done ? &x.sc->done : nullptr;
+                it.work = (int64_t)g.TY * g.PPB;
+                it.blocks = g.fwdTiles * g.fwdGroupBlocks;
+                items.push_back(it);
+                P.smem_fwd = std::max(P.smem_fwd, fwd_smem_bytes(g));
+                RedSeg r{};
+                r.g = g;
+                r.partial = it.f.partial;
+                r.desc = x.desc + x.pl->off[l];
+                r.done = it.f.done;
+                r.weight = x.pl->w[l];
+                r.blockStart = rb;
+                rb += ceil_div(g.Khalf, RED_K);
+                rv.push_back(r);
+            }
+        // heaviest blocks first: the tail of the launch is made of the light ones
+        std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.work > b.work; });
+        std::vector<FwdSeg> fv;
+        int64_t b = 0;
+        for (Item& it : items) {
+            it.f.blockStart = b;
+            b += it.blocks;
+            fv.push_back(it.f);
+        }
+        P.fwd = {push(P.tb, fv), (int)fv.size(), b};
+        P.red = {push(P.tb, rv), (int)rv.size(), rb};
+    }
+    if (flags & F_LOSS) {
+        std::vector<PenSeg> pv;
+        std::vector<LossSeg> lvv;
+        for (const Inst& x : in) {
+            double* pen = reinterpret_cast<double*>(x.ws + x.pl->o_pen);
+            if (x.lp.bc_on) pv.push_back({x.field, x.pl->N1, pen, x.use_done ? &x.sc->done : nullptr});
+            LossSeg ls{};
+            ls.lp = x.lp;
+            ls.desc = x.desc;
+            ls.target = x.target;
+            ls.pen = x.lp.bc_on ? pen : nullptr;
+            ls.sc = x.sc;
+            ls.loss_out = x.loss_out;
+            ls.history = x.history;
+            lvv.push_back(ls);
+        }
+        P.pen = {push(P.tb, pv), (int)pv.size(), (int64_t)pv.size()};
+        P.loss = {push(P.tb, lvv), (int)lvv.size(), (int64_t)lvv.size()};
+    }
+    if (flags & F_BACK) {
+        struct Item {
+            AdjSeg a;
+            int64_t work, blocks;
+        };
+        std::vector<Item> items;
+        std::vector<GSeg> gv;
+        std::vector<FinalSeg> fv;
+        int64_t gb = 0, fb = 0;
+        const bool vjp = !(flags & F_LOSS);
+        for (const Inst& x : in) {
+            FinalSeg fs{};
+            FinalArgs& fa = fs.a;
+            fa.ndim = x.pl->ndim;
+            fa.levels = x.pl->levels;
+            for (int a = 0; a < 3; ++a) fa.n1[a] = x.pl->g[0].n[a];
+            for (int l = 0; l < x.pl->levels; ++l) {
+                const LevelGeom& g = x.pl->g[l];
+                float* Gd = reinterpret_cast<float*>(x.ws + x.pl->o_gd[l]);
+                float* part = reinterpret_cast<float*>(x.ws + x.pl->o_adj[l]);
+                GSeg gs{};
+                gs.g = g;
+                gs.src = vjp ? x.target + x.pl->off[l] : x.desc + x.pl->off[l];
+                gs.sub = vjp ? nullptr : x.target + x.pl->off[l];
+                gs.sc = vjp ? nullptr : x.sc;
+                gs.scale = gcoef_scale(g, x.pl->tc, x.pl->w[l]);
+                gs.Gd = Gd;
+                gs.done = x.use_done ? &x.sc->done : nullptr;
+                gs.blockStart = gb;
+                gb += ceil_div((int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T, GCOEF_TH);
+                gv.push_back(gs);
+                Item it{};
+                it.a.g = g;
+                it.a.field = x.lv[l];
+                it.a.Gd = Gd;
+                it.a.part = part;
+                it.a.done = gs.done;
+                it.work = (int64_t)g.RZ * g.RY * g.NB;
+                it.blocks = g.adjTiles * g.nChunks;
+                items.push_back(it);
+                P.smem_adj = std::max(P.smem_adj, adj_smem_bytes(g));
+                fa.parts[l] = part;
+                fa.nChunks[l] = g.nChunks;
+                fa.Nl[l] = g.N;
+                for (int a = 0; a < 3; ++a) fa.nl[l][a] = g.n[a];
+            }
+            const bool pen = !vjp && x.lp.bc_on;
+            fa.field = pen ? x.field : nullptr;
+            fa.sc = pen ? x.sc : nullptr;
+            if (flags & F_ADAM) {
+                fa.M = x.M;
+                fa.m = x.m;
+                fa.v = x.v;
+                fa.sc = x.sc;
+                fa.field = x.field;
+                fa.beta1 = x.beta1;
+                fa.beta2 = x.beta2;
+                fa.eps = x.eps;
+            } else {
+                fa.grad_out = x.grad;
+            }
+            fs.done = x.use_done ? &x.sc->done : nullptr;
+            fs.blockStart = fb;
+            fb += ceil_div(x.pl->N1, ELEM_TH);
+            fv.push_back(fs);
+        }
+        std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.work > b.work; });
+        std::vector<AdjSeg> av;
+        int64_t ab = 0;
+        for (Item& it : items) {
+            it.a.blockStart = ab;
+            ab += it.blocks;
+            av.push_back(it.a);
+        }
+        P.gco = {push(P.tb, gv), (int)gv.size(), gb};
+        P.adj = {push(P.tb, av), (int)av.size(), ab};
+        P.fin = {push(P.tb, fv), (int)fv.size(), fb};
+    }
+    if (P.tb.h.size() > cap) return fail(DMCR_ENOMEM, "segment tables (%zu bytes) exceed their region", P.tb.h.size());
+    return DMCR_OK;
 }
 
-void penalty_and_loss(const Plan& pl, const Ws& w, const LossParams& lp, const float* field, const float* desc,
-                      const float* target, float* loss_out, float* history, const int* done, cudaStream_t s) {
-    if (lp.bc_on) {
-        ProfScope ps("penalty", -1, s);
-        launch_penalty(field, pl.N1, w.pen(), done, s);
+void upload(const Prepared& P, cudaStream_t s) {
+    if (P.tb.h.empty()) return;
+    ProfScope ps("tables", -1, s);
+    launch_blob(P.tb.h.data(), P.tb.h.size(), P.tab, s);
+}
+
+void run(const Prepared& P, cudaStream_t s) {
+    if (P.flags & F_INIT) {
+        ProfScope ps("scalars_init", -1, s);
+        launch_scalars_init(P.at<InitSeg>(P.init.off), P.init.nseg, s);
     }
-    ProfScope ps("loss", -1, s);
-    launch_loss(lp, desc, target, lp.bc_on ? w.pen() : nullptr, w.scal(), loss_out, history, s);
+    for (const Prepared::R& r : P.restricts) {
+        ProfScope ps("restrict", -1, s);
+        launch_restrict(P.at<RestrictSeg>(r.off), r.nseg, r.blocks, s);
+    }
+    if (P.flags & F_FWD) {
+        {
+            ProfScope ps("corr_fwd", -1, s);
+            launch_corr_fwd(P.at<FwdSeg>(P.fwd.off), P.fwd.nseg, P.fwd.blocks, P.smem_fwd, P.tc, s);
+        }
+        ProfScope ps("fwd_reduce", -1, s);
+        launch_fwd_reduce(P.at<RedSeg>(P.red.off), P.red.nseg, P.red.blocks, s);
+    }
+    if (P.flags & F_LOSS) {
+        if (P.pen.nseg > 0) {
+            ProfScope ps("penalty", -1, s);
+            launch_penalty(P.at<PenSeg>(P.pen.off), P.pen.nseg, s);
+        }
+        ProfScope ps("loss", -1, s);
+        launch_loss(P.at<LossSeg>(P.loss.off), P.loss.nseg, s);
+    }
+    if (P.flags & F_BACK) {
+        {
+            ProfScope ps("gcoef", -1, s);
+            launch_gcoef(P.at<GSeg>(P.gco.off), P.gco.nseg, P.gco.blocks, P.tc, s);
+        }
+        {
+            ProfScope ps("corr_adj", -1, s);
+            launch_corr_adj(P.at<AdjSeg>(P.adj.off), P.adj.nseg, P.adj.blocks, P.smem_adj, P.tc, s);
+        }
+        ProfScope ps((P.flags & F_ADAM) ? "grad_adam" : "grad_assemble", -1, s);
+        launch_final(P.at<FinalSeg>(P.fin.off), P.fin.nseg, P.fin.blocks, s);
+    }
 }
 
 LossParams make_lp(const Plan& pl, const dmcr_loss_opts* o) {
@@ -376,7 +601,192 @@ LossParams make_lp(const Plan& pl, const dmcr_loss_opts* o) {
     lp.bc_on = o ? o->bc_on : 1;
     lp.Ktot = pl.Ktot;
     lp.N = pl.N1;
+    lp.check_every = 1;
     return lp;
+}
+
+Inst single(const Plan& pl, void* ws) {
+    Inst x;
+    x.pl = &pl;
+    x.ws = static_cast<char*>(ws);
+    x.sc = reinterpret_cast<Scalars*>(x.ws + pl.o_scal);
+    x.desc = reinterpret_cast<float*>(x.ws + pl.o_desc);
+    return x;
+}
+
+char* table_region(const Plan& pl, void* ws) { return static_cast<char*>(ws) + pl.o_tab; }
+
+dmcr_status exec_single(Inst& x, unsigned flags, cudaStream_t s, const char* what) {
+    std::vector<Inst> in{x};
+    Prepared P;
+    DMCR_TRY(prepare(in, flags, table_region(*x.pl, x.ws), x.pl->tab_bytes, P));
+    upload(P, s);
+    run(P, s);
+    return cuda_check(cudaGetLastError(), what);
+}
+
+dmcr_status check_loss_opts(const dmcr_loss_opts* o) {
+    if (o != nullptr && o->mode != DMCR_LOSS_NORM && o->mode != DMCR_LOSS_SQUARED)
+        return fail(DMCR_EINVAL, "unknown loss mode %d", o->mode);
+    return DMCR_OK;
+}
+
+// ---------------------------------------------------------------------------- batches
+//
+// Batch workspace: [segment tables][count x Scalars][instance workspaces (Plan layouts)].
+struct BatchLayout {
+    std::vector<Plan> plans;
+    std::vector<size_t> o_inst;
+    size_t o_tab = 0, tab_bytes = 0, o_scal = 0, bytes = 0;
+};
+
+dmcr_status batch_layout(int count, const dmcr_params* params, BatchLayout& B) {
+    if (count < 1) return fail(DMCR_EINVAL, "count must be >= 1");
+    if (params == nullptr) return fail(DMCR_EINVAL, "params is NULL");
+    B.plans.resize(count);
+    size_t tb = table_slack();
+    for (int i = 0; i < count; ++i) {
+        DMCR_TRY(validate_and_plan(&params[i], B.plans[i]));
+        tb += table_bound(B.plans[i].levels) + 32;
+    }
+    size_t o = 0;
+    B.o_tab = o;
+    B.tab_bytes = align_up(tb);
+    o += B.tab_bytes;
+    B.o_scal = o;
+    o = align_up(o + (size_t)count * sizeof(Scalars));
+    for (int i = 0; i < count; ++i) {
+        B.o_inst.push_back(o);
+        o = align_up(o + B.plans[i].bytes);
+    }
+    B.bytes = o;
+    return DMCR_OK;
+}
+
+dmcr_status batch_ws(const BatchLayout& B, void* ws, size_t ws_bytes) {
+    if (ws == nullptr) return fail(DMCR_EINVAL, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0) return fail(DMCR_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < B.bytes) return fail(DMCR_ENOMEM, "workspace too small: %zu < %zu bytes", ws_bytes, B.bytes);
+    return DMCR_OK;
+}
+
+std::vector<Inst> batch_insts(const BatchLayout& B, void* ws) {
+    std::vector<Inst> in(B.plans.size());
+    char* base = static_cast<char*>(ws);
+    for (size_t i = 0; i < B.plans.size(); ++i) {
+        Inst& x = in[i];
+        x.pl = &B.plans[i];
+        x.ws = base + B.o_inst[i];
+        x.sc = reinterpret_cast<Scalars*>(base + B.o_scal) + i;
+        x.desc = reinterpret_cast<float*>(x.ws + B.plans[i].o_desc);
+    }
+    return in;
+}
+
+dmcr_status exec_batch(const BatchLayout& B, void* ws, std::vector<Inst>& in, unsigned flags, cudaStream_t s,
+                       const char* what) {
+    Prepared P;
+    DMCR_TRY(prepare(in, flags, static_cast<char*>(ws) + B.o_tab, B.tab_bytes, P));
+    upload(P, s);
+    run(P, s);
+    return cuda_check(cudaGetLastError(), what);
+}
+
+// Graph-captured reconstruction of every instance (each stops on its own device flag).
+dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, Scalars* scal_base,
+                              const std::vector<int>& max_iters, int poll_every, dmcr_recon_report* reports,
+                              dmcr_adam_state* states, cudaStream_t caller) {
+    const int count = (int)in.size();
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    dmcr_status st = DMCR_OK;
+    std::vector<Scalars> hs(count);
+    do {
+        if ((st = cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate"))) break;
+        if ((st = cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate"))) break;
+        if ((st = cuda_check(cudaEventRecord(ev, caller), "cudaEventRecord"))) break;
+        if ((st = cuda_check(cudaStreamWaitEvent(s, ev, 0), "cudaStreamWaitEvent"))) break;
+        Prepared P0;
+        if ((st = prepare(in, F_INIT, tab, tab_cap, P0))) break;
+        upload(P0, s);
+        run(P0, s);
+        Prepared P;
+        if ((st = prepare(in, F_FWD | F_LOSS | F_BACK | F_ADAM, tab, tab_cap, P))) break;
+        upload(P, s);
+        if ((st = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "BeginCapture"))) break;
+        run(P, s);
+        if ((st = cuda_check(cudaStreamEndCapture(s, &graph), "EndCapture"))) break;
+        if ((st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "GraphInstantiate"))) break;
+        int most = 0;
+        for (int k : max_iters) most = std::max(most, k);
+        // iteration max_iters evaluates the final field and sets the done flag
+        int launched = 0;
+        while (launched <= most) {
+            const int k = std::min(poll_every, most + 1 - launched);
+            for (int i = 0; i < k && !st; ++i) st = cuda_check(cudaGraphLaunch(exec, s), "GraphLaunch");
+            if (st) break;
+            launched += k;
+            if ((st = cuda_check(cudaMemcpyAsync(hs.data(), scal_base, count * sizeof(Scalars), cudaMemcpyDeviceToHost,
+                                                 s), "scalars D2H")))
+                break;
+            if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
+            bool all = true;
+            for (const Scalars& x : hs) all = all && x.done != 0;
+            if (all) break;
+        }
+        if (st) break;
+        for (int i = 0; i < count; ++i) {
+            dmcr_recon_report& r = reports[i];
+            memset(&r, 0, sizeof(r));
+            r.iterations = (int)(hs[i].adam_step - states[i].step);
+            r.converged = hs[i].done == 1;
+            for (int k = 0; k < DMCR_OUT_COUNT; ++k) r.loss[k] = hs[i].loss[k];
+            r.status = hs[i].done == 2 ? DMCR_ENONFINITE : DMCR_OK;
+            states[i].step = hs[i].adam_step;
+            if (hs[i].done == 2) st = fail(DMCR_ENONFINITE, "loss became non-finite in instance %d", i);
+        }
+    } while (0);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    if (ev) cudaEventDestroy(ev);
+    return st;
+}
+
+dmcr_status check_recon_opts(const dmcr_recon_opts* o) {
+    if (o == nullptr) return fail(DMCR_EINVAL, "opts is NULL");
+    if (o->max_iters < 0 || o->check_every < 1) return fail(DMCR_EINVAL, "max_iters >= 0 and check_every >= 1");
+    if (o->init != DMCR_INIT_CALLER && o->init != DMCR_INIT_UNIFORM_SEEDED)
+        return fail(DMCR_EINVAL, "unknown init %d", o->init);
+    return check_loss_opts(&o->loss);
+}
+
+void recon_inst(Inst& x, const dmcr_recon_opts* o, const float* target, float* field, const dmcr_adam_state* st,
+                float* history) {
+    x.field = field;
+    x.M = field;
+    x.target = target;
+    x.m = st->m;
+    x.v = st->v;
+    x.beta1 = o->beta1;
+    x.beta2 = o->beta2;
+    x.eps = o->eps;
+    x.lp = make_lp(*x.pl, &o->loss);
+    x.lp.tol_rel = o->tol_rel;
+    x.lp.check_every = o->check_every;
+    x.lp.lr = o->lr;
+    x.lp.beta1 = o->beta1;
+    x.lp.beta2 = o->beta2;
+    x.lp.max_iters = o->max_iters;
+    x.lp.recon = 1;
+    x.history = history;
+    x.use_done = true;
+    x.step = st->step;
 }
 
 }  // namespace
@@ -385,7 +795,7 @@ LossParams make_lp(const Plan& pl, const dmcr_loss_opts* o) {
 
 extern "C" {
 
-int dmcr_version(void) { return 100; }
+int dmcr_version(void) { return 200; }
 
 const char* dmcr_last_error(void) { return g_err; }
 
@@ -412,12 +822,10 @@ dmcr_status dmcr_descriptor(const dmcr_params* p, const float* field, float* des
     if (field == nullptr || desc == nullptr) return fail(DMCR_EINVAL, "field/desc is NULL");
     DMCR_TRY(check_ws(pl, ws, ws_bytes));
     DMCR_TRY(prepare_device());
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Ws w{static_cast<char*>(ws), &pl};
-    const float* lv[MAX_LEVELS];
-    pyramid(pl, w, field, lv, nullptr, s);
-    forward(pl, w, lv, desc, nullptr, s);
-    return cuda_check(cudaGetLastError(), "dmcr_descriptor launch");
+    Inst x = single(pl, ws);
+    x.field = field;
+    x.desc = desc;
+    return exec_single(x, F_FWD, static_cast<cudaStream_t>(stream), "dmcr_descriptor launch");
 }
 
 dmcr_status dmcr_loss_grad(const dmcr_params* p, const dmcr_loss_opts* opts, const float* field,
@@ -426,22 +834,18 @@ dmcr_status dmcr_loss_grad(const dmcr_params* p, const dmcr_loss_opts* opts, con
     Plan pl;
     DMCR_TRY(validate_and_plan(p, pl));
     if (field == nullptr || target_desc == nullptr) return fail(DMCR_EINVAL, "field/target is NULL");
-    if (opts != nullptr && opts->mode != DMCR_LOSS_NORM && opts->mode != DMCR_LOSS_SQUARED)
-        return fail(DMCR_EINVAL, "unknown loss mode %d", opts->mode);
+    DMCR_TRY(check_loss_opts(opts));
     DMCR_TRY(check_ws(pl, ws, ws_bytes));
     DMCR_TRY(prepare_device());
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Ws w{static_cast<char*>(ws), &pl};
-    const float* lv[MAX_LEVELS];
-    float* desc = desc_out != nullptr ? desc_out : w.desc();
-    const LossParams lp = make_lp(pl, opts);
-    pyramid(pl, w, field, lv, nullptr, s);
-    forward(pl, w, lv, desc, nullptr, s);
-    penalty_and_loss(pl, w, lp, field, desc, target_desc, loss_out, nullptr, nullptr, s);
-    if (grad != nullptr)
-        backward(pl, w, lv, desc, target_desc, w.scal(), field, lp.bc_on ? w.scal() : nullptr, grad, nullptr, nullptr,
-                 nullptr, 0.f, 0.f, 0.f, nullptr, s);
-    return cuda_check(cudaGetLastError(), "dmcr_loss_grad launch");
+    Inst x = single(pl, ws);
+    x.field = field;
+    x.target = target_desc;
+    if (desc_out != nullptr) x.desc = desc_out;
+    x.loss_out = loss_out;
+    x.grad = grad;
+    x.lp = make_lp(pl, opts);
+    return exec_single(x, F_FWD | F_LOSS | (grad != nullptr ? F_BACK : 0u), static_cast<cudaStream_t>(stream),
+                       "dmcr_loss_grad launch");
 }
 
 dmcr_status dmcr_descriptor_vjp(const dmcr_params* p, const float* field, const float* grad_desc, float* grad_field,
@@ -452,13 +856,11 @@ dmcr_status dmcr_descriptor_vjp(const dmcr_params* p, const float* field, const 
         return fail(DMCR_EINVAL, "field/grad_desc/grad_field is NULL");
     DMCR_TRY(check_ws(pl, ws, ws_bytes));
     DMCR_TRY(prepare_device());
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Ws w{static_cast<char*>(ws), &pl};
-    const float* lv[MAX_LEVELS];
-    pyramid(pl, w, field, lv, nullptr, s);
-    backward(pl, w, lv, grad_desc, nullptr, nullptr, nullptr, nullptr, grad_field, nullptr, nullptr, nullptr, 0.f, 0.f,
-             0.f, nullptr, s);
-    return cuda_check(cudaGetLastError(), "dmcr_descriptor_vjp launch");
+    Inst x = single(pl, ws);
+    x.field = field;
+    x.target = grad_desc;
+    x.grad = grad_field;
+    return exec_single(x, F_BACK, static_cast<cudaStream_t>(stream), "dmcr_descriptor_vjp launch");
 }
 
 dmcr_status dmcr_restrict(int ndim, const int64_t n_fine[3], const float* fine, float* coarse, void* stream) {
@@ -469,7 +871,7 @@ dmcr_status dmcr_restrict(int ndim, const int64_t n_fine[3], const float* fine, 
     else { nf[0] = n_fine[0]; nf[1] = n_fine[1]; nf[2] = n_fine[2]; }
     for (int a = (ndim == 2 ? 1 : 0); a < 3; ++a)
         if (nf[a] < 2 || nf[a] % 2) return fail(DMCR_EINVAL, "fine sizes must be even and >= 2");
-    launch_restrict(ndim, nf, fine, coarse, nullptr, static_cast<cudaStream_t>(stream));
+    launch_restrict_one(ndim, nf, fine, coarse, static_cast<cudaStream_t>(stream));
     return cuda_check(cudaGetLastError(), "dmcr_restrict launch");
 }
 
@@ -495,102 +897,6 @@ dmcr_status dmcr_init_uniform(float* field, int64_t count, uint64_t seed, void* 
     return cuda_check(cudaGetLastError(), "dmcr_init_uniform launch");
 }
 
-dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* o, const float* target_desc,
-                             float* field, dmcr_adam_state* state, float* history, dmcr_recon_report* report,
-                             void* ws, size_t ws_bytes, void* stream) {
-    Plan pl;
-    DMCR_TRY(validate_and_plan(p, pl));
-    if (o == nullptr || target_desc == nullptr || field == nullptr || state == nullptr || report == nullptr ||
-        state->m == nullptr || state->v == nullptr)
-        return fail(DMCR_EINVAL, "NULL argument");
-    if (o->max_iters < 0 || o->check_every < 1) return fail(DMCR_EINVAL, "max_iters >= 0 and check_every >= 1");
-    if (o->init != DMCR_INIT_CALLER && o->init != DMCR_INIT_UNIFORM_SEEDED)
-        return fail(DMCR_EINVAL, "unknown init %d", o->init);
-    if (o->loss.mode != DMCR_LOSS_NORM && o->loss.mode != DMCR_LOSS_SQUARED)
-        return fail(DMCR_EINVAL, "unknown loss mode %d", o->loss.mode);
-    DMCR_TRY(check_ws(pl, ws, ws_bytes));
-    DMCR_TRY(prepare_device());
-    memset(report, 0, sizeof(*report));
-    cudaStream_t caller = static_cast<cudaStream_t>(stream);
-    cudaStream_t s = nullptr;
-    cudaEvent_t ev = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    dmcr_status st = DMCR_OK;
-    Ws w{static_cast<char*>(ws), &pl};
-    Scalars* dsc = w.scal();
-    const int* done = &dsc->done;
-    LossParams lp = make_lp(pl, &o->loss);
-    lp.tol_rel = o->tol_rel;
-    lp.check_every = o->check_every;
-    lp.lr = o->lr;
-    lp.beta1 = o->beta1;
-    lp.beta2 = o->beta2;
-    lp.max_iters = o->max_iters;
-    lp.recon = 1;
-    const float* lv[MAX_LEVELS];
-
-    do {
-        if ((st = cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate"))) break;
-        if ((st = cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate"))) break;
-        if ((st = cuda_check(cudaEventRecord(ev, caller), "cudaEventRecord"))) break;
-        if ((st = cuda_check(cudaStreamWaitEvent(s, ev, 0), "cudaStreamWaitEvent"))) break;
-        if (o->init == DMCR_INIT_UNIFORM_SEEDED) launch_init_uniform(field, pl.N1, o->seed, s);
-        launch_scalars_init(dsc, state->step, s);
-        // one iteration, captured once
-        if ((st = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "BeginCapture"))) break;
-        pyramid(pl, w, field, lv, done, s);
-        forward(pl, w, lv, w.desc(), done, s);
-        penalty_and_loss(pl, w, lp, field, w.desc(), target_desc, nullptr, history, done, s);
-        backward(pl, w, lv, w.desc(), target_desc, dsc, field, lp.bc_on ? dsc : nullptr, nullptr, field, state->m,
-                 state->v, o->beta1, o->beta2, o->eps, done, s);
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        if ((st = cuda_check(ce, "EndCapture"))) break;
-        if ((st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "GraphInstantiate"))) break;
-        Scalars hs;
-        int launched = 0;
-        while (launched < o->max_iters) {
-            const int k = std::min(o->check_every, o->max_iters - launched);
-            for (int i = 0; i < k; ++i)
-                if ((st = cuda_check(cudaGraphLaunch(exec, s), "GraphLaunch"))) break;
-            if (st) break;
-            launched += k;
-            if ((st = cuda_check(cudaMemcpyAsync(&hs, dsc, sizeof(hs), cudaMemcpyDeviceToHost, s), "scalars D2H")))
-                break;
-            if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
-            if (hs.done) break;
-        }
-        if (st) break;
-        if ((st = cuda_check(cudaMemcpyAsync(&hs, dsc, sizeof(hs), cudaMemcpyDeviceToHost, s), "scalars D2H"))) break;
-        if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
-        report->converged = hs.done == 1;
-        report->iterations = (int)(hs.adam_step - state->step);
-        state->step = hs.adam_step;
-        if (hs.done == 2) {
-            st = fail(DMCR_ENONFINITE, "loss became non-finite at iteration %d", hs.iter);
-            break;
-        }
-        // loss of the returned field (not counted as an iteration)
-        LossParams lq = make_lp(pl, &o->loss);
-        pyramid(pl, w, field, lv, nullptr, s);
-        forward(pl, w, lv, w.desc(), nullptr, s);
-        penalty_and_loss(pl, w, lq, field, w.desc(), target_desc, nullptr, nullptr, nullptr, s);
-        if ((st = cuda_check(cudaMemcpyAsync(&hs, dsc, sizeof(hs), cudaMemcpyDeviceToHost, s), "scalars D2H"))) break;
-        if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
-        for (int i = 0; i < DMCR_OUT_COUNT; ++i) report->loss[i] = hs.loss[i];
-        if (o->tol_rel > 0.f && hs.loss[DMCR_OUT_REL_ERR] < o->tol_rel) report->converged = 1;
-    } while (0);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (s) {
-        cudaStreamSynchronize(s);
-        cudaStreamDestroy(s);
-    }
-    if (ev) cudaEventDestroy(ev);
-    report->status = st;
-    return st;
-}
-
 dmcr_status dmcr_adam_step(const dmcr_params* p, const dmcr_recon_opts* o, const float* target_desc, float* field,
                            dmcr_adam_state* state, float* loss_out, void* ws, size_t ws_bytes, void* stream) {
     Plan pl;
@@ -598,35 +904,165 @@ dmcr_status dmcr_adam_step(const dmcr_params* p, const dmcr_recon_opts* o, const
     if (o == nullptr || target_desc == nullptr || field == nullptr || state == nullptr || state->m == nullptr ||
         state->v == nullptr)
         return fail(DMCR_EINVAL, "NULL argument");
-    if (o->loss.mode != DMCR_LOSS_NORM && o->loss.mode != DMCR_LOSS_SQUARED)
-        return fail(DMCR_EINVAL, "unknown loss mode %d", o->loss.mode);
+    DMCR_TRY(check_loss_opts(&o->loss));
     DMCR_TRY(check_ws(pl, ws, ws_bytes));
     DMCR_TRY(prepare_device());
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Ws w{static_cast<char*>(ws), &pl};
-    Scalars* dsc = w.scal();
-    const int* done = &dsc->done;
-    LossParams lp = make_lp(pl, &o->loss);
-    lp.tol_rel = 0.f;
-    lp.check_every = 1;
-    lp.lr = o->lr;
-    lp.beta1 = o->beta1;
-    lp.beta2 = o->beta2;
-    lp.max_iters = 1;
-    lp.recon = 1;
-    const float* lv[MAX_LEVELS];
-    {
-        ProfScope ps("scalars_init", -1, s);
-        launch_scalars_init(dsc, state->step, s);
-    }
-    pyramid(pl, w, field, lv, nullptr, s);
-    forward(pl, w, lv, w.desc(), nullptr, s);
-    penalty_and_loss(pl, w, lp, field, w.desc(), target_desc, loss_out, nullptr, nullptr, s);
-    backward(pl, w, lv, w.desc(), target_desc, dsc, field, lp.bc_on ? dsc : nullptr, nullptr, field, state->m,
-             state->v, o->beta1, o->beta2, o->eps, done, s);
-    DMCR_TRY(cuda_check(cudaGetLastError(), "dmcr_adam_step launch"));
+    Inst x = single(pl, ws);
+    dmcr_recon_opts one = *o;
+    one.max_iters = 1;
+    one.tol_rel = 0.f;
+    one.check_every = 1;
+    recon_inst(x, &one, target_desc, field, state, nullptr);
+    x.loss_out = loss_out;
+    DMCR_TRY(exec_single(x, F_INIT | F_FWD | F_LOSS | F_BACK | F_ADAM, static_cast<cudaStream_t>(stream),
+                         "dmcr_adam_step launch"));
     state->step += 1;
     return DMCR_OK;
+}
+
+dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* o, const float* target_desc, float* field,
+                             dmcr_adam_state* state, float* history, dmcr_recon_report* report, void* ws,
+                             size_t ws_bytes, void* stream) {
+    Plan pl;
+    DMCR_TRY(validate_and_plan(p, pl));
+    if (target_desc == nullptr || field == nullptr || state == nullptr || report == nullptr ||
+        state->m == nullptr || state->v == nullptr)
+        return fail(DMCR_EINVAL, "NULL argument");
+    DMCR_TRY(check_recon_opts(o));
+    DMCR_TRY(check_ws(pl, ws, ws_bytes));
+    DMCR_TRY(prepare_device());
+    memset(report, 0, sizeof(*report));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (o->init == DMCR_INIT_UNIFORM_SEEDED) launch_init_uniform(field, pl.N1, o->seed, s);
+    std::vector<Inst> in{single(pl, ws)};
+    recon_inst(in[0], o, target_desc, field, state, history);
+    const dmcr_status st = reconstruct_insts(in, table_region(pl, ws), pl.tab_bytes, in[0].sc, {o->max_iters},
+                                             o->check_every, report, state, s);
+    report->status = st;
+    return st;
+}
+
+// ---------------------------------------------------------------------------- batched calls
+
+dmcr_status dmcr_batch_workspace_size(int count, const dmcr_params* params, size_t* bytes) {
+    BatchLayout B;
+    DMCR_TRY(batch_layout(count, params, B));
+    if (bytes == nullptr) return fail(DMCR_EINVAL, "bytes is NULL");
+    *bytes = B.bytes;
+    return DMCR_OK;
+}
+
+dmcr_status dmcr_descriptor_batched(int count, const dmcr_params* params, const float* const* fields,
+                                    float* const* descs, void* ws, size_t ws_bytes, void* stream) {
+    BatchLayout B;
+    DMCR_TRY(batch_layout(count, params, B));
+    if (fields == nullptr || descs == nullptr) return fail(DMCR_EINVAL, "NULL pointer array");
+    DMCR_TRY(batch_ws(B, ws, ws_bytes));
+    DMCR_TRY(prepare_device());
+    std::vector<Inst> in = batch_insts(B, ws);
+    for (int i = 0; i < count; ++i) {
+        if (fields[i] == nullptr || descs[i] == nullptr) return fail(DMCR_EINVAL, "NULL pointer in instance %d", i);
+        in[i].field = fields[i];
+        in[i].desc = descs[i];
+    }
+    return exec_batch(B, ws, in, F_FWD, static_cast<cudaStream_t>(stream), "dmcr_descriptor_batched launch");
+}
+
+dmcr_status dmcr_loss_grad_batched(int count, const dmcr_params* params, const dmcr_loss_opts* opts,
+                                   const float* const* fields, const float* const* targets, float* loss_out,
+                                   float* const* grads, void* ws, size_t ws_bytes, void* stream) {
+    BatchLayout B;
+    DMCR_TRY(batch_layout(count, params, B));
+    if (fields == nullptr || targets == nullptr) return fail(DMCR_EINVAL, "NULL pointer array");
+    DMCR_TRY(check_loss_opts(opts));
+    DMCR_TRY(batch_ws(B, ws, ws_bytes));
+    DMCR_TRY(prepare_device());
+    std::vector<Inst> in = batch_insts(B, ws);
+    for (int i = 0; i < count; ++i) {
+        if (fields[i] == nullptr || targets[i] == nullptr) return fail(DMCR_EINVAL, "NULL pointer in instance %d", i);
+        in[i].field = fields[i];
+        in[i].target = targets[i];
+        in[i].loss_out = loss_out != nullptr ? loss_out + (size_t)DMCR_OUT_COUNT * i : nullptr;
+        in[i].grad = grads != nullptr ? grads[i] : nullptr;
+        in[i].lp = make_lp(B.plans[i], opts);
+    }
+    return exec_batch(B, ws, in, F_FWD | F_LOSS | (grads != nullptr ? F_BACK : 0u), static_cast<cudaStream_t>(stream),
+                      "dmcr_loss_grad_batched launch");
+}
+
+dmcr_status dmcr_descriptor_vjp_batched(int count, const dmcr_params* params, const float* const* fields,
+                                        const float* const* grad_descs, float* const* grad_fields, void* ws,
+                                        size_t ws_bytes, void* stream) {
+    BatchLayout B;
+    DMCR_TRY(batch_layout(count, params, B));
+    if (fields == nullptr || grad_descs == nullptr || grad_fields == nullptr)
+        return fail(DMCR_EINVAL, "NULL pointer array");
+    DMCR_TRY(batch_ws(B, ws, ws_bytes));
+    DMCR_TRY(prepare_device());
+    std::vector<Inst> in = batch_insts(B, ws);
+    for (int i = 0; i < count; ++i) {
+        if (fields[i] == nullptr || grad_descs[i] == nullptr || grad_fields[i] == nullptr)
+            return fail(DMCR_EINVAL, "NULL pointer in instance %d", i);
+        in[i].field = fields[i];
+        in[i].target = grad_descs[i];
+        in[i].grad = grad_fields[i];
+    }
+    return exec_batch(B, ws, in, F_BACK, static_cast<cudaStream_t>(stream), "dmcr_descriptor_vjp_batched launch");
+}
+
+dmcr_status dmcr_adam_step_batched(int count, const dmcr_params* params, const dmcr_recon_opts* opts,
+                                   const float* const* targets, float* const* fields, dmcr_adam_state* states,
+                                   float* loss_out, void* ws, size_t ws_bytes, void* stream) {
+    BatchLayout B;
+    DMCR_TRY(batch_layout(count, params, B));
+    if (opts == nullptr || targets == nullptr || fields == nullptr || states == nullptr)
+        return fail(DMCR_EINVAL, "NULL argument");
+    DMCR_TRY(check_loss_opts(&opts->loss));
+    DMCR_TRY(batch_ws(B, ws, ws_bytes));
+    DMCR_TRY(prepare_device());
+    std::vector<Inst> in = batch_insts(B, ws);
+    dmcr_recon_opts one = *opts;
+    one.max_iters = 1;
+    one.tol_rel = 0.f;
+    one.check_every = 1;
+    for (int i = 0; i < count; ++i) {
+        if (targets[i] == nullptr || fields[i] == nullptr || states[i].m == nullptr || states[i].v == nullptr)
+            return fail(DMCR_EINVAL, "NULL pointer in instance %d", i);
+        recon_inst(in[i], &one, targets[i], fields[i], &states[i], nullptr);
+        in[i].loss_out = loss_out != nullptr ? loss_out + (size_t)DMCR_OUT_COUNT * i : nullptr;
+    }
+    DMCR_TRY(exec_batch(B, ws, in, F_INIT | F_FWD | F_LOSS | F_BACK | F_ADAM, static_cast<cudaStream_t>(stream),
+                        "dmcr_adam_step_batched launch"));
+    for (int i = 0; i < count; ++i) states[i].step += 1;
+    return DMCR_OK;
+}
+
+dmcr_status dmcr_reconstruct_batched(int count, const dmcr_params* params, const dmcr_recon_opts* opts,
+                                     const float* const* targets, float* const* fields, dmcr_adam_state* states,
+                                     dmcr_recon_report* reports, void* ws, size_t ws_bytes, void* stream) {
+    BatchLayout B;
+    DMCR_TRY(batch_layout(count, params, B));
+    if (opts == nullptr || targets == nullptr || fields == nullptr || states == nullptr || reports == nullptr)
+        return fail(DMCR_EINVAL, "NULL argument");
+    DMCR_TRY(batch_ws(B, ws, ws_bytes));
+    DMCR_TRY(prepare_device());
+    std::vector<Inst> in = batch_insts(B, ws);
+    std::vector<int> iters(count);
+    int poll = 1 << 30;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < count; ++i) {
+        DMCR_TRY(check_recon_opts(&opts[i]));
+        if (targets[i] == nullptr || fields[i] == nullptr || states[i].m == nullptr || states[i].v == nullptr)
+            return fail(DMCR_EINVAL, "NULL pointer in instance %d", i);
+        recon_inst(in[i], &opts[i], targets[i], fields[i], &states[i], nullptr);
+        iters[i] = opts[i].max_iters;
+        poll = std::min(poll, opts[i].check_every);
+    }
+    for (int i = 0; i < count; ++i)
+        if (opts[i].init == DMCR_INIT_UNIFORM_SEEDED) launch_init_uniform(fields[i], B.plans[i].N1, opts[i].seed, s);
+    return reconstruct_insts(in, static_cast<char*>(ws) + B.o_tab, B.tab_bytes,
+                             reinterpret_cast<Scalars*>(static_cast<char*>(ws) + B.o_scal), iters, poll, reports,
+                             states, s);
 }
 
 dmcr_status dmcr_profile_enable(int on) {
@@ -703,9 +1139,11 @@ extern "C" dmcr_status dmcr_descriptor_noalloc(const dmcr_params* p, const float
     Plan pl;
     DMCR_TRY(validate_and_plan(p, pl));
     if (field == nullptr || desc == nullptr) return fail(DMCR_EINVAL, "field/desc is NULL");
-    // compact layout: pyramid levels 2.. and the forward partials of every level
+    // compact layout: segment tables, pyramid levels 2.. and the forward partials of every level
     Plan cp = pl;
     size_t o = 0;
+    cp.o_tab = o;
+    o += cp.tab_bytes;
     for (int l = 0; l < cp.levels; ++l) {
         const LevelGeom& g = cp.g[l];
         if (l > 0) { cp.o_pyr[l] = o; o = align_up(o + (size_t)g.N * sizeof(float)); }
@@ -717,11 +1155,11 @@ extern "C" dmcr_status dmcr_descriptor_noalloc(const dmcr_params* p, const float
     void* scratch = nullptr;
     DMCR_TRY(noalloc_scratch(&scratch));
     DMCR_TRY(prepare_device());
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Ws w{static_cast<char*>(scratch), &cp};
-    const float* lv[MAX_LEVELS];
     // every scratch entry read below is written first in the same call: nothing to clear
-    pyramid(cp, w, field, lv, nullptr, s);
-    forward(cp, w, lv, desc, nullptr, s);
-    return cuda_check(cudaGetLastError(), "dmcr_descriptor_noalloc launch");
+    Inst x;
+    x.pl = &cp;
+    x.ws = static_cast<char*>(scratch);
+    x.field = field;
+    x.desc = desc;
+    return exec_single(x, F_FWD, static_cast<cudaStream_t>(stream), "dmcr_descriptor_noalloc launch");
 }

@@ -4,6 +4,7 @@
 // uniform start field.  All reductions use fixed grids and fixed summation orders, so
 // every result is bitwise reproducible run to run.
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -12,12 +13,8 @@ namespace dmcr {
 // --------------------------------------------------------------------- multigrid
 
 // coarse[c] = mean of the 2^d children of c (children summed in a fixed order).
-__global__ void restrict_kernel(int ndim, int64_t c0, int64_t c1, int64_t c2, const float* __restrict__ fine,
-                                float* __restrict__ coarse, const int* __restrict__ done) {
-    if (done != nullptr && *done) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t Nc = c0 * c1 * c2;
-    if (i >= Nc) return;
+__device__ __forceinline__ void restrict_one(int ndim, int64_t c0, int64_t c1, int64_t c2, const float* __restrict__ fine,
+                                             float* __restrict__ coarse, int64_t i) {
     const int64_t x = i % c2, y = (i / c2) % c1, z = i / (c1 * c2);
     const int64_t f1 = 2 * c1, f2 = 2 * c2;
     float s;
@@ -33,13 +30,32 @@ __global__ void restrict_kernel(int ndim, int64_t c0, int64_t c1, int64_t c2, co
     coarse[i] = s;
 }
 
-void launch_restrict(int ndim, const int64_t nf[3], const float* fine, float* coarse, const int* done,
-                     cudaStream_t s) {
+__global__ void restrict_kernel(const RestrictSeg* __restrict__ segs, int nseg) {
+    const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
+    const RestrictSeg& sg = segs[si];
+    if (sg.done != nullptr && *sg.done) return;
+    const int64_t i = ((int64_t)blockIdx.x - sg.blockStart) * ELEM_TH + threadIdx.x;
+    if (i >= sg.c[0] * sg.c[1] * sg.c[2]) return;
+    restrict_one(sg.ndim, sg.c[0], sg.c[1], sg.c[2], sg.fine, sg.coarse, i);
+}
+
+__global__ void restrict_plain_kernel(int ndim, int64_t c0, int64_t c1, int64_t c2, const float* __restrict__ fine,
+                                      float* __restrict__ coarse) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c0 * c1 * c2) return;
+    restrict_one(ndim, c0, c1, c2, fine, coarse, i);
+}
+
+void launch_restrict(const RestrictSeg* segs, int nseg, int64_t blocks, cudaStream_t s) {
+    if (blocks <= 0) return;
+    restrict_kernel<<<(unsigned)blocks, ELEM_TH, 0, s>>>(segs, nseg);
+}
+
+void launch_restrict_one(int ndim, const int64_t nf[3], const float* fine, float* coarse, cudaStream_t s) {
     const int64_t c0 = (ndim == 2) ? 1 : nf[0] / 2;
     const int64_t c1 = nf[1] / 2, c2 = nf[2] / 2;
     const int64_t Nc = c0 * c1 * c2;
-    const int th = 256;
-    restrict_kernel<<<(unsigned)((Nc + th - 1) / th), th, 0, s>>>(ndim, c0, c1, c2, fine, coarse, done);
+    restrict_plain_kernel<<<(unsigned)((Nc + ELEM_TH - 1) / ELEM_TH), ELEM_TH, 0, s>>>(ndim, c0, c1, c2, fine, coarse);
 }
 
 // fine[f] += coarse[parent(f)] / 2^d   (transpose of restrict)   or   fine[f] = coarse[parent(f)]
@@ -82,30 +98,37 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
     return r;
 }
 
-__global__ void penalty_kernel(const float* __restrict__ M, int64_t N, double* __restrict__ partials,
-                               const int* __restrict__ done) {
-    if (done != nullptr && *done) return;
+// grid (NPEN_BLOCKS, instances): fixed-grid FP64 partial sums of the squared box excess.
+__global__ void penalty_kernel(const PenSeg* __restrict__ segs) {
+    const PenSeg& sg = segs[blockIdx.y];
+    if (sg.done != nullptr && *sg.done) return;
     __shared__ double sh[256];
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        const double e = (double)box_excess(M[i]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sg.N; i += stride) {
+        const double e = (double)box_excess(sg.field[i]);
         acc += e * e;
     }
     const double t = block_sum_d(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    if (threadIdx.x == 0) sg.partials[blockIdx.x] = t;
 }
 
-void launch_penalty(const float* field, int64_t N, double* partials, const int* done, cudaStream_t s) {
-    penalty_kernel<<<NPEN_BLOCKS, 256, 0, s>>>(field, N, partials, done);
+void launch_penalty(const PenSeg* segs, int nseg, cudaStream_t s) {
+    if (nseg <= 0) return;
+    penalty_kernel<<<dim3(NPEN_BLOCKS, nseg), 256, 0, s>>>(segs);
 }
 
 // Single block: E, E^2, E_bc, lambda, L, rel_err and the gradient scalars; in a
 // reconstruction also the stopping test and the Adam step bookkeeping.
-__global__ void __launch_bounds__(1024) loss_kernel(LossParams lp, const float* __restrict__ desc,
-                                                    const float* __restrict__ target,
-                                                    const double* __restrict__ pen, Scalars* sc,
-                                                    float* __restrict__ loss_out, float* __restrict__ history) {
+__global__ void __launch_bounds__(1024) loss_kernel(const LossSeg* __restrict__ segs) {
+    const LossSeg& sg = segs[blockIdx.x];
+    const LossParams lp = sg.lp;
+    const float* __restrict__ desc = sg.desc;
+    const float* __restrict__ target = sg.target;
+    const double* __restrict__ pen = sg.pen;
+    Scalars* sc = sg.sc;
+    float* loss_out = sg.loss_out;
+    float* history = sg.history;
     if (lp.recon && sc->done) return;
     __shared__ double sh[1024];
     double r2 = 0.0, t2 = 0.0;
@@ -150,25 +173,30 @@ __global__ void __launch_bounds__(1024) loss_kernel(LossParams lp, const float* 
     if (!isfinite(L)) { sc->done = 2; return; }
     if (lp.tol_rel > 0.f && (it % lp.check_every) == 0 && rel < (double)lp.tol_rel) { sc->done = 1; return; }
     if (it + 1 > lp.max_iters) { sc->done = 3; return; }
-    const int64_t t = sc->adam_step + 1;
-    sc->adam_step = t;
-    sc->lr_t = (float)((double)lp.lr * sqrt(1.0 - pow((double)lp.beta2, (double)t)) /
-                       (1.0 - pow((double)lp.beta1, (double)t)));
+    sc->adam_step = sc->adam_step + 1;
+    const double b1t = sc->b1t * (double)lp.beta1;
+    const double b2t = sc->b2t * (double)lp.beta2;
+    sc->b1t = b1t;
+    sc->b2t = b2t;
+    sc->lr_t = (float)((double)lp.lr * sqrt(1.0 - b2t) / (1.0 - b1t));
 }
 
-void launch_loss(const LossParams& lp, const float* desc, const float* target, const double* pen, Scalars* sc,
-                 float* loss_out, float* history, cudaStream_t s) {
-    loss_kernel<<<1, 1024, 0, s>>>(lp, desc, target, pen, sc, loss_out, history);
+void launch_loss(const LossSeg* segs, int nseg, cudaStream_t s) {
+    if (nseg <= 0) return;
+    loss_kernel<<<nseg, 1024, 0, s>>>(segs);
 }
 
 // --------------------------------------------------------------------- gradient + Adam
 
 // g(y) = sum_l 2^{-d(l-1)} sum_chunks part_l[chunk][ancestor_l(y)]  (+ penalty gradient),
 // then either written out, or used for one Adam step (Keras form) on the field.
-__global__ void final_kernel(FinalArgs a, const int* __restrict__ done) {
-    if (done != nullptr && *done) return;
+__global__ void final_kernel(const FinalSeg* __restrict__ segs, int nseg) {
+    const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
+    const FinalSeg& sg = segs[si];
+    if (sg.done != nullptr && *sg.done) return;
+    const FinalArgs& a = sg.a;
     const int64_t N1 = a.n1[0] * a.n1[1] * a.n1[2];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = ((int64_t)blockIdx.x - sg.blockStart) * ELEM_TH + threadIdx.x;
     if (i >= N1) return;
     const int64_t x = i % a.n1[2], y = (i / a.n1[2]) % a.n1[1], z = i / (a.n1[1] * a.n1[2]);
     float g = 0.f;
@@ -199,24 +227,57 @@ __global__ void final_kernel(FinalArgs a, const int* __restrict__ done) {
     }
 }
 
-void launch_final(const FinalArgs& a, const int* done, cudaStream_t s) {
-    const int64_t N1 = a.n1[0] * a.n1[1] * a.n1[2];
-    const int th = 256;
-    final_kernel<<<(unsigned)((N1 + th - 1) / th), th, 0, s>>>(a, done);
+void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, cudaStream_t s) {
+    if (blocks <= 0) return;
+    final_kernel<<<(unsigned)blocks, ELEM_TH, 0, s>>>(segs, nseg);
 }
 
-__global__ void scalars_init_kernel(Scalars* sc, int64_t adam_step) {
-    for (int i = 0; i < 6; ++i) sc->loss[i] = 0.f;
+__global__ void scalars_init_kernel(const InitSeg* __restrict__ segs, int nseg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nseg) return;
+    Scalars* sc = segs[i].sc;
+    for (int k = 0; k < 6; ++k) sc->loss[k] = 0.f;
     sc->gscale = 0.f;
     sc->pen_coef = 0.f;
     sc->lr_t = 0.f;
     sc->done = 0;
     sc->iter = 0;
-    sc->adam_step = adam_step;
+    sc->adam_step = segs[i].step;
+    sc->b1t = segs[i].b1t;
+    sc->b2t = segs[i].b2t;
 }
 
-void launch_scalars_init(Scalars* sc, int64_t adam_step, cudaStream_t s) {
-    scalars_init_kernel<<<1, 1, 0, s>>>(sc, adam_step);
+void launch_scalars_init(const InitSeg* segs, int nseg, cudaStream_t s) {
+    if (nseg <= 0) return;
+    scalars_init_kernel<<<(nseg + 127) / 128, 128, 0, s>>>(segs, nseg);
+}
+
+// Writes up to BLOB_BYTES of host data, passed by value as a kernel parameter, to device
+// memory: stream ordered, no host synchronisation, and valid inside a graph capture.
+constexpr int BLOB_BYTES = 30720;
+struct Blob {
+    unsigned int words;
+    unsigned int data[BLOB_BYTES / 4];
+};
+
+__global__ void blob_kernel(const Blob b, unsigned int* __restrict__ dst) {
+    for (unsigned int i = threadIdx.x; i < b.words; i += blockDim.x) dst[i] = b.data[i];
+}
+
+void launch_blob(const void* host, size_t bytes, void* dst, cudaStream_t s) {
+    const unsigned char* src = static_cast<const unsigned char*>(host);
+    unsigned char* out = static_cast<unsigned char*>(dst);
+    size_t off = 0;
+    static thread_local Blob b;
+    while (off < bytes) {
+        const size_t n = bytes - off < (size_t)BLOB_BYTES ? bytes - off : (size_t)BLOB_BYTES;
+        const size_t words = (n + 3) / 4;
+        memset(b.data, 0, words * 4);
+        memcpy(b.data, src + off, n);
+        b.words = (unsigned int)words;
+        blob_kernel<<<1, 256, 0, s>>>(b, reinterpret_cast<unsigned int*>(out + off));
+        off += words * 4;
+    }
 }
 
 // --------------------------------------------------------------------- start field

@@ -55,6 +55,7 @@ struct Scalars {
     int done;             // 0 running, 1 converged, 2 non-finite loss
     int iter;             // iterations evaluated in this call
     int64_t adam_step;    // Adam steps taken (global, for bias correction)
+    double b1t, b2t;      // beta1^adam_step, beta2^adam_step (running products)
 };
 
 struct LossParams {
@@ -70,22 +71,6 @@ struct LossParams {
     int recon;          // 1: update iteration / Adam bookkeeping
 };
 
-// ---------------------------------------------------------------- launchers (kernels.cu)
-void launch_restrict(int ndim, const int64_t nf[3], const float* fine, float* coarse,
-                     const int* done, cudaStream_t s);
-void launch_prolongate(int ndim, const int64_t nc[3], const float* coarse, float* fine, int mode,
-                       cudaStream_t s);
-void launch_corr_fwd(const LevelGeom& g, const ThreshConst& tc, const float* field, float* partial,
-                     const int* done, cudaStream_t s);
-void launch_fwd_reduce(const LevelGeom& g, const ThreshConst& tc, const float* partial, float weight,
-                       float* desc, const int* done, cudaStream_t s);
-void launch_penalty(const float* field, int64_t N, double* partials, const int* done, cudaStream_t s);
-void launch_loss(const LossParams& lp, const float* desc, const float* target, const double* pen,
-                 Scalars* sc, float* loss_out, float* history, cudaStream_t s);
-void launch_gcoef(const LevelGeom& g, const ThreshConst& tc, const float* src, const float* sub,
-                  const Scalars* sc, float weight, float* Gd, const int* done, cudaStream_t s);
-void launch_corr_adj(const LevelGeom& g, const ThreshConst& tc, const float* field, const float* Gd,
-                     float* part, const int* done, cudaStream_t s);
 struct FinalArgs {
     int ndim;
     int levels;
@@ -102,11 +87,114 @@ struct FinalArgs {
     float* v;
     float beta1, beta2, eps;
 };
-void launch_final(const FinalArgs& a, const int* done, cudaStream_t s);
+
+// ---------------------------------------------------------------- segment tables
+// A fused launch covers several (instance, level) segments; every segment owns the
+// contiguous block range [blockStart, next blockStart) of a 1-D grid and the kernels find
+// their segment by binary search.  Tables live in device memory (written by blob_kernel).
+struct FwdSeg {
+    LevelGeom g;
+    const float* field;
+    float* partial;
+    const int* done;
+    int64_t blockStart;
+};
+struct RedSeg {
+    LevelGeom g;
+    const float* partial;
+    float* desc;
+    const int* done;
+    float weight;
+    int64_t blockStart;
+};
+struct AdjSeg {
+    LevelGeom g;
+    const float* field;
+    const float* Gd;
+    float* part;
+    const int* done;
+    int64_t blockStart;
+};
+struct GSeg {
+    LevelGeom g;
+    const float* src;
+    const float* sub;
+    const Scalars* sc;
+    float scale;
+    float* Gd;
+    const int* done;
+    int64_t blockStart;
+};
+struct RestrictSeg {
+    int ndim;
+    int64_t c[3];               // coarse sizes (3-D embedded)
+    const float* fine;
+    float* coarse;
+    const int* done;
+    int64_t blockStart;
+};
+struct PenSeg {
+    const float* field;
+    int64_t N;
+    double* partials;
+    const int* done;
+};
+struct LossSeg {
+    LossParams lp;
+    const float* desc;
+    const float* target;
+    const double* pen;
+    Scalars* sc;
+    float* loss_out;
+    float* history;
+};
+struct FinalSeg {
+    FinalArgs a;
+    const int* done;
+    int64_t blockStart;
+};
+struct InitSeg {
+    Scalars* sc;
+    int64_t step;
+    double b1t, b2t;
+};
+
+// ---------------------------------------------------------------- launchers
+void launch_blob(const void* host, size_t bytes, void* dst, cudaStream_t s);
+void launch_restrict(const RestrictSeg* segs, int nseg, int64_t blocks, cudaStream_t s);
+void launch_restrict_one(int ndim, const int64_t nf[3], const float* fine, float* coarse, cudaStream_t s);
+void launch_prolongate(int ndim, const int64_t nc[3], const float* coarse, float* fine, int mode,
+                       cudaStream_t s);
+void launch_corr_fwd(const FwdSeg* segs, int nseg, int64_t blocks, size_t smem, const ThreshConst& tc,
+                     cudaStream_t s);
+void launch_fwd_reduce(const RedSeg* segs, int nseg, int64_t blocks, cudaStream_t s);
+void launch_penalty(const PenSeg* segs, int nseg, cudaStream_t s);
+void launch_loss(const LossSeg* segs, int nseg, cudaStream_t s);
+void launch_gcoef(const GSeg* segs, int nseg, int64_t blocks, const ThreshConst& tc, cudaStream_t s);
+void launch_corr_adj(const AdjSeg* segs, int nseg, int64_t blocks, size_t smem, const ThreshConst& tc,
+                     cudaStream_t s);
+void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, cudaStream_t s);
 void launch_init_uniform(float* field, int64_t count, uint64_t seed, cudaStream_t s);
-void launch_scalars_init(Scalars* sc, int64_t adam_step, cudaStream_t s);
+void launch_scalars_init(const InitSeg* segs, int nseg, cudaStream_t s);
 void set_kernel_attributes();
 size_t fwd_smem_bytes(const LevelGeom& g);
 size_t adj_smem_bytes(const LevelGeom& g);
+float gcoef_scale(const LevelGeom& g, const ThreshConst& tc, float weight);
+
+constexpr int RED_K = 32;      // shifts per fwd_reduce block
+constexpr int GCOEF_TH = 256;  // entries per gcoef block
+constexpr int ELEM_TH = 256;   // pixels per restrict / final block
+
+// Segment of linear block b: the last segment whose blockStart <= b.
+template <typename S>
+__device__ __forceinline__ int find_segment(const S* __restrict__ segs, int nseg, int64_t b) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].blockStart <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 }  // namespace dmcr

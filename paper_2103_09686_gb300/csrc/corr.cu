@@ -49,6 +49,13 @@ __device__ __forceinline__ int64_t wrapi(int64_t i, int64_t n) {
     return m < 0 ? m + n : m;
 }
 
+// v mod n for v within a few periods of [0, n) (the halos reach at most one window past a tile)
+__device__ __forceinline__ int64_t wrap1(int64_t v, int64_t n) {
+    while (v < 0) v += n;
+    while (v >= n) v -= n;
+    return v;
+}
+
 __host__ __device__ inline int stride_4mod32(int cols) {
     // smallest s >= cols with s % 32 == 4
     int s = ((cols - 4 + 31) / 32) * 32 + 4;
@@ -129,41 +136,68 @@ __device__ __forceinline__ void fwd_chunk(const float (&x)[T], const float (&y)[
                                           float (&r2)[T]) {
 #pragma unroll
     for (int k = 0; k < T; ++k) {
+        if (MODE == MODE_FAST) {
+            // two pairs per reciprocal: s_a = d_b / (d_a d_b), s_b = d_a / (d_a d_b); on the fast
+            // path every d <= 2^62, so d_a d_b stays finite (d >= 1 always)
 #pragma unroll
-        for (int m = 0; m < T; ++m) {
-            if (MODE == MODE_IDENT) {
-                const float a = x[k] + y[k + m];
-                r2[m] = fmaf(a, a, r2[m]);
-            } else {
-                float d;
-                if (MODE == MODE_FAST) d = fmaf(x[k], y[k + m], 1.0f);
-                else d = ex2_approx(x[k] - y[k + m]) + 1.0f;
-                const float s = rcp_approx(d);
-                r1[m] += s;
-                r2[m] = fmaf(s, s, r2[m]);
+            for (int m = 0; m < T / 2; ++m) {
+                const float da = fmaf(x[k], y[k + m], 1.0f);
+                const float db = fmaf(x[k], y[k + m + T / 2], 1.0f);
+                const float r = rcp_approx(da * db);
+                const float sa = db * r, sb = da * r;
+                r1[m] += sa;
+                r2[m] = fmaf(sa, sa, r2[m]);
+                r1[m + T / 2] += sb;
+                r2[m + T / 2] = fmaf(sb, sb, r2[m + T / 2]);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < T; ++m) {
+                if (MODE == MODE_IDENT) {
+                    const float a = x[k] + y[k + m];
+                    r2[m] = fmaf(a, a, r2[m]);
+                } else {
+                    const float s = rcp_approx(ex2_approx(x[k] - y[k + m]) + 1.0f);
+                    r1[m] += s;
+                    r2[m] = fmaf(s, s, r2[m]);
+                }
             }
         }
     }
 }
 
+// acc[k] += sum_m G[m] H(s_km) with H(s) = s (1 - s) (c1 s + c3), written with the
+// per-shift coefficients A = -c1 G, B = (c1 - c3) G, C = c3 G as  s (C + s (B + A s)).
 template <int MODE>
-__device__ __forceinline__ void adj_chunk(const float (&x)[T], const float (&y)[2 * T], const float (&G)[T],
-                                          float (&acc)[T], float c1, float c1mc3, float c3) {
+__device__ __forceinline__ void adj_chunk(const float (&x)[T], const float (&y)[2 * T], const float (&A)[T],
+                                          const float (&B)[T], const float (&C)[T], float (&acc)[T]) {
 #pragma unroll
     for (int k = 0; k < T; ++k) {
+        if (MODE == MODE_FAST) {
 #pragma unroll
-        for (int m = 0; m < T; ++m) {
-            if (MODE == MODE_IDENT) {
-                acc[k] = fmaf(G[m], x[k] + y[k + m], acc[k]);
-            } else {
-                float d;
-                if (MODE == MODE_FAST) d = fmaf(x[k], y[k + m], 1.0f);
-                else d = ex2_approx(x[k] - y[k + m]) + 1.0f;
-                const float s = rcp_approx(d);
-                // H(s) = s (1 - s) (c1 s + c3) = s (c3 + s ((c1 - c3) - c1 s))
-                const float q = fmaf(-c1, s, c1mc3);
-                const float q2 = fmaf(s, q, c3);
-                acc[k] = fmaf(G[m] * s, q2, acc[k]);
+            for (int m = 0; m < T / 2; ++m) {
+                const float da = fmaf(x[k], y[k + m], 1.0f);
+                const float db = fmaf(x[k], y[k + m + T / 2], 1.0f);
+                const float r = rcp_approx(da * db);
+                const float sa = db * r, sb = da * r;
+                float qa = fmaf(A[m], sa, B[m]);
+                qa = fmaf(qa, sa, C[m]);
+                acc[k] = fmaf(qa, sa, acc[k]);
+                float qb = fmaf(A[m + T / 2], sb, B[m + T / 2]);
+                qb = fmaf(qb, sb, C[m + T / 2]);
+                acc[k] = fmaf(qb, sb, acc[k]);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < T; ++m) {
+                if (MODE == MODE_IDENT) {
+                    acc[k] = fmaf(A[m], x[k] + y[k + m], acc[k]);
+                } else {
+                    const float s = rcp_approx(ex2_approx(x[k] - y[k + m]) + 1.0f);
+                    float q = fmaf(A[m], s, B[m]);
+                    q = fmaf(q, s, C[m]);
+                    acc[k] = fmaf(q, s, acc[k]);
+                }
             }
         }
     }
@@ -209,12 +243,17 @@ __device__ __forceinline__ void fwd_plane(const float* xs, const float* ybase, i
 
 template <bool IDENT>
 __global__ void __launch_bounds__(FWD_THREADS)
-corr_fwd_kernel(const float* __restrict__ field, LevelGeom g, ThreshConst tc, float* __restrict__ partial,
-                const int* __restrict__ done) {
-    if (done != nullptr && *done) return;
+corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
+    const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
+    const FwdSeg& sg = segs[si];
+    if (sg.done != nullptr && *sg.done) return;
+    const LevelGeom g = sg.g;
+    const float* __restrict__ field = sg.field;
+    float* __restrict__ partial = sg.partial;
+    const int64_t local = (int64_t)blockIdx.x - sg.blockStart;
     extern __shared__ __align__(16) float smem[];
     const int tid = threadIdx.x;
-    const int64_t ts = blockIdx.x;
+    const int64_t ts = local % g.fwdTiles;
     const int tx = (int)(ts % g.tilesX);
     const int ty = (int)((ts / g.tilesX) % g.tilesY);
     const int pc = (int)(ts / ((int64_t)g.tilesX * g.tilesY));
@@ -223,7 +262,7 @@ corr_fwd_kernel(const float* __restrict__ field, LevelGeom g, ThreshConst tc, fl
     const int64_t z1 = min(z0 + (int64_t)g.PPB, g.n[0]);
     const int64_t n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
 
-    const int64_t gfirst = (int64_t)blockIdx.y * FWD_THREADS;
+    const int64_t gfirst = (local / g.fwdTiles) * FWD_THREADS;
     const int64_t glast = min(gfirst + FWD_THREADS, g.NG) - 1;
     const GroupBox bx = group_box(g, gfirst, glast);
     const FwdSmem sh = fwd_smem_shape(g, bx);
@@ -245,53 +284,57 @@ corr_fwd_kernel(const float* __restrict__ field, LevelGeom g, ThreshConst tc, fl
 #pragma unroll
     for (int m = 0; m < T; ++m) { t1[m] = 0.f; t2[m] = 0.f; }
 
-    const int nx = g.TY * TX;
-    const int ny = sh.planesH * sh.rowsH * sh.colsH;
+    const int warp = tid >> 5, lane = tid & 31;
+    constexpr int NW = FWD_THREADS / 32;
+    const int rowsAll = sh.planesH * sh.rowsH;
     const int64_t hx0 = x0 - g.P[2] + (int64_t)T * bx.blo;
+    const float kinf = __int_as_float(0x7f800000);
 
     for (int64_t z = z0; z < z1; ++z) {
         __syncthreads();
         bool bad = false;
-        for (int i = tid; i < nx; i += FWD_THREADS) {
-            const int iy = i / TX, ix = i % TX;
-            const bool valid = (y0 + iy < n1) && (x0 + ix < n2);
-            const float v = valid ? field[(z * n1 + y0 + iy) * n2 + x0 + ix] : 0.f;
-            xs[i] = v;
-            bad |= !(fabsf(tc.kappa * v) <= tc.lim) && valid && !isnan(v);
+        // tails: one row per warp, one column per lane; +inf marks positions outside the field (s = 0)
+        for (int iy = warp; iy < g.TY; iy += NW) {
+            const bool valid = (y0 + iy < n1) && (x0 + lane < n2);
+            const float v = valid ? field[(z * n1 + y0 + iy) * n2 + x0 + lane] : 0.f;
+            bad |= valid && !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
+            xs[iy * TX + lane] = IDENT ? (valid ? 0.5f * v : 0.f)
+                                       : (valid ? ex2_approx(fmaf(-tc.kappa, v, tc.cexp)) : 0x1p100f);
         }
-        for (int i = tid; i < ny; i += FWD_THREADS) {
-            const int c = i % sh.colsH;
-            const int r = (i / sh.colsH) % sh.rowsH;
-            const int p = i / (sh.colsH * sh.rowsH);
-            const int64_t gz = wrapi(z + bx.rzA + p, n0);
-            const int64_t gy = wrapi(y0 + bx.rylo + r, n1);
-            const int64_t gx = wrapi(hx0 + c, n2);
-            const float v = field[(gz * n1 + gy) * n2 + gx];
-            ys[((int64_t)p * sh.rowsH + r) * sh.strideH + c] = v;
-            bad |= !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
+        // tips: the periodic halo, one row per warp, columns strided by the lanes
+        for (int pr = warp; pr < rowsAll; pr += NW) {
+            const int p = pr / sh.rowsH, r = pr - p * sh.rowsH;
+            const float* src = field + (wrap1(z + bx.rzA + p, n0) * n1 + wrap1(y0 + bx.rylo + r, n1)) * n2;
+            float* dst = ys + pr * sh.strideH;
+            int64_t gx = wrap1(hx0 + lane, n2);
+            for (int c = lane; c < sh.colsH; c += 32) {
+                const float v = src[gx];
+                bad |= !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
+                dst[c] = IDENT ? 0.5f * v : ex2_approx(-tc.kappa * v);
+                gx += 32;
+                while (gx >= n2) gx -= n2;
+            }
         }
         const int slow = __syncthreads_or(bad);
-        // transform in place: each thread rewrites the elements it loaded
-        for (int i = tid; i < nx; i += FWD_THREADS) {
-            const int iy = i / TX, ix = i % TX;
-            const bool valid = (y0 + iy < n1) && (x0 + ix < n2);
-            const float v = xs[i];
-            float o;
-            if (IDENT) o = valid ? 0.5f * v : 0.f;
-            else if (!valid) o = __int_as_float(0x7f800000);            // +inf: s = 0
-            else o = slow ? fmaf(-tc.kappa, v, tc.cexp) : ex2_approx(fmaf(-tc.kappa, v, tc.cexp));
-            xs[i] = o;
-        }
-        for (int i = tid; i < ny; i += FWD_THREADS) {
-            const int c = i % sh.colsH;
-            const int r = (i / sh.colsH) % sh.rowsH;
-            const int p = i / (sh.colsH * sh.rowsH);
-            float* q = ys + ((int64_t)p * sh.rowsH + r) * sh.strideH + c;
-            const float v = *q;
-            float o;
-            if (IDENT) o = 0.5f * v;
-            else o = slow ? tc.kappa * v : ex2_approx(-tc.kappa * v);
-            *q = o;
+        if (!IDENT && slow) {
+            // rare: the block holds values outside the fast range; rewrite both tiles in the
+            // exact form (exponents, combined per pair) from the field
+            for (int iy = warp; iy < g.TY; iy += NW) {
+                const bool valid = (y0 + iy < n1) && (x0 + lane < n2);
+                const float v = valid ? field[(z * n1 + y0 + iy) * n2 + x0 + lane] : 0.f;
+                xs[iy * TX + lane] = valid ? fmaf(-tc.kappa, v, tc.cexp) : kinf;
+            }
+            for (int pr = warp; pr < rowsAll; pr += NW) {
+                const int p = pr / sh.rowsH, r = pr - p * sh.rowsH;
+                const float* src = field + (wrap1(z + bx.rzA + p, n0) * n1 + wrap1(y0 + bx.rylo + r, n1)) * n2;
+                float* dst = ys + pr * sh.strideH;
+                int64_t gx = wrap1(hx0 + lane, n2);
+                for (int c = lane; c < sh.colsH; c += 32) {
+                    dst[c] = tc.kappa * src[gx];
+                    gx += 32;
+                    while (gx >= n2) gx -= n2;
+                }
+            }
         }
         __syncthreads();
         float p1[T], p2[T];
@@ -320,50 +363,70 @@ corr_fwd_kernel(const float* __restrict__ field, LevelGeom g, ThreshConst tc, fl
     }
 }
 
-// Fixed-order FP64 sum over tiles, scaled by w_l / N_l.
-__global__ void fwd_reduce_kernel(LevelGeom g, const float* __restrict__ partial, float weight,
-                                  float* __restrict__ desc, const int* __restrict__ done) {
-    if (done != nullptr && *done) return;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.Khalf) return;
+// Fixed-order FP64 sum over tiles, scaled by w_l / N_l.  A block owns 32 consecutive
+// shifts (one per lane, coalesced rows); warp w sums the tiles t = w (mod 8) in order and
+// the 8 warp sums are combined in a fixed order.
+__global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedSeg* __restrict__ segs, int nseg) {
+    const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
+    const RedSeg& sg = segs[si];
+    if (sg.done != nullptr && *sg.done) return;
+    const int64_t Khalf = sg.g.Khalf, tiles = sg.g.fwdTiles;
+    __shared__ double sh[8][RED_K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t k = ((int64_t)blockIdx.x - sg.blockStart) * RED_K + lane;
     double s = 0.0;
-    for (int64_t t = 0; t < g.fwdTiles; ++t) s += (double)partial[t * g.Khalf + k];
-    desc[k] = (float)((double)weight * s / (double)g.N);
+    if (k < Khalf)
+        for (int64_t t = warp; t < tiles; t += 8) s += (double)sg.partial[t * Khalf + k];
+    sh[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && k < Khalf) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += sh[w][lane];
+        sg.desc[k] = (float)((double)sg.weight * tot / (double)sg.g.N);
+    }
 }
 
 // ------------------------------------------------------------------------- adjoint
 
 template <int MODE>
 __device__ __forceinline__ void adj_rows(const float* ys, const float* Gs, int strideH, int WB, int NB, int ryN,
-                                         int lane, int strip, const float (&x)[T], float (&acc)[T], float c1,
-                                         float c1mc3, float c3) {
+                                         int lane, int strip, const float (&x)[T], float (&acc)[T]) {
+    const int plane = ryN * WB;
     for (int r = 0; r < ryN; ++r) {
         const float* yrow = ys + (lane + r) * strideH + T * strip;
         const float* grow = Gs + r * WB;
 #pragma unroll 1
         for (int bb = 0; bb < NB; ++bb) {
-            float y[2 * T], G[T];
+            float y[2 * T], A[T], B[T], C[T];
             load16(yrow + T * bb, y);
-            load8(grow + T * bb, G);
-            adj_chunk<MODE>(x, y, G, acc, c1, c1mc3, c3);
+            load8(grow + T * bb, A);
+            load8(grow + plane + T * bb, B);
+            load8(grow + 2 * plane + T * bb, C);
+            adj_chunk<MODE>(x, y, A, B, C, acc);
         }
     }
 }
 
 template <bool IDENT>
 __global__ void __launch_bounds__(ADJ_THREADS)
-corr_adj_kernel(const float* __restrict__ field, LevelGeom g, ThreshConst tc, const float* __restrict__ Gd,
-                float* __restrict__ part, const int* __restrict__ done) {
-    if (done != nullptr && *done) return;
+corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
+    const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
+    const AdjSeg& sg = segs[si];
+    if (sg.done != nullptr && *sg.done) return;
+    const LevelGeom g = sg.g;
+    const float* __restrict__ field = sg.field;
+    const float* __restrict__ Gd = sg.Gd;
+    float* __restrict__ part = sg.part;
+    const int64_t local = (int64_t)blockIdx.x - sg.blockStart;
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31, strip = threadIdx.x >> 5;
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = local % g.adjTiles;
     const int tx = (int)(tile % g.adjTilesX);
     const int ty = (int)((tile / g.adjTilesX) % g.adjTilesY);
     const int64_t z = tile / ((int64_t)g.adjTilesX * g.adjTilesY);
     const int64_t x0 = (int64_t)tx * TX, y0 = (int64_t)ty * 32;
     const int64_t n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
-    const int chunk = blockIdx.y;
+    const int chunk = (int)(local / g.adjTiles);
     const int zc = chunk / g.nYc, yc = chunk % g.nYc;
     const int rzA = -g.P[0] + zc * g.RZ;
     const int rzB = min(rzA + g.RZ, g.P[0] + 1);
@@ -392,30 +455,45 @@ corr_adj_kernel(const float* __restrict__ field, LevelGeom g, ThreshConst tc, co
     float acc[T];
 #pragma unroll
     for (int k = 0; k < T; ++k) acc[k] = 0.f;
-    const float c1 = tc.c1, c3 = tc.c3, c1mc3 = tc.c1 - tc.c3;
 
-    const int ny = rowsH * colsH;
     const int ng = ryN * WB;
+    const int warp = threadIdx.x >> 5;
+    constexpr int NW = ADJ_THREADS / 32;
     for (int rz = rzA; rz < rzB; ++rz) {
         __syncthreads();
-        const int64_t gz = wrapi(z + rz, n0);
+        const int64_t gz = wrap1(z + rz, n0);
         bool bad = xbad;
-        for (int i = threadIdx.x; i < ny; i += ADJ_THREADS) {
-            const int c = i % colsH, r = i / colsH;
-            const int64_t gy = wrapi(y0 + ryA + r, n1);
-            const int64_t gx = wrapi(hx0 + c, n2);
-            const float v = field[(gz * n1 + gy) * n2 + gx];
-            ys[r * strideH + c] = v;
-            bad |= !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
+        for (int r = warp; r < rowsH; r += NW) {
+            const float* src = field + (gz * n1 + wrap1(y0 + ryA + r, n1)) * n2;
+            float* dst = ys + r * strideH;
+            int64_t gx = wrap1(hx0 + lane, n2);
+            for (int c = lane; c < colsH; c += 32) {
+                const float v = src[gx];
+                bad |= !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
+                dst[c] = IDENT ? 0.5f * v : ex2_approx(-tc.kappa * v);
+                gx += 32;
+                while (gx >= n2) gx -= n2;
+            }
         }
+        const int64_t gplane = (int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * WB;
         const float* grow0 = Gd + ((int64_t)(rz + g.P[0]) * (2 * g.P[1] + 1) + (ryA + g.P[1])) * WB;
-        for (int i = threadIdx.x; i < ng; i += ADJ_THREADS) Gs[i] = grow0[i];
+        for (int i = threadIdx.x; i < ng; i += ADJ_THREADS) {
+            Gs[i] = grow0[i];
+            Gs[ng + i] = grow0[gplane + i];
+            Gs[2 * ng + i] = grow0[2 * gplane + i];
+        }
         const int slow = __syncthreads_or(bad);
-        for (int i = threadIdx.x; i < ny; i += ADJ_THREADS) {
-            const int c = i % colsH, r = i / colsH;
-            float* q = ys + r * strideH + c;
-            const float v = *q;
-            *q = IDENT ? 0.5f * v : (slow ? tc.kappa * v : ex2_approx(-tc.kappa * v));
+        if (!IDENT && slow) {
+            for (int r = warp; r < rowsH; r += NW) {
+                const float* src = field + (gz * n1 + wrap1(y0 + ryA + r, n1)) * n2;
+                float* dst = ys + r * strideH;
+                int64_t gx = wrap1(hx0 + lane, n2);
+                for (int c = lane; c < colsH; c += 32) {
+                    dst[c] = tc.kappa * src[gx];
+                    gx += 32;
+                    while (gx >= n2) gx -= n2;
+                }
+            }
         }
         float x[T];
 #pragma unroll
@@ -424,9 +502,9 @@ corr_adj_kernel(const float* __restrict__ field, LevelGeom g, ThreshConst tc, co
             x[k] = IDENT ? 0.5f * mx[k] : (slow ? u : ex2_approx(u));
         }
         __syncthreads();
-        if (IDENT) adj_rows<MODE_IDENT>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc, c1, c1mc3, c3);
-        else if (slow) adj_rows<MODE_SLOW>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc, c1, c1mc3, c3);
-        else adj_rows<MODE_FAST>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc, c1, c1mc3, c3);
+        if (IDENT) adj_rows<MODE_IDENT>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc);
+        else if (slow) adj_rows<MODE_SLOW>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc);
+        else adj_rows<MODE_FAST>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc);
     }
 
     if (py >= n1) return;
@@ -442,13 +520,19 @@ corr_adj_kernel(const float* __restrict__ field, LevelGeom g, ThreshConst tc, co
 //   Gd[rz][ry][col], rx = col - P2 (zero where rx > P2),
 //   value = scale * (src[k] - sub[k]) * (2 if r = 0),  k = canonical index of +-r,
 //   scale = weight * (gscale from the loss, or 1) * (c1 alpha / N_l, or 1 / N_l for f(x)=x).
-__global__ void gcoef_kernel(LevelGeom g, const float* __restrict__ src, const float* __restrict__ sub,
-                             const Scalars* __restrict__ sc, float scale, float* __restrict__ Gd,
-                             const int* __restrict__ done) {
-    if (done != nullptr && *done) return;
+// Dense full-window coefficient grid of one level, three planes [A | B | C]:
+//   G(r) = scale * (src[k] - sub[k]) * (2 if r = 0),  k = canonical index of +-r,
+//   scale = weight * (gscale from the loss, or 1) * (c1 alpha / N_l, or 1 / N_l for f(x)=x),
+//   A = -c1 G, B = (c1 - c3) G, C = c3 G   (f(x) = x: A = G, B = C = 0),
+// zero where rx > P2 (padding of the last rx block).
+__global__ void gcoef_kernel(const GSeg* __restrict__ segs, int nseg, ThreshConst tc) {
+    const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
+    const GSeg& sg = segs[si];
+    if (sg.done != nullptr && *sg.done) return;
+    const LevelGeom& g = sg.g;
     const int WB = g.NB * T;
     const int64_t total = (int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * WB;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = ((int64_t)blockIdx.x - sg.blockStart) * GCOEF_TH + threadIdx.x;
     if (i >= total) return;
     const int col = (int)(i % WB);
     const int ryi = (int)((i / WB) % (2 * g.P[1] + 1));
@@ -458,12 +542,20 @@ __global__ void gcoef_kernel(LevelGeom g, const float* __restrict__ src, const f
     if (rx <= g.P[2]) {
         int64_t k = canon_index(g, rz, ry, rx);
         if (k < 0) k = canon_index(g, -rz, -ry, -rx);
-        float d = src[k] - (sub != nullptr ? sub[k] : 0.f);
-        float s = scale * (sc != nullptr ? sc->gscale : 1.f);
-        if (rz == 0 && ry == 0 && rx == 0) s *= 2.f;
-        v = s * d;
+        const float d = sg.src[k] - (sg.sub != nullptr ? sg.sub[k] : 0.f);
+        float sc = sg.scale * (sg.sc != nullptr ? sg.sc->gscale : 1.f);
+        if (rz == 0 && ry == 0 && rx == 0) sc *= 2.f;
+        v = sc * d;
     }
-    Gd[i] = v;
+    if (tc.identity) {
+        sg.Gd[i] = v;
+        sg.Gd[total + i] = 0.f;
+        sg.Gd[2 * total + i] = 0.f;
+    } else {
+        sg.Gd[i] = -tc.c1 * v;
+        sg.Gd[total + i] = (tc.c1 - tc.c3) * v;
+        sg.Gd[2 * total + i] = tc.c3 * v;
+    }
 }
 
 // ------------------------------------------------------------------------- launchers
@@ -481,34 +573,30 @@ size_t fwd_smem_bytes(const LevelGeom& g) {
     return (size_t)maxFloats * sizeof(float);
 }
 
-void launch_corr_fwd(const LevelGeom& g, const ThreshConst& tc, const float* field, float* partial,
-                     const int* done, cudaStream_t s) {
-    const size_t smem = fwd_smem_bytes(g);
-    dim3 grid((unsigned)g.fwdTiles, (unsigned)g.fwdGroupBlocks);
-    if (tc.identity) corr_fwd_kernel<true><<<grid, FWD_THREADS, smem, s>>>(field, g, tc, partial, done);
-    else corr_fwd_kernel<false><<<grid, FWD_THREADS, smem, s>>>(field, g, tc, partial, done);
+void launch_corr_fwd(const FwdSeg* segs, int nseg, int64_t blocks, size_t smem, const ThreshConst& tc,
+                     cudaStream_t s) {
+    if (blocks <= 0) return;
+    if (tc.identity) corr_fwd_kernel<true><<<(unsigned)blocks, FWD_THREADS, smem, s>>>(segs, nseg, tc);
+    else corr_fwd_kernel<false><<<(unsigned)blocks, FWD_THREADS, smem, s>>>(segs, nseg, tc);
 }
 
-void launch_fwd_reduce(const LevelGeom& g, const ThreshConst& tc, const float* partial, float weight,
-                       float* desc, const int* done, cudaStream_t s) {
-    (void)tc;
-    const int th = 256;
-    fwd_reduce_kernel<<<(unsigned)((g.Khalf + th - 1) / th), th, 0, s>>>(g, partial, weight, desc, done);
+void launch_fwd_reduce(const RedSeg* segs, int nseg, int64_t blocks, cudaStream_t s) {
+    if (blocks <= 0) return;
+    fwd_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(segs, nseg);
 }
 
 size_t adj_smem_bytes(const LevelGeom& g) {
     const int WB = g.NB * T;
     const int rowsH = 32 + g.RY - 1;
     const int colsH = WB + 5 * T;
-    return (size_t)(rowsH * stride_4mod32(colsH) + g.RY * WB) * sizeof(float);
+    return (size_t)(rowsH * stride_4mod32(colsH) + 3 * g.RY * WB) * sizeof(float);
 }
 
-void launch_corr_adj(const LevelGeom& g, const ThreshConst& tc, const float* field, const float* Gd, float* part,
-                     const int* done, cudaStream_t s) {
-    const size_t smem = adj_smem_bytes(g);
-    dim3 grid((unsigned)g.adjTiles, (unsigned)g.nChunks);
-    if (tc.identity) corr_adj_kernel<true><<<grid, ADJ_THREADS, smem, s>>>(field, g, tc, Gd, part, done);
-    else corr_adj_kernel<false><<<grid, ADJ_THREADS, smem, s>>>(field, g, tc, Gd, part, done);
+void launch_corr_adj(const AdjSeg* segs, int nseg, int64_t blocks, size_t smem, const ThreshConst& tc,
+                     cudaStream_t s) {
+    if (blocks <= 0) return;
+    if (tc.identity) corr_adj_kernel<true><<<(unsigned)blocks, ADJ_THREADS, smem, s>>>(segs, nseg, tc);
+    else corr_adj_kernel<false><<<(unsigned)blocks, ADJ_THREADS, smem, s>>>(segs, nseg, tc);
 }
 
 void set_kernel_attributes() {
@@ -519,14 +607,15 @@ void set_kernel_attributes() {
     cudaFuncSetAttribute(corr_adj_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-void launch_gcoef(const LevelGeom& g, const ThreshConst& tc, const float* src, const float* sub, const Scalars* sc,
-                  float weight, float* Gd, const int* done, cudaStream_t s) {
-    const int WB = g.NB * T;
-    const int64_t total = (int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * WB;
-    const float scale = tc.identity ? weight / (float)g.N
-                                    : (float)((double)weight * (double)tc.c1 * (double)tc.alpha / (double)g.N);
-    const int th = 256;
-    gcoef_kernel<<<(unsigned)((total + th - 1) / th), th, 0, s>>>(g, src, sub, sc, scale, Gd, done);
+// Coefficient scale of one level: w_l * c1 * alpha / N_l (soft; h = c1 alpha H(s)) or w_l / N_l.
+float gcoef_scale(const LevelGeom& g, const ThreshConst& tc, float weight) {
+    return tc.identity ? (float)((double)weight / (double)g.N)
+                       : (float)((double)weight * (double)tc.c1 * (double)tc.alpha / (double)g.N);
+}
+
+void launch_gcoef(const GSeg* segs, int nseg, int64_t blocks, const ThreshConst& tc, cudaStream_t s) {
+    if (blocks <= 0) return;
+    gcoef_kernel<<<(unsigned)blocks, GCOEF_TH, 0, s>>>(segs, nseg, tc);
 }
 
 }  // namespace dmcr
