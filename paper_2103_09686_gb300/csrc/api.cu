@@ -162,6 +162,8 @@ void plan_level(LevelGeom& g) {
     const int64_t perPlane = (int64_t)g.tilesY * g.tilesX * g.fwdGroupBlocks;
     int64_t pcs = std::min<int64_t>(g.n[0], std::max<int64_t>(1, ceil_div(target, perPlane)));
     g.PPB = (int)ceil_div(g.n[0], pcs);
+    // the forward's per-thread block sums hold at most 64 row sums
+    g.PPB = std::max(1, std::min(g.PPB, 64 / g.TY));
     g.planeChunks = (int)ceil_div(g.n[0], g.PPB);
     g.fwdTiles = (int64_t)g.planeChunks * g.tilesY * g.tilesX;
     // adjoint tiles and shift chunks
@@ -169,7 +171,9 @@ void plan_level(LevelGeom& g) {
     g.adjTilesY = (int)ceil_div(g.n[1], 32);
     g.adjTiles = g.n[0] * g.adjTilesY * g.adjTilesX;
     const int wy = 2 * g.P[1] + 1, wz = 2 * g.P[0] + 1;
-    int64_t want = std::max<int64_t>(1, ceil_div(target, g.adjTiles));
+    // at most 16 shift chunks: levels share one fused launch, so a small level does not
+    // have to fill the GPU on its own, and the gradient assembly reads <= 16 partials
+    int64_t want = std::min<int64_t>(16, std::max<int64_t>(1, ceil_div(target, g.adjTiles)));
     int nYc = (int)std::min<int64_t>(wy, want);
     g.RY = (int)ceil_div(wy, nYc);
     if (g.RY > 16) g.RY = 16;
@@ -258,13 +262,13 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
     pl.tab_bytes = align_up(table_bound(pl.levels) + table_slack());
     pl.o_tab = o; o += pl.tab_bytes;
     pl.o_scal = o; o = align_up(o + sizeof(Scalars));
-    pl.o_pen = o; o = align_up(o + NPEN_BLOCKS * sizeof(double));
+    pl.o_pen = o; o = align_up(o + 3 * NPEN_BLOCKS * sizeof(double));
     pl.o_desc = o; o = align_up(o + (size_t)pl.Ktot * sizeof(float));
     for (int l = 0; l < pl.levels; ++l) {
         const LevelGeom& g = pl.g[l];
         if (l > 0) { pl.o_pyr[l] = o; o = align_up(o + (size_t)g.N * sizeof(float)); }
         pl.o_fwd[l] = o; o = align_up(o + (size_t)g.fwdTiles * g.Khalf * sizeof(float));
-        pl.o_gd[l] = o; o = align_up(o + 3 * (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T * sizeof(float));
+        pl.o_gd[l] = o; o = align_up(o + 4 * (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T * sizeof(float));
         pl.o_adj[l] = o; o = align_up(o + (size_t)g.nChunks * g.N * sizeof(float));
     }
     pl.bytes = o;
@@ -452,12 +456,13 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         std::vector<LossSeg> lvv;
         for (const Inst& x : in) {
             double* pen = reinterpret_cast<double*>(x.ws + x.pl->o_pen);
-            if (x.lp.bc_on) pv.push_back({x.field, x.pl->N1, pen, x.use_done ? &x.sc->done : nullptr});
+            pv.push_back({x.lp.bc_on ? x.field : nullptr, x.pl->N1, x.desc, x.target, x.pl->Ktot, pen,
+                          x.use_done ? &x.sc->done : nullptr});
             LossSeg ls{};
             ls.lp = x.lp;
             ls.desc = x.desc;
             ls.target = x.target;
-            ls.pen = x.lp.bc_on ? pen : nullptr;
+            ls.pen = pen;
             ls.sc = x.sc;
             ls.loss_out = x.loss_out;
             ls.history = x.history;
@@ -572,8 +577,8 @@ void run(const Prepared& P, cudaStream_t s) {
         launch_fwd_reduce(P.at<RedSeg>(P.red.off), P.red.nseg, P.red.blocks, s);
     }
     if (P.flags & F_LOSS) {
-        if (P.pen.nseg > 0) {
-            ProfScope ps("penalty", -1, s);
+        {
+            ProfScope ps("loss_stats", -1, s);
             launch_penalty(P.at<PenSeg>(P.pen.off), P.pen.nseg, s);
         }
         ProfScope ps("loss", -1, s);

@@ -98,51 +98,58 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
     return r;
 }
 
-// grid (NPEN_BLOCKS, instances): fixed-grid FP64 partial sums of the squared box excess.
-__global__ void penalty_kernel(const PenSeg* __restrict__ segs) {
+// grid (NPEN_BLOCKS, instances): fixed-grid FP64 partial sums of one loss evaluation --
+// sum (D - D_des)^2 and sum D_des^2 over the descriptor, and sum ex^2 of the box excess over
+// the field (when the penalty is on).  partials[3 b + {0, 1, 2}] for block b.
+__global__ void stats_kernel(const PenSeg* __restrict__ segs) {
     const PenSeg& sg = segs[blockIdx.y];
     if (sg.done != nullptr && *sg.done) return;
     __shared__ double sh[256];
-    double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sg.N; i += stride) {
-        const double e = (double)box_excess(sg.field[i]);
-        acc += e * e;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double r2 = 0.0, t2 = 0.0, e2 = 0.0;
+    for (int64_t k = i0; k < sg.K; k += stride) {
+        const double t = (double)sg.target[k];
+        const double r = (double)sg.desc[k] - t;
+        r2 += r * r;
+        t2 += t * t;
     }
-    const double t = block_sum_d(acc, sh);
-    if (threadIdx.x == 0) sg.partials[blockIdx.x] = t;
+    if (sg.field != nullptr)
+        for (int64_t i = i0; i < sg.N; i += stride) {
+            const double e = (double)box_excess(sg.field[i]);
+            e2 += e * e;
+        }
+    r2 = block_sum_d(r2, sh);
+    t2 = block_sum_d(t2, sh);
+    e2 = block_sum_d(e2, sh);
+    if (threadIdx.x == 0) {
+        sg.partials[3 * blockIdx.x + 0] = r2;
+        sg.partials[3 * blockIdx.x + 1] = t2;
+        sg.partials[3 * blockIdx.x + 2] = e2;
+    }
 }
 
 void launch_penalty(const PenSeg* segs, int nseg, cudaStream_t s) {
     if (nseg <= 0) return;
-    penalty_kernel<<<dim3(NPEN_BLOCKS, nseg), 256, 0, s>>>(segs);
+    stats_kernel<<<dim3(NPEN_BLOCKS, nseg), 256, 0, s>>>(segs);
 }
 
-// Single block: E, E^2, E_bc, lambda, L, rel_err and the gradient scalars; in a
-// reconstruction also the stopping test and the Adam step bookkeeping.
-__global__ void __launch_bounds__(1024) loss_kernel(const LossSeg* __restrict__ segs) {
+// One block per instance: sums the stats partials in a fixed tree, then E, E^2, E_bc,
+// lambda, L, rel_err and the gradient scalars; in a reconstruction also the stopping test
+// and the Adam step bookkeeping.
+__global__ void __launch_bounds__(NPEN_BLOCKS) loss_kernel(const LossSeg* __restrict__ segs) {
     const LossSeg& sg = segs[blockIdx.x];
     const LossParams lp = sg.lp;
-    const float* __restrict__ desc = sg.desc;
-    const float* __restrict__ target = sg.target;
     const double* __restrict__ pen = sg.pen;
     Scalars* sc = sg.sc;
     float* loss_out = sg.loss_out;
     float* history = sg.history;
     if (lp.recon && sc->done) return;
-    __shared__ double sh[1024];
-    double r2 = 0.0, t2 = 0.0;
-    for (int64_t k = threadIdx.x; k < lp.Ktot; k += blockDim.x) {
-        const double t = (double)target[k];
-        const double r = (double)desc[k] - t;
-        r2 += r * r;
-        t2 += t * t;
-    }
-    const double E2 = block_sum_d(r2, sh);
-    const double T2 = block_sum_d(t2, sh);
-    double pe = 0.0;
-    if (threadIdx.x < NPEN_BLOCKS && pen != nullptr) pe = pen[threadIdx.x];
-    const double ex2 = block_sum_d(pe, sh);
+    __shared__ double sh[NPEN_BLOCKS];
+    const int b = threadIdx.x;
+    const double E2 = block_sum_d(pen[3 * b + 0], sh);
+    const double T2 = block_sum_d(pen[3 * b + 1], sh);
+    const double ex2 = block_sum_d(pen[3 * b + 2], sh);
     if (threadIdx.x != 0) return;
     const double N = (double)lp.N;
     const double lam0 = lp.bc_on ? (double)lp.lambda0 : 0.0;
@@ -183,7 +190,7 @@ __global__ void __launch_bounds__(1024) loss_kernel(const LossSeg* __restrict__ 
 
 void launch_loss(const LossSeg* segs, int nseg, cudaStream_t s) {
     if (nseg <= 0) return;
-    loss_kernel<<<nseg, 1024, 0, s>>>(segs);
+    loss_kernel<<<nseg, NPEN_BLOCKS, 0, s>>>(segs);
 }
 
 // --------------------------------------------------------------------- gradient + Adam

@@ -134,9 +134,12 @@ struct RestrictSeg {
     int64_t blockStart;
 };
 struct PenSeg {
-    const float* field;
+    const float* field;      // null: no box penalty
     int64_t N;
-    double* partials;
+    const float* desc;
+    const float* target;
+    int64_t K;
+    double* partials;        // 3 x NPEN_BLOCKS
     const int* done;
 };
 struct LossSeg {

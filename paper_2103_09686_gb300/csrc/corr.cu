@@ -168,36 +168,45 @@ __device__ __forceinline__ void fwd_chunk(const float (&x)[T], const float (&y)[
 
 // acc[k] += sum_m G[m] H(s_km) with H(s) = s (1 - s) (c1 s + c3), written with the
 // per-shift coefficients A = -c1 G, B = (c1 - c3) G, C = c3 G as  s (C + s (B + A s)).
+// Shared-memory coefficient layout per block of 8 shifts: for mp = 0..3 the two quads
+// (A, B, C, 0) of shifts mp and mp + 4, i.e. 32 floats.
 template <int MODE>
-__device__ __forceinline__ void adj_chunk(const float (&x)[T], const float (&y)[2 * T], const float (&A)[T],
-                                          const float (&B)[T], const float (&C)[T], float (&acc)[T]) {
+__device__ __forceinline__ void adj_chunk(const float (&x)[T], const float (&y)[2 * T], const float* gq,
+                                          float (&acc)[T]) {
+    // all 24 coefficients of the 8 shifts live in registers for the 8 positions
+    float4 ca[T / 2], cb[T / 2];
+#pragma unroll
+    for (int mp = 0; mp < T / 2; ++mp) {
+        ca[mp] = *reinterpret_cast<const float4*>(gq + 8 * mp);
+        cb[mp] = *reinterpret_cast<const float4*>(gq + 8 * mp + 4);
+    }
 #pragma unroll
     for (int k = 0; k < T; ++k) {
-        if (MODE == MODE_FAST) {
 #pragma unroll
-            for (int m = 0; m < T / 2; ++m) {
-                const float da = fmaf(x[k], y[k + m], 1.0f);
-                const float db = fmaf(x[k], y[k + m + T / 2], 1.0f);
+        for (int mp = 0; mp < T / 2; ++mp) {
+            if (MODE == MODE_FAST) {
+                const float da = fmaf(x[k], y[k + mp], 1.0f);
+                const float db = fmaf(x[k], y[k + mp + T / 2], 1.0f);
                 const float r = rcp_approx(da * db);
                 const float sa = db * r, sb = da * r;
-                float qa = fmaf(A[m], sa, B[m]);
-                qa = fmaf(qa, sa, C[m]);
+                float qa = fmaf(ca[mp].x, sa, ca[mp].y);
+                qa = fmaf(qa, sa, ca[mp].z);
                 acc[k] = fmaf(qa, sa, acc[k]);
-                float qb = fmaf(A[m + T / 2], sb, B[m + T / 2]);
-                qb = fmaf(qb, sb, C[m + T / 2]);
+                float qb = fmaf(cb[mp].x, sb, cb[mp].y);
+                qb = fmaf(qb, sb, cb[mp].z);
                 acc[k] = fmaf(qb, sb, acc[k]);
-            }
-        } else {
-#pragma unroll
-            for (int m = 0; m < T; ++m) {
-                if (MODE == MODE_IDENT) {
-                    acc[k] = fmaf(A[m], x[k] + y[k + m], acc[k]);
-                } else {
-                    const float s = rcp_approx(ex2_approx(x[k] - y[k + m]) + 1.0f);
-                    float q = fmaf(A[m], s, B[m]);
-                    q = fmaf(q, s, C[m]);
-                    acc[k] = fmaf(q, s, acc[k]);
-                }
+            } else if (MODE == MODE_IDENT) {
+                acc[k] = fmaf(ca[mp].x, x[k] + y[k + mp], acc[k]);
+                acc[k] = fmaf(cb[mp].x, x[k] + y[k + mp + T / 2], acc[k]);
+            } else {
+                const float sa = rcp_approx(ex2_approx(x[k] - y[k + mp]) + 1.0f);
+                const float sb = rcp_approx(ex2_approx(x[k] - y[k + mp + T / 2]) + 1.0f);
+                float qa = fmaf(ca[mp].x, sa, ca[mp].y);
+                qa = fmaf(qa, sa, ca[mp].z);
+                acc[k] = fmaf(qa, sa, acc[k]);
+                float qb = fmaf(cb[mp].x, sb, cb[mp].y);
+                qb = fmaf(qb, sb, cb[mp].z);
+                acc[k] = fmaf(qb, sb, acc[k]);
             }
         }
     }
@@ -220,9 +229,11 @@ __device__ __forceinline__ void load16(const float* p, float (&v)[2 * T]) {
 
 // ------------------------------------------------------------------------- forward
 
+// One plane of the block's tile; row sums (<= 32 terms) are added to the block sums, which
+// hold at most 64 row sums (plans keep TY x planes-per-block <= 64).
 template <int MODE>
 __device__ __forceinline__ void fwd_plane(const float* xs, const float* ybase, int strideH, int rowsValid,
-                                          int chunksValid, float (&p1)[T], float (&p2)[T]) {
+                                          int chunksValid, float (&t1)[T], float (&t2)[T]) {
     for (int iy = 0; iy < rowsValid; ++iy) {
         float r1[T], r2[T];
 #pragma unroll
@@ -237,12 +248,12 @@ __device__ __forceinline__ void fwd_plane(const float* xs, const float* ybase, i
             fwd_chunk<MODE>(x, y, r1, r2);
         }
 #pragma unroll
-        for (int m = 0; m < T; ++m) { p1[m] += r1[m]; p2[m] += r2[m]; }
+        for (int m = 0; m < T; ++m) { t1[m] += r1[m]; t2[m] += r2[m]; }
     }
 }
 
 template <bool IDENT>
-__global__ void __launch_bounds__(FWD_THREADS)
+__global__ void __launch_bounds__(FWD_THREADS, 5)
 corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
     const FwdSeg& sg = segs[si];
@@ -337,14 +348,9 @@ corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
             }
         }
         __syncthreads();
-        float p1[T], p2[T];
-#pragma unroll
-        for (int m = 0; m < T; ++m) { p1[m] = 0.f; p2[m] = 0.f; }
-        if (IDENT) fwd_plane<MODE_IDENT>(xs, ybase, sh.strideH, rowsValid, chunksValid, p1, p2);
-        else if (slow) fwd_plane<MODE_SLOW>(xs, ybase, sh.strideH, rowsValid, chunksValid, p1, p2);
-        else fwd_plane<MODE_FAST>(xs, ybase, sh.strideH, rowsValid, chunksValid, p1, p2);
-#pragma unroll
-        for (int m = 0; m < T; ++m) { t1[m] += p1[m]; t2[m] += p2[m]; }
+        if (IDENT) fwd_plane<MODE_IDENT>(xs, ybase, sh.strideH, rowsValid, chunksValid, t1, t2);
+        else if (slow) fwd_plane<MODE_SLOW>(xs, ybase, sh.strideH, rowsValid, chunksValid, t1, t2);
+        else fwd_plane<MODE_FAST>(xs, ybase, sh.strideH, rowsValid, chunksValid, t1, t2);
     }
 
     if (!gvalid) return;
@@ -374,10 +380,16 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedSeg* __restric
     __shared__ double sh[8][RED_K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k = ((int64_t)blockIdx.x - sg.blockStart) * RED_K + lane;
-    double s = 0.0;
+    // compensated (Kahan) FP32 sum over this warp's tiles, then an FP64 sum of the 8 warps
+    float sum = 0.f, comp = 0.f;
     if (k < Khalf)
-        for (int64_t t = warp; t < tiles; t += 8) s += (double)sg.partial[t * Khalf + k];
-    sh[warp][lane] = s;
+        for (int64_t t = warp; t < tiles; t += 8) {
+            const float y = sg.partial[t * Khalf + k] - comp;
+            const float u = sum + y;
+            comp = (u - sum) - y;
+            sum = u;
+        }
+    sh[warp][lane] = (double)sum - (double)comp;
     __syncthreads();
     if (warp == 0 && k < Khalf) {
         double tot = 0.0;
@@ -389,26 +401,22 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedSeg* __restric
 // ------------------------------------------------------------------------- adjoint
 
 template <int MODE>
-__device__ __forceinline__ void adj_rows(const float* ys, const float* Gs, int strideH, int WB, int NB, int ryN,
-                                         int lane, int strip, const float (&x)[T], float (&acc)[T]) {
-    const int plane = ryN * WB;
+__device__ __forceinline__ void adj_rows(const float* ys, const float* Gs, int strideH, int NB, int ryN, int lane,
+                                         int strip, const float (&x)[T], float (&acc)[T]) {
     for (int r = 0; r < ryN; ++r) {
         const float* yrow = ys + (lane + r) * strideH + T * strip;
-        const float* grow = Gs + r * WB;
+        const float* grow = Gs + r * (NB * 4 * T);
 #pragma unroll 1
         for (int bb = 0; bb < NB; ++bb) {
-            float y[2 * T], A[T], B[T], C[T];
+            float y[2 * T];
             load16(yrow + T * bb, y);
-            load8(grow + T * bb, A);
-            load8(grow + plane + T * bb, B);
-            load8(grow + 2 * plane + T * bb, C);
-            adj_chunk<MODE>(x, y, A, B, C, acc);
+            adj_chunk<MODE>(x, y, grow + 4 * T * bb, acc);
         }
     }
 }
 
 template <bool IDENT>
-__global__ void __launch_bounds__(ADJ_THREADS)
+__global__ void __launch_bounds__(ADJ_THREADS, 4)
 corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
     const AdjSeg& sg = segs[si];
@@ -441,22 +449,21 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     float* Gs = smem + rowsH * strideH;
     const int64_t hx0 = x0 - g.P[2];
 
-    // own positions: row y0 + lane, columns x0 + 8 strip + k
+    // own positions: row y0 + lane, columns x0 + 8 strip + k (values reloaded per rz plane)
     const int64_t py = y0 + lane;
-    float mx[T];
+    const float* xrow = field + (z * n1 + (py < n1 ? py : 0)) * n2;
     bool xbad = false;
 #pragma unroll
     for (int k = 0; k < T; ++k) {
         const int64_t px = x0 + T * strip + k;
-        const bool valid = py < n1 && px < n2;
-        mx[k] = valid ? field[(z * n1 + py) * n2 + px] : 0.f;
-        xbad |= !(fabsf(tc.kappa * mx[k]) <= tc.lim) && !isnan(mx[k]);
+        const float v = (py < n1 && px < n2) ? xrow[px] : 0.f;
+        xbad |= !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
     }
     float acc[T];
 #pragma unroll
     for (int k = 0; k < T; ++k) acc[k] = 0.f;
 
-    const int ng = ryN * WB;
+    const int ng = ryN * 4 * WB;
     const int warp = threadIdx.x >> 5;
     constexpr int NW = ADJ_THREADS / 32;
     for (int rz = rzA; rz < rzB; ++rz) {
@@ -475,13 +482,9 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
                 while (gx >= n2) gx -= n2;
             }
         }
-        const int64_t gplane = (int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * WB;
-        const float* grow0 = Gd + ((int64_t)(rz + g.P[0]) * (2 * g.P[1] + 1) + (ryA + g.P[1])) * WB;
-        for (int i = threadIdx.x; i < ng; i += ADJ_THREADS) {
-            Gs[i] = grow0[i];
-            Gs[ng + i] = grow0[gplane + i];
-            Gs[2 * ng + i] = grow0[2 * gplane + i];
-        }
+        const float4* grow0 = reinterpret_cast<const float4*>(
+            Gd + ((int64_t)(rz + g.P[0]) * (2 * g.P[1] + 1) + (ryA + g.P[1])) * 4 * WB);
+        for (int i = threadIdx.x; i < ng / 4; i += ADJ_THREADS) reinterpret_cast<float4*>(Gs)[i] = grow0[i];
         const int slow = __syncthreads_or(bad);
         if (!IDENT && slow) {
             for (int r = warp; r < rowsH; r += NW) {
@@ -498,13 +501,15 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
         float x[T];
 #pragma unroll
         for (int k = 0; k < T; ++k) {
-            const float u = fmaf(-tc.kappa, mx[k], tc.cexp);
-            x[k] = IDENT ? 0.5f * mx[k] : (slow ? u : ex2_approx(u));
+            const int64_t px = x0 + T * strip + k;
+            const float v = (py < n1 && px < n2) ? xrow[px] : 0.f;
+            const float u = fmaf(-tc.kappa, v, tc.cexp);
+            x[k] = IDENT ? 0.5f * v : (slow ? u : ex2_approx(u));
         }
         __syncthreads();
-        if (IDENT) adj_rows<MODE_IDENT>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc);
-        else if (slow) adj_rows<MODE_SLOW>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc);
-        else adj_rows<MODE_FAST>(ys, Gs, strideH, WB, g.NB, ryN, lane, strip, x, acc);
+        if (IDENT) adj_rows<MODE_IDENT>(ys, Gs, strideH, g.NB, ryN, lane, strip, x, acc);
+        else if (slow) adj_rows<MODE_SLOW>(ys, Gs, strideH, g.NB, ryN, lane, strip, x, acc);
+        else adj_rows<MODE_FAST>(ys, Gs, strideH, g.NB, ryN, lane, strip, x, acc);
     }
 
     if (py >= n1) return;
@@ -520,11 +525,12 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
 //   Gd[rz][ry][col], rx = col - P2 (zero where rx > P2),
 //   value = scale * (src[k] - sub[k]) * (2 if r = 0),  k = canonical index of +-r,
 //   scale = weight * (gscale from the loss, or 1) * (c1 alpha / N_l, or 1 / N_l for f(x)=x).
-// Dense full-window coefficient grid of one level, three planes [A | B | C]:
+// Dense full-window coefficient grid of one level, in adjoint order:
 //   G(r) = scale * (src[k] - sub[k]) * (2 if r = 0),  k = canonical index of +-r,
 //   scale = weight * (gscale from the loss, or 1) * (c1 alpha / N_l, or 1 / N_l for f(x)=x),
-//   A = -c1 G, B = (c1 - c3) G, C = c3 G   (f(x) = x: A = G, B = C = 0),
-// zero where rx > P2 (padding of the last rx block).
+//   quad (A, B, C, 0) = (-c1 G, (c1 - c3) G, c3 G, 0)   (f(x) = x: (G, 0, 0, 0)),
+// zero where rx > P2 (padding of the last rx block).  Row (rz, ry) holds NB blocks of 8
+// shifts; a block stores for mp = 0..3 the quads of shifts mp and mp + 4 (32 floats).
 __global__ void gcoef_kernel(const GSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
     const GSeg& sg = segs[si];
@@ -535,8 +541,9 @@ __global__ void gcoef_kernel(const GSeg* __restrict__ segs, int nseg, ThreshCons
     const int64_t i = ((int64_t)blockIdx.x - sg.blockStart) * GCOEF_TH + threadIdx.x;
     if (i >= total) return;
     const int col = (int)(i % WB);
-    const int ryi = (int)((i / WB) % (2 * g.P[1] + 1));
-    const int rzi = (int)(i / ((int64_t)WB * (2 * g.P[1] + 1)));
+    const int64_t row = i / WB;
+    const int ryi = (int)(row % (2 * g.P[1] + 1));
+    const int rzi = (int)(row / (2 * g.P[1] + 1));
     const int rz = rzi - g.P[0], ry = ryi - g.P[1], rx = col - g.P[2];
     float v = 0.f;
     if (rx <= g.P[2]) {
@@ -547,15 +554,12 @@ __global__ void gcoef_kernel(const GSeg* __restrict__ segs, int nseg, ThreshCons
         if (rz == 0 && ry == 0 && rx == 0) sc *= 2.f;
         v = sc * d;
     }
-    if (tc.identity) {
-        sg.Gd[i] = v;
-        sg.Gd[total + i] = 0.f;
-        sg.Gd[2 * total + i] = 0.f;
-    } else {
-        sg.Gd[i] = -tc.c1 * v;
-        sg.Gd[total + i] = (tc.c1 - tc.c3) * v;
-        sg.Gd[2 * total + i] = tc.c3 * v;
-    }
+    const int b = col / T, m = col % T;
+    float4 q;
+    if (tc.identity) q = make_float4(v, 0.f, 0.f, 0.f);
+    else q = make_float4(-tc.c1 * v, (tc.c1 - tc.c3) * v, tc.c3 * v, 0.f);
+    float4* dst = reinterpret_cast<float4*>(sg.Gd + (row * g.NB + b) * (4 * T)) + (2 * (m % (T / 2)) + m / (T / 2));
+    *dst = q;
 }
 
 // ------------------------------------------------------------------------- launchers
@@ -589,7 +593,7 @@ size_t adj_smem_bytes(const LevelGeom& g) {
     const int WB = g.NB * T;
     const int rowsH = 32 + g.RY - 1;
     const int colsH = WB + 5 * T;
-    return (size_t)(rowsH * stride_4mod32(colsH) + 3 * g.RY * WB) * sizeof(float);
+    return (size_t)(rowsH * stride_4mod32(colsH) + 4 * g.RY * WB) * sizeof(float);
 }
 
 void launch_corr_adj(const AdjSeg* segs, int nseg, int64_t blocks, size_t smem, const ThreshConst& tc,
