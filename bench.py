@@ -43,7 +43,26 @@ WORKLOADS = {
                       desc="3D 128^3 GRF(l=6/6/12, vf=0.25), window +-24, 2 levels (128,64), one Adam iteration"),
     "grf64": dict(shape=(64, 64), window=(16, 16), levels=1,
                   desc="2D 64x64 GRF(l=4, vf=0.30), window +-16, 1 level, one Adam iteration"),
+    "batch256": dict(shape=None, window=None, levels=1, count=256,
+                     desc="256 independent 2D instances, sizes uniform over {64,128,256,512}^2, GRF vf U[0.1,0.5], "
+                          "windows U{16..64} capped at n/2, 1 level; one fused batched Adam iteration per step"),
 }
+
+
+def batch_instances(count: int, seed: int):
+    """(shape, window, target) of the mixed-size batch (seeds 4000 + instance)."""
+    out = []
+    for tgt, P, _ in synthetic.batch_instances(count, seed):
+        out.append((tgt.shape, (P, P), tgt))
+    return out
+
+
+def make_instances(name: str, rank: int):
+    """List of (shape, window, levels, target) for one rank."""
+    wl = WORKLOADS[name]
+    if wl.get("count"):
+        return [(sh, w, wl["levels"], t) for sh, w, t in batch_instances(wl["count"], 4000 + 1000 * rank)]
+    return [(wl["shape"], wl["window"], wl["levels"], make_target(name, rank))]
 
 
 def make_target(name: str, seed_base: int) -> np.ndarray:
@@ -177,13 +196,14 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     wl = WORKLOADS[args.workload]
-    shape, window, levels = wl["shape"], wl["window"], wl["levels"]
-    units = units_per_step(shape, window, levels)
+    insts = make_instances(args.workload, rank)
+    units = sum(units_per_step(sh, w, lev) for sh, w, lev, _ in insts)
+    big = max(insts, key=lambda x: int(np.prod(x[0])) * int(np.prod([2 * q + 1 for q in x[1]])))
 
     if args.impl == "reference":
         if rank != 0:
             return 0
-        target = make_target(args.workload, 0)
+        shape, window, levels, target = big
         field = synthetic.uniform_field(shape, seed=1)
         per_step = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
         vals = []
@@ -213,28 +233,39 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    # inputs: one independent instance per rank (weak scaling, no data-path collective)
-    target = make_target(args.workload, rank)
-    p = dm.Params(shape=shape, window=window, levels=levels)
+    # inputs: this rank's own instances (weak scaling, no data-path collective)
+    params = [dm.Params(shape=sh, window=w, levels=lev) for sh, w, lev, _ in insts]
+    count = len(params)
+    batched = count > 1
     opts = dm.ReconOpts(lr=1e-2)
-    ws = dm.workspace(p, dev)
-    t_dev = torch.tensor(target, dtype=torch.float32, device=dev)
-    d_des = dm.descriptor(t_dev, p, ws)
-    field0 = torch.tensor(synthetic.uniform_field(shape, seed=7 + rank), dtype=torch.float32, device=dev)
-    field = field0.clone()
-    m = torch.zeros_like(field)
-    v = torch.zeros_like(field)
-    loss = torch.empty(6, dtype=torch.float32, device=dev)
+    ws = dm.batch_workspace(params, dev) if batched else dm.workspace(params[0], dev)
+    targets = [torch.tensor(t, dtype=torch.float32, device=dev) for _, _, _, t in insts]
+    d_des = [torch.empty(dm.dmcr_descriptor_length(p), dtype=torch.float32, device=dev) for p in params]
+    if batched:
+        dm.dmcr_descriptor_batched(params, targets, d_des, ws)
+    else:
+        dm.dmcr_descriptor(params[0], targets[0], d_des[0], ws)
+    fields0 = [torch.tensor(synthetic.uniform_field(sh, seed=7 + rank + 7919 * i), dtype=torch.float32, device=dev)
+               for i, (sh, _, _, _) in enumerate(insts)]
+    fields = [f.clone() for f in fields0]
+    ms = [torch.zeros_like(f) for f in fields]
+    vs = [torch.zeros_like(f) for f in fields]
+    loss = torch.empty(6 * count, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > 129 MB L2
-    step = 0
+    steps = [0] * count
     stream = torch.cuda.current_stream()
+
+    def one_step(tg, fl, st):
+        if batched:
+            return dm.dmcr_adam_step_batched(params, opts, tg, fl, ms, vs, st, loss, ws)
+        return [dm.dmcr_adam_step(params[0], opts, tg[0], fl[0], ms[0], vs[0], st[0], loss, ws)]
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
     for _ in range(args.warmup):
-        step = dm.dmcr_adam_step(p, opts, d_des, field, m, v, step, loss, ws)
+        steps = one_step(d_des, fields, steps)
     torch.cuda.synchronize()
 
     # ---- timed region: device-resident inputs, L2 flushed before every step
@@ -248,7 +279,7 @@ def main():
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        step = dm.dmcr_adam_step(p, opts, d_des, field, m, v, step, loss, ws)
+        steps = one_step(d_des, fields, steps)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -262,24 +293,29 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
     value = units * args.steps * world / total_s
-    loss_h = loss.cpu().numpy().tolist()
+    loss_h = loss[:6].cpu().numpy().tolist()
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the region
-    h_field = torch.tensor(synthetic.uniform_field(shape, seed=7 + rank), dtype=torch.float32).pin_memory()
-    h_target = d_des.cpu().pin_memory()
-    h_loss = torch.empty(6, dtype=torch.float32).pin_memory()
-    e2e_steps = max(20, args.steps // 4)
-    d_field = torch.empty_like(field)
-    d_t = torch.empty_like(d_des)
-    m.zero_(); v.zero_()
-    estep = 0
+    h_fields = [f.cpu().pin_memory() for f in fields0]
+    h_targets = [d.cpu().pin_memory() for d in d_des]
+    h_loss = torch.empty(6 * count, dtype=torch.float32).pin_memory()
+    e2e_steps = max(10, args.steps // 4)
+    d_fields = [torch.empty_like(f) for f in fields]
+    d_t = [torch.empty_like(d) for d in d_des]
+    for m in ms:
+        m.zero_()
+    for v in vs:
+        v.zero_()
+    esteps = [0] * count
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        d_field.copy_(h_field, non_blocking=True)
-        d_t.copy_(h_target, non_blocking=True)
-        estep = dm.dmcr_adam_step(p, opts, d_t, d_field, m, v, estep, loss, ws)
+        for a, b in zip(d_fields, h_fields):
+            a.copy_(b, non_blocking=True)
+        for a, b in zip(d_t, h_targets):
+            a.copy_(b, non_blocking=True)
+        esteps = one_step(d_t, d_fields, esteps)
         h_loss.copy_(loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0
@@ -289,21 +325,19 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_value = units * e2e_steps * world / e2e_s
-    h2d = h_field.numel() * 4 + h_target.numel() * 4
+    h2d = sum(h.numel() * 4 for h in h_fields) + sum(h.numel() * 4 for h in h_targets)
     d2h = h_loss.numel() * 4
 
     # ---- roofline of the dominant kernel (largest summed duration in the timed region);
-    # the correlation kernels are one fused launch over all levels
+    # the correlation kernels are one fused launch over all levels (and instances)
     name, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
-    sizes = level_sizes(shape, levels)
-    kfull = int(np.prod([2 * q + 1 for q in window]))
-    khalf = (kfull + 1) // 2
-    if name.startswith("corr_adj"):
-        pairs = sum(sizes) * kfull
-    elif name.startswith("corr_fwd"):
-        pairs = sum(sizes) * khalf
-    else:
-        pairs = None
+    pairs_adj = pairs_fwd = 0
+    for sh, w, lev, _ in insts:
+        kfull = int(np.prod([2 * q + 1 for q in w]))
+        nsum = sum(level_sizes(sh, lev))
+        pairs_adj += nsum * kfull
+        pairs_fwd += nsum * ((kfull + 1) // 2)
+    pairs = pairs_adj if name.startswith("corr_adj") else (pairs_fwd if name.startswith("corr_fwd") else None)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = sm_count * MUFU_RCP_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9      # Gpair/s
@@ -320,16 +354,18 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v_cpu, sample = oracle_sample(shape, window, levels, target, field0.cpu().numpy(), args.cpu_budget)
+        shape, window, levels, target = big
+        v_cpu, sample = oracle_sample(shape, window, levels, target, synthetic.uniform_field(shape, seed=7),
+                                      args.cpu_budget)
         cpu = {"value": v_cpu, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": sample}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": wl["desc"], "units_per_step": units,
+                "config": {"workload": wl["desc"], "instances_per_gpu": count, "units_per_step": units,
                            "l2": "flushed before every timed step (256 MB write)",
-                           "parallelism": "independent instance per GPU" if world > 1 else "single GPU"},
+                           "parallelism": "independent instances per GPU" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
