@@ -57,6 +57,57 @@ def batch_instances(count: int, seed: int):
     return out
 
 
+def serve_jobs(n_jobs: int, rate: float, seed: int, dm, serve):
+    """The served workload: Poisson arrivals; 2-D GRF targets n in {128, 256, 512} (window
+    +-16, levels down to a 64^2 coarsest level, l = n/32) and 3-D 64^3 targets (window +-8,
+    2 levels, l = 2), vf ~ U[0.1, 0.5]; every job runs to rel_err < 1e-3 (tested every 10
+    iterations) or 5000 iterations."""
+    def make(i, rng):
+        if rng.random() < 1.0 / 6.0:
+            n, shape, win, lev, lr = 64, (64, 64, 64), (8, 8, 8), 2, 3e-3
+            tgt = synthetic.target_3d(64, seed + i, (2.0, 2.0, 2.0), float(rng.uniform(0.1, 0.5)))
+        else:
+            n = int(rng.choice([128, 256, 512]))
+            shape, win, lev, lr = (n, n), (16, 16), int(np.log2(n // 64)) + 1, 1e-2
+            tgt = synthetic.target_2d_grf(n, n / 32.0, float(rng.uniform(0.1, 0.5)), seed + i)
+        opts = dm.ReconOpts(max_iters=5000, lr=lr, tol_rel=1e-3, check_every=10, seed=seed + 7 * i)
+        return serve.Job(job_id=i, params=dm.Params(shape=shape, window=win, levels=lev), target=tgt, opts=opts)
+    return serve.poisson_trace(n_jobs, rate, seed, make)
+
+
+def main_serve(args):
+    """Served vs plain form on the same Poisson trace, equal S2 error target."""
+    import torch
+    import paper_2103_09686_gb300 as dm
+    from paper_2103_09686_gb300 import serve
+    dm.load()
+    sampler = ClockSampler(0)
+    jobs = serve_jobs(args.jobs, 200.0, 5000, dm, serve)
+    # warm the library and the allocator on a small job (not part of either run)
+    serve.reconstruct_alone(serve_jobs(1, 200.0, 4999, dm, serve)[0])
+    sampler.start()
+    served = serve.run_trace(jobs, "serve", max_slots=args.slots, tick_iters=50, class_caps=(1.5e8, 1e9, float("inf")))
+    units = 0
+    for j in jobs:
+        kfull = int(np.prod([2 * q + 1 for q in j.params.window]))
+        units += j.iters_done * sum(level_sizes(j.params.shape, j.params.levels)) * kfull
+    plain_jobs = serve_jobs(args.jobs, 200.0, 5000, dm, serve)
+    plain = serve.run_trace(plain_jobs, "plain")
+    clocks = sampler.stop()
+    same = all(np.array_equal(a.result, b.result) for a, b in zip(sorted(jobs, key=lambda j: j.job_id),
+                                                                 sorted(plain_jobs, key=lambda j: j.job_id)))
+    line = {"metric": "reconstructions/s", "value": served["reconstructions_per_s"], "unit": "reconstructions/s",
+            "n_gpus": 1, "steps": args.jobs, "warmup": 1, "ms_per_step": served["wall_s"] * 1e3 / args.jobs,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served Poisson trace (200 req/s), %d jobs: 2D GRF {128,256,512}^2 +-16 multigrid "
+                                   "to 64^2, 3D GRF 64^3 +-8 2 levels, to rel_err<1e-3; slots %d, tick 50 iterations"
+                                   % (args.jobs, args.slots)},
+            "served": served, "plain": plain, "results_identical_served_vs_plain": bool(same),
+            "voxel_shifts_per_s_served": units / served["wall_s"], "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def make_instances(name: str, rank: int):
     """List of (shape, window, levels, target) for one rank."""
     wl = WORKLOADS[name]
@@ -190,7 +241,12 @@ def main():
     ap.add_argument("--workload", default="grf512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=16.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--serve", action="store_true", help="served vs plain reconstructions on a Poisson trace")
+    ap.add_argument("--jobs", type=int, default=48)
+    ap.add_argument("--slots", type=int, default=64)
     args = ap.parse_args()
+    if args.serve:
+        return main_serve(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -183,7 +183,8 @@ dmcr_status dmcr_init_uniform(float* field, int64_t count, uint64_t seed, void* 
  *   state: Adam moments (device) and step count (host), updated for resume.
  *   history: max_iters * 3 floats (device: E, L, rel_err per iteration) or NULL.
  *   SYNCHRONOUS: returns after the run, with `report` (host) filled in; report.loss is the
- *   loss of the returned field.
+ *   loss of the returned field.  The graph runs on a private stream created with the
+ *   priority of `stream` (so a high-priority caller stream keeps its priority).
  */
 dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* opts,
                              const float* target_desc, float* field_inout, dmcr_adam_state* state,

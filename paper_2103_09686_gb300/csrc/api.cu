@@ -709,7 +709,14 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
     dmcr_status st = DMCR_OK;
     std::vector<Scalars> hs(count);
     do {
-        if ((st = cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate"))) break;
+        // the captured graph runs on a private stream with the caller stream's priority
+        int prio = 0;
+        if (cudaStreamGetPriority(caller, &prio) != cudaSuccess) {
+            cudaGetLastError();
+            prio = 0;
+        }
+        if ((st = cuda_check(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio), "cudaStreamCreate")))
+            break;
         if ((st = cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate"))) break;
         if ((st = cuda_check(cudaEventRecord(ev, caller), "cudaEventRecord"))) break;
         if ((st = cuda_check(cudaStreamWaitEvent(s, ev, 0), "cudaStreamWaitEvent"))) break;
