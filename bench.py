@@ -108,6 +108,45 @@ def main_serve(args):
     return 0
 
 
+def main_crossover(args):
+    """Identity threshold (f(x) = x): descriptor + gradient (dmcr_loss_grad) time of the
+    direct kernels vs the FFT path over the window P per axis, on 64^3 and 128^3 (one
+    level); CUDA events, median of 5 after 2 warm-ups."""
+    import torch
+    import paper_2103_09686_gb300 as dm
+    dm.load()
+    out = {"metric": "direct vs FFT crossover (identity threshold, descriptor+gradient)", "unit": "ms", "sizes": {}}
+    for n in (64, 128):
+        rows = []
+        M = torch.tensor(synthetic.uniform_field((n, n, n), 11), dtype=torch.float32, device="cuda")
+        T = torch.tensor(synthetic.target_3d(n, 12, (3.0, 3.0, 3.0), 0.3), dtype=torch.float32, device="cuda")
+        for P in (1, 2, 3, 4, 6, 8, 10, 12, 16, 20, 24):
+            if 2 * P > n:
+                continue
+            row = {"P": P}
+            for path, key in ((dm.DMCR_PATH_DIRECT, "direct_ms"), (dm.DMCR_PATH_FFT, "fft_ms")):
+                p = dm.Params(shape=(n, n, n), window=(P, P, P), threshold=dm.DMCR_IDENTITY, path=path)
+                ws = dm.workspace(p)
+                d = dm.descriptor(T, p, ws)
+                loss = torch.empty(6, device="cuda")
+                g = torch.empty_like(M)
+                times = []
+                for r in range(7):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    dm.dmcr_loss_grad(p, dm.LossOpts(), M, d, loss, g, None, ws)
+                    b.record()
+                    torch.cuda.synchronize()
+                    if r >= 2:
+                        times.append(a.elapsed_time(b))
+                row[key] = float(np.median(times))
+            rows.append(row)
+        cross = next((r["P"] for r in rows if r["fft_ms"] < r["direct_ms"]), None)
+        out["sizes"]["%d^3" % n] = {"rows": rows, "crossover_P": cross}
+    print(json.dumps(out))
+    return 0
+
+
 def make_instances(name: str, rank: int):
     """List of (shape, window, levels, target) for one rank."""
     wl = WORKLOADS[name]
@@ -244,9 +283,12 @@ def main():
     ap.add_argument("--serve", action="store_true", help="served vs plain reconstructions on a Poisson trace")
     ap.add_argument("--jobs", type=int, default=48)
     ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--crossover", action="store_true", help="identity threshold: direct vs FFT over the window")
     args = ap.parse_args()
     if args.serve:
         return main_serve(args)
+    if args.crossover:
+        return main_crossover(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -57,7 +57,13 @@ typedef enum {
 } dmcr_status;
 
 enum { DMCR_SOFT = 0, DMCR_IDENTITY = 1 };           /* threshold (Sec. 3.2.4; f(x)=x ablation of Sec. 4.1) */
-enum { DMCR_PATH_AUTO = 0, DMCR_PATH_DIRECT = 1 };   /* evaluation path */
+/* Evaluation path.  DIRECT: the shift-by-shift kernels (any threshold).  FFT: the
+ * autocorrelation by hand-written FP64 FFTs -- exact (up to rounding) for the identity
+ * threshold, and for the soft threshold of BINARY fields through the App. A mapping
+ * (descriptor only; use it to characterise binary targets).  Every level size must factor
+ * into 2, 3 and 5 and be <= 4096 per axis.  AUTO: DIRECT for the soft threshold; for the
+ * identity threshold the cheaper of the two per level (measured crossover). */
+enum { DMCR_PATH_AUTO = 0, DMCR_PATH_DIRECT = 1, DMCR_PATH_FFT = 2 };
 enum { DMCR_LOSS_NORM = 0, DMCR_LOSS_SQUARED = 1 };  /* L = E(1 + lambda0 E_bc)  |  E^2 (1 + lambda0 E_bc) */
 enum { DMCR_PROLONG_ADJOINT_ACCUMULATE = 0, DMCR_PROLONG_INJECT = 1 };
 enum { DMCR_INIT_CALLER = 0, DMCR_INIT_UNIFORM_SEEDED = 1 };

@@ -22,7 +22,7 @@ c_int, c_int64, c_float, c_void_p, c_uint64, c_size_t = (ctypes.c_int, ctypes.c_
 
 DMCR_OK, DMCR_EINVAL, DMCR_ENOMEM, DMCR_ECUDA, DMCR_ENONFINITE, DMCR_ETIMEOUT, DMCR_ENOTSUP = range(7)
 DMCR_SOFT, DMCR_IDENTITY = 0, 1
-DMCR_PATH_AUTO, DMCR_PATH_DIRECT = 0, 1
+DMCR_PATH_AUTO, DMCR_PATH_DIRECT, DMCR_PATH_FFT = 0, 1, 2
 DMCR_LOSS_NORM, DMCR_LOSS_SQUARED = 0, 1
 DMCR_PROLONG_ADJOINT_ACCUMULATE, DMCR_PROLONG_INJECT = 0, 1
 DMCR_INIT_CALLER, DMCR_INIT_UNIFORM_SEEDED = 0, 1

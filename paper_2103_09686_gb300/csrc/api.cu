@@ -133,8 +133,30 @@ struct Plan {
     // workspace offsets (bytes)
     size_t o_tab = 0, tab_bytes = 0, o_scal = 0, o_pen = 0, o_desc = 0, o_pyr[MAX_LEVELS] = {},
            o_fwd[MAX_LEVELS] = {}, o_gd[MAX_LEVELS] = {}, o_adj[MAX_LEVELS] = {};
+    // FFT levels: two complex FP64 grids, twiddles of the three axes, one FP64 scalar
+    size_t o_fx[MAX_LEVELS] = {}, o_fh[MAX_LEVELS] = {}, o_tw[MAX_LEVELS] = {}, o_dc[MAX_LEVELS] = {};
+    bool any_fft = false;
+    double fh2 = 0.0;          // f(1/2)^2 of the soft threshold (App. A mapping of the FFT path)
     size_t bytes = 0;
 };
+
+bool fft_size_ok(int64_t n) {
+    if (n < 1 || n > 4096) return false;
+    for (int r : {2, 3, 5})
+        while (n % r == 0) n /= r;
+    return n == 1;
+}
+
+// Identity threshold, AUTO path: the FFT when its estimated cost is lower.  Both costs are
+// fitted to GB300 measurements of descriptor + gradient on 64^3 and 128^3 (P = 1..24):
+// the FFT path is ~1.15 ns per grid point + 0.18 ms; the direct kernels ~0.18 ps per
+// voxel-shift + 0.6 ns per point + 0.1 ms.  Measured crossovers: P = 6 (64^3), P = 8 (128^3).
+bool fft_cheaper(const LevelGeom& g) {
+    const double kfull = (double)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * (2 * g.P[2] + 1);
+    const double t_direct = (double)g.N * kfull * 1.8e-13 + (double)g.N * 6e-10 + 1e-4;
+    const double t_fft = (double)g.N * 1.15e-9 + 1.8e-4;
+    return t_fft < t_direct;
+}
 
 // Upper bound of the segment-table bytes of one instance (every phase, 16-B aligned arrays).
 size_t table_bound(int levels) {
@@ -191,8 +213,8 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         return fail(DMCR_EINVAL, "levels must be in [1, %d] (got %d)", MAX_LEVELS, p->levels);
     if (p->threshold != DMCR_SOFT && p->threshold != DMCR_IDENTITY)
         return fail(DMCR_EINVAL, "unknown threshold %d", p->threshold);
-    if (p->path != DMCR_PATH_AUTO && p->path != DMCR_PATH_DIRECT)
-        return fail(DMCR_ENOTSUP, "path %d is not available in this build", p->path);
+    if (p->path != DMCR_PATH_AUTO && p->path != DMCR_PATH_DIRECT && p->path != DMCR_PATH_FFT)
+        return fail(DMCR_EINVAL, "unknown path %d", p->path);
     if (p->threshold == DMCR_SOFT && !(p->alpha > 0.f && isfinite(p->alpha)))
         return fail(DMCR_EINVAL, "alpha must be positive and finite");
     pl.ndim = p->ndim;
@@ -226,10 +248,22 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             if (2LL * P[a] > g.n[a])
                 return fail(DMCR_EINVAL, "window %d exceeds half the level-%d size %lld on axis %d", P[a], l + 1,
                             (long long)g.n[a], a - first);
-        if (p->threshold == DMCR_IDENTITY && g.n[2] % T != 0)
-            return fail(DMCR_ENOTSUP, "the identity threshold needs the last axis of every level divisible by 8");
         plan_level(g);
-        if (fwd_smem_bytes(g) > (size_t)MAX_DYN_SMEM || adj_smem_bytes(g) > (size_t)MAX_DYN_SMEM)
+        const bool fft_sizes = fft_size_ok(g.n[0]) && fft_size_ok(g.n[1]) && fft_size_ok(g.n[2]);
+        if (p->path == DMCR_PATH_FFT) {
+            if (!fft_sizes)
+                return fail(DMCR_ENOTSUP, "FFT path: level %d sizes must factor into 2, 3, 5 and be <= 4096", l + 1);
+            g.fft = 1;
+        } else if (p->path == DMCR_PATH_AUTO && p->threshold == DMCR_IDENTITY && fft_sizes && fft_cheaper(g)) {
+            g.fft = 1;
+        }
+        if (g.fft) {
+            g.nChunks = 1;
+            pl.any_fft = true;
+        }
+        if (!g.fft && p->threshold == DMCR_IDENTITY && g.n[2] % T != 0)
+            return fail(DMCR_ENOTSUP, "the direct identity path needs the last axis of every level divisible by 8");
+        if (!g.fft && (fwd_smem_bytes(g) > (size_t)MAX_DYN_SMEM || adj_smem_bytes(g) > (size_t)MAX_DYN_SMEM))
             return fail(DMCR_ENOTSUP, "window too large for the shared-memory tiles of this build");
         pl.w[l] = (float)pow(2.0, we * l);
         pl.off[l] = off;
@@ -256,6 +290,8 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         // fast path: every pair factor d = 1 + E'_x E_y stays <= 2^62, so the product of two
         // factors that share one reciprocal is finite
         tc.lim = (float)std::max(0.0, 0.5 * (61.0 - 0.75 * a * log2e));
+        const double fh = c1 / (1.0 + exp(0.25 * a)) - c1 * s0;
+        pl.fh2 = fh * fh;
     }
     // workspace layout
     size_t o = 0;
@@ -267,7 +303,14 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
     for (int l = 0; l < pl.levels; ++l) {
         const LevelGeom& g = pl.g[l];
         if (l > 0) { pl.o_pyr[l] = o; o = align_up(o + (size_t)g.N * sizeof(float)); }
-        pl.o_fwd[l] = o; o = align_up(o + (size_t)g.fwdTiles * g.Khalf * sizeof(float));
+        if (g.fft) {
+            pl.o_fx[l] = o; o = align_up(o + (size_t)g.N * 16);
+            pl.o_fh[l] = o; o = align_up(o + (size_t)g.N * 16);
+            pl.o_tw[l] = o; o = align_up(o + (size_t)(g.n[0] + g.n[1] + g.n[2]) * 16);
+            pl.o_dc[l] = o; o = align_up(o + 16);
+        } else {
+            pl.o_fwd[l] = o; o = align_up(o + (size_t)g.fwdTiles * g.Khalf * sizeof(float));
+        }
         pl.o_gd[l] = o; o = align_up(o + 4 * (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T * sizeof(float));
         pl.o_adj[l] = o; o = align_up(o + (size_t)g.nChunks * g.N * sizeof(float));
     }
@@ -283,6 +326,7 @@ dmcr_status prepare_device() {
     std::lock_guard<std::mutex> lk(mu);
     if (std::find(ready.begin(), ready.end(), dev) != ready.end()) return DMCR_OK;
     set_kernel_attributes();
+    set_fft_attributes();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute");
     ready.push_back(dev);
@@ -357,6 +401,21 @@ struct Prepared {
     R fwd{0, 0, 0}, red{0, 0, 0}, pen{0, 0, 0}, loss{0, 0, 0}, gco{0, 0, 0}, adj{0, 0, 0}, fin{0, 0, 0},
         init{0, 0, 0};
     size_t smem_fwd = 0, smem_adj = 0;
+    struct FftJob {
+        LevelGeom g;
+        const float* field;
+        double2* X;
+        double2* H;
+        double2* tw;
+        double* dc;
+        float* desc;
+        float weight;
+        int mode;
+        double fh2;
+        const float* Gd;
+        float* part;
+    };
+    std::vector<FftJob> fftf, fftb;
     template <typename S>
     const S* at(size_t off) const { return reinterpret_cast<const S*>(tab + off); }
 };
@@ -368,6 +427,22 @@ size_t push(TableBuf& tb, const std::vector<S>& v) {
 
 bool same_thresh(const ThreshConst& a, const ThreshConst& b) {
     return a.identity == b.identity && a.kappa == b.kappa && a.cexp == b.cexp && a.c1 == b.c1 && a.c3 == b.c3;
+}
+
+Prepared::FftJob fft_job(const Inst& x, int l) {
+    const Plan& pl = *x.pl;
+    Prepared::FftJob j{};
+    j.g = pl.g[l];
+    j.field = x.lv[l];
+    j.X = reinterpret_cast<double2*>(x.ws + pl.o_fx[l]);
+    j.H = reinterpret_cast<double2*>(x.ws + pl.o_fh[l]);
+    j.tw = reinterpret_cast<double2*>(x.ws + pl.o_tw[l]);
+    j.dc = reinterpret_cast<double*>(x.ws + pl.o_dc[l]);
+    j.desc = x.desc + pl.off[l];
+    j.weight = pl.w[l];
+    j.mode = pl.tc.identity ? 0 : 1;
+    j.fh2 = pl.fh2;
+    return j;
 }
 
 // Build every table of the requested phases; `tab`/`cap` is the device table region.
@@ -383,6 +458,11 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         for (int l = 1; l < x.pl->levels; ++l) x.lv[l] = reinterpret_cast<const float*>(x.ws + x.pl->o_pyr[l]);
     }
     const bool need_pyr = (flags & (F_FWD | F_BACK)) != 0;
+    if ((flags & (F_LOSS | F_BACK)) != 0)
+        for (const Inst& x : in)
+            if (x.pl->any_fft && !x.pl->tc.identity)
+                return fail(DMCR_ENOTSUP, "the FFT path of the soft threshold is exact for binary fields only: "
+                                          "descriptor calls only (characterise targets with it)");
     if (flags & F_INIT) {
         std::vector<InitSeg> v;
         for (const Inst& x : in)
@@ -420,6 +500,10 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         for (const Inst& x : in)
             for (int l = 0; l < x.pl->levels; ++l) {
                 const LevelGeom& g = x.pl->g[l];
+                if (g.fft) {
+                    P.fftf.push_back(fft_job(x, l));
+                    continue;
+                }
                 Item it{};
                 it.f.g = g;
                 it.f.field = x.lv[l];
@@ -502,6 +586,17 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
                 gs.blockStart = gb;
                 gb += ceil_div((int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T, GCOEF_TH);
                 gv.push_back(gs);
+                fa.parts[l] = part;
+                fa.nChunks[l] = g.nChunks;
+                fa.Nl[l] = g.N;
+                for (int a = 0; a < 3; ++a) fa.nl[l][a] = g.n[a];
+                if (g.fft) {
+                    Prepared::FftJob j = fft_job(x, l);
+                    j.Gd = Gd;
+                    j.part = part;
+                    P.fftb.push_back(j);
+                    continue;
+                }
                 Item it{};
                 it.a.g = g;
                 it.a.field = x.lv[l];
@@ -512,10 +607,6 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
                 it.blocks = g.adjTiles * g.nChunks;
                 items.push_back(it);
                 P.smem_adj = std::max(P.smem_adj, adj_smem_bytes(g));
-                fa.parts[l] = part;
-                fa.nChunks[l] = g.nChunks;
-                fa.Nl[l] = g.N;
-                for (int a = 0; a < 3; ++a) fa.nl[l][a] = g.n[a];
             }
             const bool pen = !vjp && x.lp.bc_on;
             fa.field = pen ? x.field : nullptr;
@@ -553,6 +644,76 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
     return DMCR_OK;
 }
 
+// Axis passes of one grid (last axis first); the first forward pass may read the real field.
+void fft_grid(const Prepared::FftJob& j, double2* data, const float* real_in, int sign, cudaStream_t s) {
+    const double two_pi = 6.283185307179586476925;
+    for (int axis = 2; axis >= 0; --axis) {
+        const int len = (int)j.g.n[axis];
+        const int64_t tw_off = axis == 2 ? 0 : (axis == 1 ? j.g.n[2] : j.g.n[2] + j.g.n[1]);
+        if (len == 1) continue;
+        FftPass p{};
+        p.data = data;
+        p.real_in = real_in;
+        real_in = nullptr;
+        for (int a = 0; a < 3; ++a) p.n[a] = j.g.n[a];
+        p.axis = axis;
+        p.sign = sign;
+        p.len = len;
+        p.L = fft_lines_per_block(len);
+        int m = len;
+        p.nrad = 0;
+        while (m % 4 == 0) { p.rad[p.nrad++] = 4; m /= 4; }
+        while (m % 2 == 0) { p.rad[p.nrad++] = 2; m /= 2; }
+        while (m % 3 == 0) { p.rad[p.nrad++] = 3; m /= 3; }
+        while (m % 5 == 0) { p.rad[p.nrad++] = 5; m /= 5; }
+        p.tw = j.tw + tw_off;
+        for (int t = 0; t < 3; ++t) p.om3[t] = make_double2(cos(two_pi * t / 3), -sin(two_pi * t / 3));
+        for (int t = 0; t < 5; ++t) p.om5[t] = make_double2(cos(two_pi * t / 5), -sin(two_pi * t / 5));
+        launch_fft_pass(p, s);
+    }
+    if (real_in != nullptr) {
+        // a 1 x 1 x 1 grid has no pass: copy the value in through a trivial pass of length 1
+        FftPass p{};
+        p.data = data;
+        p.real_in = real_in;
+        for (int a = 0; a < 3; ++a) p.n[a] = j.g.n[a];
+        p.axis = 2;
+        p.sign = sign;
+        p.len = 1;
+        p.L = 1;
+        p.nrad = 0;
+        p.tw = j.tw;
+        launch_fft_pass(p, s);
+    }
+}
+
+void fft_twiddles(const Prepared::FftJob& j, cudaStream_t s) {
+    int64_t off = 0;
+    for (int axis = 2; axis >= 0; --axis) {
+        if (j.g.n[axis] > 1) launch_fft_twiddles(j.tw + off, (int)j.g.n[axis], s);
+        off += j.g.n[axis];
+    }
+}
+
+void fft_descriptor(const Prepared::FftJob& j, cudaStream_t s) {
+    fft_twiddles(j, s);
+    fft_grid(j, j.X, j.field, -1, s);
+    launch_fft_power(j.X, j.g.N, s);
+    fft_grid(j, j.X, nullptr, +1, s);
+    launch_fft_sample(j.g, j.X, j.weight, j.mode, j.fh2, j.desc, s);
+}
+
+void fft_vjp(const Prepared::FftJob& j, cudaStream_t s) {
+    fft_twiddles(j, s);
+    fft_grid(j, j.X, j.field, -1, s);
+    launch_fft_embed(j.g, j.Gd, j.H, s);
+    fft_grid(j, j.H, nullptr, -1, s);
+    launch_fft_dc(j.H, j.dc, s);
+    launch_fft_xcorr(j.X, j.H, j.g.N, s);
+    fft_grid(j, j.H, nullptr, +1, s);
+    launch_fft_vjp_combine(j.g.N, j.field, j.H, j.dc, j.part, s);
+}
+
 void upload(const Prepared& P, cudaStream_t s) {
     if (P.tb.h.empty()) return;
     ProfScope ps("tables", -1, s);
@@ -573,8 +734,14 @@ void run(const Prepared& P, cudaStream_t s) {
             ProfScope ps("corr_fwd", -1, s);
             launch_corr_fwd(P.at<FwdSeg>(P.fwd.off), P.fwd.nseg, P.fwd.blocks, P.smem_fwd, P.tc, s);
         }
-        ProfScope ps("fwd_reduce", -1, s);
-        launch_fwd_reduce(P.at<RedSeg>(P.red.off), P.red.nseg, P.red.blocks, s);
+        {
+            ProfScope ps("fwd_reduce", -1, s);
+            launch_fwd_reduce(P.at<RedSeg>(P.red.off), P.red.nseg, P.red.blocks, s);
+        }
+        if (!P.fftf.empty()) {
+            ProfScope ps("fft_descriptor", -1, s);
+            for (const Prepared::FftJob& j : P.fftf) fft_descriptor(j, s);
+        }
     }
     if (P.flags & F_LOSS) {
         {
@@ -592,6 +759,10 @@ void run(const Prepared& P, cudaStream_t s) {
         {
             ProfScope ps("corr_adj", -1, s);
             launch_corr_adj(P.at<AdjSeg>(P.adj.off), P.adj.nseg, P.adj.blocks, P.smem_adj, P.tc, s);
+        }
+        if (!P.fftb.empty()) {
+            ProfScope ps("fft_vjp", -1, s);
+            for (const Prepared::FftJob& j : P.fftb) fft_vjp(j, s);
         }
         ProfScope ps((P.flags & F_ADAM) ? "grad_adam" : "grad_assemble", -1, s);
         launch_final(P.at<FinalSeg>(P.fin.off), P.fin.nseg, P.fin.blocks, s);

@@ -32,6 +32,7 @@ struct LevelGeom {
     int64_t adjTiles;  // n[0] * adjTilesY * adjTilesX
     int nZc, nYc, RZ, RY;   // shift chunks over rz and ry
     int nChunks;
+    int fft;          // 1: this level runs on the FFT path (identity threshold / binary target)
 };
 
 // Soft-threshold constants in the product form used on the device:
@@ -162,6 +163,21 @@ struct InitSeg {
     double b1t, b2t;
 };
 
+// One mixed-radix Stockham pass over the lines of one axis (fft.cu).
+struct FftPass {
+    double2* data;            // complex grid, transformed in place
+    const float* real_in;     // non-null: read the real input from here instead of `data`
+    int64_t n[3];
+    int axis;                 // 0, 1, 2
+    int sign;                 // -1 forward, +1 inverse (unnormalised)
+    int len;                  // n[axis]
+    int L;                    // lines per block
+    int nrad;
+    int rad[16];
+    const double2* tw;        // tw[t] = exp(-2 pi i t / len)
+    double2 om3[3], om5[5];   // exp(-2 pi i t / 3), exp(-2 pi i t / 5)
+};
+
 // ---------------------------------------------------------------- launchers
 void launch_blob(const void* host, size_t bytes, void* dst, cudaStream_t s);
 void launch_restrict(const RestrictSeg* segs, int nseg, int64_t blocks, cudaStream_t s);
@@ -180,6 +196,19 @@ void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, cudaStream_t s
 void launch_init_uniform(float* field, int64_t count, uint64_t seed, cudaStream_t s);
 void launch_scalars_init(const InitSeg* segs, int nseg, cudaStream_t s);
 void set_kernel_attributes();
+void set_fft_attributes();
+size_t fft_smem_bytes(int len, int L);
+int fft_lines_per_block(int len);
+void launch_fft_pass(const FftPass& p, cudaStream_t s);
+void launch_fft_twiddles(double2* tw, int len, cudaStream_t s);
+void launch_fft_power(double2* X, int64_t N, cudaStream_t s);
+void launch_fft_xcorr(const double2* X, double2* H, int64_t N, cudaStream_t s);
+void launch_fft_sample(const LevelGeom& g, const double2* X, float weight, int mode, double fh2, float* desc,
+                       cudaStream_t s);
+void launch_fft_embed(const LevelGeom& g, const float* Gd, double2* H, cudaStream_t s);
+void launch_fft_dc(const double2* H, double* out, cudaStream_t s);
+void launch_fft_vjp_combine(int64_t N, const float* M, const double2* Z, const double* sumA, float* part,
+                            cudaStream_t s);
 size_t fwd_smem_bytes(const LevelGeom& g);
 size_t adj_smem_bytes(const LevelGeom& g);
 float gcoef_scale(const LevelGeom& g, const ThreshConst& tc, float weight);

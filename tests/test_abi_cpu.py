@@ -51,7 +51,8 @@ def test_version_and_lengths(lib):
     (dict(shape=(60, 64), window=(4, 4), levels=4), 1),    # 60 not divisible by 8
     (dict(shape=(64, 64), window=(4, 4), threshold=7), 1),
     (dict(shape=(64, 64), window=(4, 4), alpha=-1.0), 1),
-    (dict(shape=(64, 64), window=(4, 4), path=2), 6),
+    (dict(shape=(64, 64), window=(4, 4), path=3), 1),      # unknown path
+    (dict(shape=(14, 14), window=(3, 3), path=2), 6),      # FFT path: sizes must factor into 2, 3, 5
     (dict(shape=(64, 60), window=(4, 4), threshold=1), 6),  # identity needs n % 8 == 0
 ])
 def test_argument_validation(lib, kw, status):
