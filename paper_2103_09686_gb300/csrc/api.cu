@@ -193,12 +193,20 @@ void plan_level(LevelGeom& g) {
     g.adjTilesY = (int)ceil_div(g.n[1], 32);
     g.adjTiles = g.n[0] * g.adjTilesY * g.adjTilesX;
     const int wy = 2 * g.P[1] + 1, wz = 2 * g.P[0] + 1;
-    // at most 16 shift chunks: levels share one fused launch, so a small level does not
-    // have to fill the GPU on its own, and the gradient assembly reads <= 16 partials
-    int64_t want = std::min<int64_t>(16, std::max<int64_t>(1, ceil_div(target, g.adjTiles)));
+    // at most 32 shift chunks: levels share one fused launch, so a small level does not
+    // have to fill the GPU on its own, and the gradient assembly reads few partials; the ry
+    // rows per chunk are capped so that the halo + coefficient tile stays within 48 KB
+    // (4 CTAs of 128 threads per SM at 128 registers)
+    int64_t want = std::min<int64_t>(32, std::max<int64_t>(1, ceil_div(target, g.adjTiles)));
     int nYc = (int)std::min<int64_t>(wy, want);
     g.RY = (int)ceil_div(wy, nYc);
-    if (g.RY > 16) g.RY = 16;
+    int cap = 16;
+    while (cap > 1) {
+        g.RY = cap;
+        if (adj_smem_bytes(g) <= 48 * 1024) break;
+        --cap;
+    }
+    g.RY = std::min((int)ceil_div(wy, nYc), cap);
     g.nYc = (int)ceil_div(wy, g.RY);
     int nZc = (int)std::min<int64_t>(wz, ceil_div(want, g.nYc));
     g.RZ = (int)ceil_div(wz, nZc);
