@@ -39,6 +39,10 @@ ISSUE_PER_CLK_PER_SM = 128        # 4 schedulers x 32 lanes: thread-instructions
 # pairs share one reciprocal): forward 2 FFMA + FMUL + MUFU.RCP + 2 FMUL + 2 FADD + 2 FFMA per
 # 2 pairs; adjoint 2 FFMA + FMUL + MUFU.RCP + 2 FMUL + 6 FFMA per 2 pairs.
 INSTR_PER_PAIR = {"corr_fwd": 5.0, "corr_adj": 6.0}
+# DRAM bytes (read + write) per launch of the current kernels on the 512^2, +-64, 3-level
+# workload, from the ncu full-set capture summarised in profiles/corr_kernels_grf512_w64_L3.md
+# (set to None whenever the kernels change until they are captured again).
+NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2255360 + 0, ("grf512", "corr_fwd"): 1651968 + 225024}
 
 WORKLOADS = {
     "grf512": dict(shape=(512, 512), window=(64, 64), levels=3,
@@ -289,7 +293,17 @@ def main():
     ap.add_argument("--jobs", type=int, default=48)
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--crossover", action="store_true", help="identity threshold: direct vs FFT over the window")
+    ap.add_argument("--pipes", action="store_true", help="measured MUFU / FMA rates per SM per clock")
     args = ap.parse_args()
+    if args.pipes:
+        import ctypes
+        import paper_2103_09686_gb300 as dm
+        lib = dm.load()
+        r = (ctypes.c_double * 5)()
+        st = lib.dmcr_pipe_rates(r)
+        print(json.dumps({"metric": "pipe rates", "unit": "ops/SM/clk", "status": st,
+                          "rcp": r[0], "ex2": r[1], "tanh": r[2], "lg2": r[3], "ffma": r[4]}))
+        return 0
     if args.serve:
         return main_serve(args)
     if args.crossover:
@@ -451,7 +465,7 @@ def main():
         achieved = pairs * INSTR_PER_PAIR[kind] / (avg_ms / 1e3) / 1e12
         mufu_peak = sm_count * MUFU_RCP_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9          # Gpair/s at 1 rcp/pair
         roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Tinst/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get((args.workload, kind)),
                     "peak_basis": "issue slots: %d SMs x %d thread-instructions/clk x %.0f MHz (max SM clock); "
                                   "achieved = algorithmic pairs x %.0f instructions/pair / launch time"
                                   % (sm_count, ISSUE_PER_CLK_PER_SM, max_mhz, INSTR_PER_PAIR[kind]),

@@ -236,7 +236,9 @@ dmcr_status dmcr_adam_step_batched(int count, const dmcr_params* params, const d
  * Graph-captured reconstruction of every instance (opts, states, reports: host arrays of
  * count).  Instances stop independently on their own device flags (converged instances
  * cost nothing in later launches); the call returns when all have stopped.  SYNCHRONOUS.
- * report.loss is the loss of the returned field of that instance.
+ * report.loss is the loss of the returned field of that instance.  An instance whose loss
+ * becomes non-finite stops with report.status = DMCR_ENONFINITE (its field is left at the
+ * last finite iterate); the other instances are unaffected and the call returns DMCR_OK.
  */
 dmcr_status dmcr_reconstruct_batched(int count, const dmcr_params* params, const dmcr_recon_opts* opts,
                                      const float* const* targets, float* const* fields, dmcr_adam_state* states,
@@ -272,6 +274,15 @@ dmcr_status dmcr_profile_read(int index, char* name, int name_len, double* total
  */
 #define DMCR_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 dmcr_status dmcr_descriptor_noalloc(const dmcr_params* p, const float* field, float* desc, void* stream);
+
+/*
+ * dmcr_pipe_rates -- diagnostic: measured throughput, in operations per SM per clock, of
+ *   rates[0] MUFU reciprocal, [1] MUFU exp2, [2] MUFU tanh, [3] MUFU log2, [4] FP32 FMA
+ *   (independent chains at full occupancy, clock64-timed).  The roofline peaks of the
+ *   correlation kernels are derived from these unit rates and the SM count and clock.
+ *   SYNCHRONOUS; allocates a few bytes of device memory.  No counterpart in the paper.
+ */
+dmcr_status dmcr_pipe_rates(double rates[5]);
 
 #ifdef __cplusplus
 }

@@ -879,7 +879,7 @@ dmcr_status exec_batch(const BatchLayout& B, void* ws, std::vector<Inst>& in, un
 // Graph-captured reconstruction of every instance (each stops on its own device flag).
 dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, Scalars* scal_base,
                               const std::vector<int>& max_iters, int poll_every, dmcr_recon_report* reports,
-                              dmcr_adam_state* states, cudaStream_t caller) {
+                              dmcr_adam_state* states, cudaStream_t caller, bool per_instance_status) {
     const int count = (int)in.size();
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
@@ -936,7 +936,8 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
             for (int k = 0; k < DMCR_OUT_COUNT; ++k) r.loss[k] = hs[i].loss[k];
             r.status = hs[i].done == 2 ? DMCR_ENONFINITE : DMCR_OK;
             states[i].step = hs[i].adam_step;
-            if (hs[i].done == 2) st = fail(DMCR_ENONFINITE, "loss became non-finite in instance %d", i);
+            if (hs[i].done == 2 && !per_instance_status)
+                st = fail(DMCR_ENONFINITE, "loss became non-finite in instance %d", i);
         }
     } while (0);
     if (exec) cudaGraphExecDestroy(exec);
@@ -1128,7 +1129,7 @@ dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* o, con
     std::vector<Inst> in{single(pl, ws)};
     recon_inst(in[0], o, target_desc, field, state, history);
     const dmcr_status st = reconstruct_insts(in, table_region(pl, ws), pl.tab_bytes, in[0].sc, {o->max_iters},
-                                             o->check_every, report, state, s);
+                                             o->check_every, report, state, s, false);
     report->status = st;
     return st;
 }
@@ -1253,7 +1254,7 @@ dmcr_status dmcr_reconstruct_batched(int count, const dmcr_params* params, const
         if (opts[i].init == DMCR_INIT_UNIFORM_SEEDED) launch_init_uniform(fields[i], B.plans[i].N1, opts[i].seed, s);
     return reconstruct_insts(in, static_cast<char*>(ws) + B.o_tab, B.tab_bytes,
                              reinterpret_cast<Scalars*>(static_cast<char*>(ws) + B.o_scal), iters, poll, reports,
-                             states, s);
+                             states, s, true);
 }
 
 dmcr_status dmcr_profile_enable(int on) {

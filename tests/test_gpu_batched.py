@@ -100,3 +100,31 @@ def test_reconstruction_same_alone_and_in_the_mix(cuda_lib):
         assert rep["converged"] == reps[i]["converged"]
         assert torch.equal(f, fb[i]), i
         assert rep["rel_err"] == reps[i]["rel_err"]
+
+
+def test_nan_poisoned_instance_is_isolated(cuda_lib):
+    """A NaN-poisoned job stops with DMCR_ENONFINITE; the other jobs of the batch finish
+    exactly as they would alone, and the single-instance call reports the error."""
+    dm = cuda_lib
+    params, fields, targets = _mix(dm)
+    params, fields, targets = params[:3], fields[:3], targets[:3]
+    d_des = [dm.descriptor(t, p) for p, t in zip(params, targets)]
+    fields[1] = fields[1].clone()
+    fields[1].view(-1)[5] = float("nan")
+    opts = dm.ReconOpts(max_iters=30, lr=1e-2)
+    fb = [f.clone() for f in fields]
+    mb = [torch.zeros_like(f) for f in fields]
+    vb = [torch.zeros_like(f) for f in fields]
+    reps, steps = dm.dmcr_reconstruct_batched(params, opts, d_des, fb, mb, vb, [0, 0, 0])
+    assert reps[1]["status"] == 4 and steps[1] == 0
+    for i in (0, 2):
+        assert reps[i]["status"] == 0 and steps[i] == 30
+        f = fields[i].clone()
+        m = torch.zeros_like(f)
+        v = torch.zeros_like(f)
+        dm.dmcr_reconstruct(params[i], opts, d_des[i], f, m, v)
+        assert torch.equal(f, fb[i])
+    f = fields[1].clone()
+    with pytest.raises(dm.DmcrError) as e:
+        dm.dmcr_reconstruct(params[1], opts, d_des[1], f, torch.zeros_like(f), torch.zeros_like(f))
+    assert e.value.status == 4
