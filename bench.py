@@ -294,6 +294,7 @@ def main():
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--crossover", action="store_true", help="identity threshold: direct vs FFT over the window")
     ap.add_argument("--pipes", action="store_true", help="measured MUFU / FMA rates per SM per clock")
+    ap.add_argument("--tune", action="store_true", help="launch shapes from the autotuner (measured, cached)")
     args = ap.parse_args()
     if args.pipes:
         import ctypes
@@ -352,6 +353,9 @@ def main():
 
     # inputs: this rank's own instances (weak scaling, no data-path collective)
     params = [dm.Params(shape=sh, window=w, levels=lev) for sh, w, lev, _ in insts]
+    if args.tune:
+        from paper_2103_09686_gb300 import tune
+        params = [tune.tuned(p) for p in params]
     count = len(params)
     batched = count > 1
     opts = dm.ReconOpts(lr=1e-2)
@@ -488,6 +492,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl["desc"], "instances_per_gpu": count, "units_per_step": units,
                            "l2": "flushed before every timed step (256 MB write)",
+                           "launch_shapes": "autotuned %s" % sorted({tuple(p.tune) for p in params})
+                           if args.tune else "built-in plan",
                            "parallelism": "independent instances per GPU" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

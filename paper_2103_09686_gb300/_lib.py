@@ -31,7 +31,8 @@ OUT_NAMES = ("E", "E2", "Ebc", "lambda", "L", "rel_err")
 
 class dmcr_params(ctypes.Structure):
     _fields_ = [("ndim", c_int), ("n", c_int64 * 3), ("window", c_int * 3), ("levels", c_int),
-                ("threshold", c_int), ("alpha", c_float), ("level_weight_exp", c_float), ("path", c_int)]
+                ("threshold", c_int), ("alpha", c_float), ("level_weight_exp", c_float), ("path", c_int),
+                ("tune", c_int * 4)]
 
 
 class dmcr_loss_opts(ctypes.Structure):
@@ -150,6 +151,7 @@ class Params:
     alpha: float = 10.0
     level_weight_exp: float = -1.0
     path: int = DMCR_PATH_AUTO
+    tune: tuple = (0, 0, 0, 0)     # launch shape; 0 = built-in choice (see tune.py)
 
     @property
     def ndim(self) -> int:
@@ -167,6 +169,8 @@ class Params:
         p.alpha = float(self.alpha)
         p.level_weight_exp = float(self.level_weight_exp)
         p.path = int(self.path)
+        for i, t in enumerate(tuple(self.tune)[:4]):
+            p.tune[i] = int(t)
         return p
 
 

@@ -167,18 +167,37 @@ size_t table_slack() { return (size_t)(16 + MAX_LEVELS) * 16 + 256; }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-void plan_level(LevelGeom& g) {
+// Forward tile rows for the whole problem (all levels share one fused launch): the tallest
+// tile (fewest halo rows per output row) that still gives ~8 blocks per SM summed over levels.
+int forward_rows(const int64_t n[3], const int P[3], int levels, int ndim) {
+    const int64_t groups = ceil_div(
+        (int64_t)(P[1] + 1) * ceil_div(2 * P[2] + 1, T) + (int64_t)P[0] * (2 * P[1] + 1) * ceil_div(2 * P[2] + 1, T),
+        FWD_THREADS);
+    for (int TY = 32; TY > 8; TY /= 2) {
+        int64_t blocks = 0;
+        for (int l = 0; l < levels; ++l) {
+            const int64_t n0 = ndim == 2 ? 1 : n[0] >> l;
+            blocks += n0 * ceil_div(n[1] >> l, TY) * ceil_div(n[2] >> l, TX) * groups;
+        }
+        if (blocks >= 1216) return TY;
+    }
+    return 8;
+}
+
+// tune: {forward tile rows (8/16/32; 0 is taken as forward_rows()), adjoint ry rows per
+// chunk (0 = auto, else 1..16), adjoint chunk count limit (0 = auto, else 1..64)}
+void plan_level(LevelGeom& g, const int tune[4]) {
     g.N = g.n[0] * g.n[1] * g.n[2];
     g.NB = (int)ceil_div(2 * g.P[2] + 1, T);
     g.NG = (int64_t)(g.P[1] + 1) * g.NB + (int64_t)g.P[0] * (2 * g.P[1] + 1) * g.NB;
     g.Khalf = ((int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * (2 * g.P[2] + 1) + 1) / 2;
     g.NGT = g.NG * T;
     g.fwdGroupBlocks = (int)ceil_div(g.NG, FWD_THREADS);
-    // forward tiles: rows per tile and planes per block chosen for >= ~2400 blocks
-    const int64_t target = 2400;
+    // forward tiles: rows per tile from forward_rows(); planes per block chosen for
+    // >= ~2400 blocks
+    const int64_t target = 2400, rows_target = 1216;
     g.tilesX = (int)ceil_div(g.n[2], TX);
-    int TY = (int)std::min<int64_t>(32, g.n[1]);
-    while (TY > 8 && (int64_t)ceil_div(g.n[1], TY) * g.tilesX * g.fwdGroupBlocks * g.n[0] < target) TY /= 2;
+    const int TY = (int)std::min<int64_t>(tune[0], g.n[1]);
     g.TY = TY;
     g.tilesY = (int)ceil_div(g.n[1], TY);
     const int64_t perPlane = (int64_t)g.tilesY * g.tilesX * g.fwdGroupBlocks;
@@ -193,22 +212,24 @@ void plan_level(LevelGeom& g) {
     g.adjTilesY = (int)ceil_div(g.n[1], 32);
     g.adjTiles = g.n[0] * g.adjTilesY * g.adjTilesX;
     const int wy = 2 * g.P[1] + 1, wz = 2 * g.P[0] + 1;
-    // at most 32 shift chunks: levels share one fused launch, so a small level does not
-    // have to fill the GPU on its own, and the gradient assembly reads few partials; the ry
-    // rows per chunk are capped so that the halo + coefficient tile stays within 48 KB
-    // (4 CTAs of 128 threads per SM at 128 registers)
-    int64_t want = std::min<int64_t>(32, std::max<int64_t>(1, ceil_div(target, g.adjTiles)));
-    int nYc = (int)std::min<int64_t>(wy, want);
-    g.RY = (int)ceil_div(wy, nYc);
+    // shift chunks: enough for ~8 blocks per SM, at most 32 (levels share one fused launch,
+    // so a small level does not have to fill the GPU on its own, and the gradient assembly
+    // reads few partials).  A chunk's halo and coefficient loads are amortised over its
+    // RY x RZ shifts, so the split goes along z first and keeps the ry rows per chunk as
+    // many as the 48 KB tile allows (4 CTAs of 128 threads per SM at 128 registers).
+    const int64_t chunk_cap = tune[2] > 0 ? tune[2] : 32;
+    const int64_t want = std::min<int64_t>(chunk_cap, std::max<int64_t>(1, ceil_div(rows_target, g.adjTiles)));
     int cap = 16;
     while (cap > 1) {
         g.RY = cap;
         if (adj_smem_bytes(g) <= 48 * 1024) break;
         --cap;
     }
-    g.RY = std::min((int)ceil_div(wy, nYc), cap);
+    const int nZc = (int)std::min<int64_t>(wz, want);
+    g.RY = (int)std::min<int64_t>(ceil_div(wy, ceil_div(want, nZc)), cap);
+    if (tune[1] > 0) g.RY = std::min(tune[1], cap);
+    g.RY = std::min(g.RY, wy);
     g.nYc = (int)ceil_div(wy, g.RY);
-    int nZc = (int)std::min<int64_t>(wz, ceil_div(want, g.nYc));
     g.RZ = (int)ceil_div(wz, nZc);
     g.nZc = (int)ceil_div(wz, g.RZ);
     g.nChunks = g.nZc * g.nYc;
@@ -223,6 +244,9 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         return fail(DMCR_EINVAL, "unknown threshold %d", p->threshold);
     if (p->path != DMCR_PATH_AUTO && p->path != DMCR_PATH_DIRECT && p->path != DMCR_PATH_FFT)
         return fail(DMCR_EINVAL, "unknown path %d", p->path);
+    if (!(p->tune[0] == 0 || p->tune[0] == 8 || p->tune[0] == 16 || p->tune[0] == 32) || p->tune[1] < 0 ||
+        p->tune[1] > 16 || p->tune[2] < 0 || p->tune[2] > 64)
+        return fail(DMCR_EINVAL, "tune = {0|8|16|32, 0..16, 0..64, 0} expected");
     if (p->threshold == DMCR_SOFT && !(p->alpha > 0.f && isfinite(p->alpha)))
         return fail(DMCR_EINVAL, "alpha must be positive and finite");
     pl.ndim = p->ndim;
@@ -244,6 +268,8 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
     }
     if (n[0] * n[1] * n[2] > (1LL << 34)) return fail(DMCR_EINVAL, "field too large");
     const double we = p->level_weight_exp < 0.f ? p->ndim / 2.0 : (double)p->level_weight_exp;
+    int tune[4] = {p->tune[0], p->tune[1], p->tune[2], p->tune[3]};
+    if (tune[0] == 0) tune[0] = forward_rows(n, P, p->levels, p->ndim);
     int64_t off = 0;
     for (int l = 0; l < p->levels; ++l) {
         LevelGeom& g = pl.g[l];
@@ -256,7 +282,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             if (2LL * P[a] > g.n[a])
                 return fail(DMCR_EINVAL, "window %d exceeds half the level-%d size %lld on axis %d", P[a], l + 1,
                             (long long)g.n[a], a - first);
-        plan_level(g);
+        plan_level(g, tune);
         const bool fft_sizes = fft_size_ok(g.n[0]) && fft_size_ok(g.n[1]) && fft_size_ok(g.n[2]);
         if (p->path == DMCR_PATH_FFT) {
             if (!fft_sizes)

@@ -54,6 +54,7 @@ def test_version_and_lengths(lib):
     (dict(shape=(64, 64), window=(4, 4), path=3), 1),      # unknown path
     (dict(shape=(14, 14), window=(3, 3), path=2), 6),      # FFT path: sizes must factor into 2, 3, 5
     (dict(shape=(64, 60), window=(4, 4), threshold=1), 6),  # identity needs n % 8 == 0
+    (dict(shape=(64, 64), window=(4, 4), tune=(12, 0, 0, 0)), 1),   # forward tile rows must be 8/16/32
 ])
 def test_argument_validation(lib, kw, status):
     import paper_2103_09686_gb300 as dm
