@@ -79,8 +79,9 @@ typedef struct {
     float level_weight_exp;  /* w_l = 2^(level_weight_exp (l-1)); <0 selects ndim/2 (2^(l-1) in 2-D) */
     int path;                /* DMCR_PATH_AUTO, DMCR_PATH_DIRECT or DMCR_PATH_FFT */
     int tune[4];             /* launch shape (0 = built-in choice): forward tile rows {8,16,32},
-                                adjoint ry rows per shift chunk (1..16), adjoint chunk limit
-                                (1..64), reserved (0).  Results agree to rounding across shapes. */
+                                adjoint ry rows per shift chunk (1..16), adjoint chunk target
+                                limit (1..64), adjoint rx blocks of 8 shifts per chunk at most
+                                (1..32).  Results agree to rounding across shapes. */
 } dmcr_params;
 
 /* Loss options (Sec. 3.1).  lambda = lambda0 * E (NORM) or lambda0 * E^2 (SQUARED). */

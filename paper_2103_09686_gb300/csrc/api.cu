@@ -185,7 +185,8 @@ int forward_rows(const int64_t n[3], const int P[3], int levels, int ndim) {
 }
 
 // tune: {forward tile rows (8/16/32; 0 is taken as forward_rows()), adjoint ry rows per
-// chunk (0 = auto, else 1..16), adjoint chunk count limit (0 = auto, else 1..64)}
+// chunk (0 = auto, else 1..16), adjoint chunk target limit (0 = auto, else 1..64), adjoint rx
+// blocks of 8 shifts per chunk at most (0 = auto, else 1..32)}
 void plan_level(LevelGeom& g, const int tune[4]) {
     g.N = g.n[0] * g.n[1] * g.n[2];
     g.NB = (int)ceil_div(2 * g.P[2] + 1, T);
@@ -197,7 +198,7 @@ void plan_level(LevelGeom& g, const int tune[4]) {
     // >= ~2400 blocks
     const int64_t target = 2400, rows_target = 1216;
     g.tilesX = (int)ceil_div(g.n[2], TX);
-    const int TY = (int)std::min<int64_t>(tune[0], g.n[1]);
+    const int TY = (int)std::min<int64_t>(tune[0], g.n[1] + (g.n[1] & 1));   // whole row pairs
     g.TY = TY;
     g.tilesY = (int)ceil_div(g.n[1], TY);
     const int64_t perPlane = (int64_t)g.tilesY * g.tilesX * g.fwdGroupBlocks;
@@ -209,30 +210,36 @@ void plan_level(LevelGeom& g, const int tune[4]) {
     g.fwdTiles = (int64_t)g.planeChunks * g.tilesY * g.tilesX;
     // adjoint tiles and shift chunks
     g.adjTilesX = (int)ceil_div(g.n[2], TX);
-    g.adjTilesY = (int)ceil_div(g.n[1], 32);
+    g.adjTilesY = (int)ceil_div(g.n[1], ADJ_ROWS);
     g.adjTiles = g.n[0] * g.adjTilesY * g.adjTilesX;
     const int wy = 2 * g.P[1] + 1, wz = 2 * g.P[0] + 1;
-    // shift chunks: enough for ~8 blocks per SM, at most 32 (levels share one fused launch,
-    // so a small level does not have to fill the GPU on its own, and the gradient assembly
-    // reads few partials).  A chunk's halo and coefficient loads are amortised over its
-    // RY x RZ shifts, so the split goes along z first and keeps the ry rows per chunk as
-    // many as the 48 KB tile allows (4 CTAs of 128 threads per SM at 128 registers).
-    const int64_t chunk_cap = tune[2] > 0 ? tune[2] : 32;
-    const int64_t want = std::min<int64_t>(chunk_cap, std::max<int64_t>(1, ceil_div(rows_target, g.adjTiles)));
+    // shift chunks.  A chunk's halo and coefficient loads are amortised over its
+    // RZ x RY x (8 NBc) shifts: the rx blocks are split into balanced chunks of at most 12
+    // (96 shifts) and the ry rows per chunk are as many as a 56 KB tile allows (4 CTAs of
+    // 128 threads per SM at 128 registers), unless a level has too few tiles for ~8 blocks
+    // per SM: then it splits z first and ry next (at most 32 chunks by default: levels share
+    // one fused launch, so a small level does not have to fill the GPU on its own, and the
+    // gradient assembly reads few partials).
+    const int nbMax = tune[3] > 0 ? tune[3] : 12;
+    g.nXc = (int)ceil_div(g.NB, nbMax);
+    g.NBc = (int)ceil_div(g.NB, g.nXc);
     int cap = 16;
     while (cap > 1) {
         g.RY = cap;
-        if (adj_smem_bytes(g) <= 48 * 1024) break;
+        if (adj_smem_bytes(g) <= 56 * 1024) break;
         --cap;
     }
-    const int nZc = (int)std::min<int64_t>(wz, want);
-    g.RY = (int)std::min<int64_t>(ceil_div(wy, ceil_div(want, nZc)), cap);
+    const int64_t chunk_cap = tune[2] > 0 ? tune[2] : 32;
+    const int64_t want = std::min<int64_t>(chunk_cap, std::max<int64_t>(1, ceil_div(rows_target, g.adjTiles)));
+    const int64_t perX = ceil_div(want, (int64_t)g.nXc);
+    const int nZc = (int)std::min<int64_t>(wz, perX);
+    g.RY = (int)std::min<int64_t>(ceil_div(wy, ceil_div(perX, nZc)), cap);
     if (tune[1] > 0) g.RY = std::min(tune[1], cap);
     g.RY = std::min(g.RY, wy);
     g.nYc = (int)ceil_div(wy, g.RY);
     g.RZ = (int)ceil_div(wz, nZc);
     g.nZc = (int)ceil_div(wz, g.RZ);
-    g.nChunks = g.nZc * g.nYc;
+    g.nChunks = g.nZc * g.nYc * g.nXc;
 }
 
 dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
@@ -245,8 +252,8 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
     if (p->path != DMCR_PATH_AUTO && p->path != DMCR_PATH_DIRECT && p->path != DMCR_PATH_FFT)
         return fail(DMCR_EINVAL, "unknown path %d", p->path);
     if (!(p->tune[0] == 0 || p->tune[0] == 8 || p->tune[0] == 16 || p->tune[0] == 32) || p->tune[1] < 0 ||
-        p->tune[1] > 16 || p->tune[2] < 0 || p->tune[2] > 64)
-        return fail(DMCR_EINVAL, "tune = {0|8|16|32, 0..16, 0..64, 0} expected");
+        p->tune[1] > 16 || p->tune[2] < 0 || p->tune[2] > 64 || p->tune[3] < 0 || p->tune[3] > 32)
+        return fail(DMCR_EINVAL, "tune = {0|8|16|32, 0..16, 0..64, 0..32} expected");
     if (p->threshold == DMCR_SOFT && !(p->alpha > 0.f && isfinite(p->alpha)))
         return fail(DMCR_EINVAL, "alpha must be positive and finite");
     pl.ndim = p->ndim;
@@ -321,9 +328,11 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         tc.alpha = (float)a;
         tc.kappa = (float)(0.5 * a * log2e);
         tc.cexp = (float)(0.75 * a * log2e);
-        // fast path: every pair factor d = 1 + E'_x E_y stays <= 2^62, so the product of two
-        // factors that share one reciprocal is finite
+        // product forms: every pair factor d = 1 + E'_x E_y stays <= 2^62 (two factors share
+        // one reciprocal) or <= 1 + 2^31 (four factors share one, product < 2^126)
         tc.lim = (float)std::max(0.0, 0.5 * (61.0 - 0.75 * a * log2e));
+        tc.lim4 = (float)std::max(0.0, 0.5 * (31.0 - 0.75 * a * log2e));
+        tc.beta = (float)(-s0);
         const double fh = c1 / (1.0 + exp(0.25 * a)) - c1 * s0;
         pl.fh2 = fh * fh;
     }
@@ -345,7 +354,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         } else {
             pl.o_fwd[l] = o; o = align_up(o + (size_t)g.fwdTiles * g.Khalf * sizeof(float));
         }
-        pl.o_gd[l] = o; o = align_up(o + 4 * (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T * sizeof(float));
+        pl.o_gd[l] = o; o = align_up(o + (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * GBLOCK * sizeof(float));
         pl.o_adj[l] = o; o = align_up(o + (size_t)g.nChunks * g.N * sizeof(float));
     }
     pl.bytes = o;
@@ -637,7 +646,7 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
                 it.a.Gd = Gd;
                 it.a.part = part;
                 it.a.done = gs.done;
-                it.work = (int64_t)g.RZ * g.RY * g.NB;
+                it.work = (int64_t)g.RZ * g.RY * g.NBc;
                 it.blocks = g.adjTiles * g.nChunks;
                 items.push_back(it);
                 P.smem_adj = std::max(P.smem_adj, adj_smem_bytes(g));

@@ -8,7 +8,12 @@ namespace dmcr {
 constexpr int T = 8;            // shifts per thread (forward) / positions per strip (adjoint)
 constexpr int TX = 32;          // tile width in positions (fastest axis)
 constexpr int FWD_THREADS = 128;
-constexpr int ADJ_THREADS = 128;   // 32 rows x 4 strips of 8 positions
+constexpr int ADJ_THREADS = 128;   // 32 row pairs (lane, lane + 32) x 4 strips of 8 positions
+constexpr int ADJ_ROWS = 64;       // adjoint tile rows
+constexpr int GBLOCK = 48;         // coefficient floats per block of 8 shifts (packed pairs)
+
+// offset of C_m inside a coefficient block: (C_m, C_m, C_m+1, C_m+1) after the 8 (A, A, B, B)
+__host__ __device__ inline int gblock_c(int m) { return 4 * T + 2 * m; }
 constexpr int NPEN_BLOCKS = 256;   // fixed grid of the penalty reduction (deterministic)
 constexpr int MAX_DYN_SMEM = 200 * 1024;   // dynamic shared memory limit of the correlation kernels
 
@@ -31,6 +36,7 @@ struct LevelGeom {
     int adjTilesY, adjTilesX;
     int64_t adjTiles;  // n[0] * adjTilesY * adjTilesX
     int nZc, nYc, RZ, RY;   // shift chunks over rz and ry
+    int nXc, NBc;           // shift chunks over the rx blocks: NBc blocks of T per chunk
     int nChunks;
     int fft;          // 1: this level runs on the FFT path (identity threshold / binary target)
 };
@@ -43,7 +49,9 @@ struct ThreshConst {
     float cexp;      // 0.75 alpha log2(e)
     float c1, c3;
     float alpha;
-    float lim;       // fast path when |kappa M| <= lim everywhere in a block
+    float lim;       // two-pair product form when |kappa M| <= lim everywhere in a block
+    float lim4;      // four-pair product form when |kappa M| <= lim4 everywhere in a block
+    float beta;      // c3 / c1: f = c1 (s + beta)
     int identity;    // f(x) = x
 };
 

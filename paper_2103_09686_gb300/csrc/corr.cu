@@ -114,146 +114,224 @@ __host__ __device__ inline GroupBox group_box(const LevelGeom& g, int64_t gfirst
 }
 
 struct FwdSmem {
-    int planesH, rowsH, colsH, strideH;
+    int planesH, rowsH, colsH, strideP;
 };
 
+// Halo of a forward block: rows rylo .. ryhi + TY (one more row for the shifts that take
+// the tail rows offset by one), rounded up to whole row pairs; a pair row stores float2
+// (row 2p, row 2p + 1) per column, stride 4 mod 32 words.
 __host__ __device__ inline FwdSmem fwd_smem_shape(const LevelGeom& g, const GroupBox& bx) {
     FwdSmem s;
     s.planesH = bx.rzB - bx.rzA + 1;
-    s.rowsH = g.TY + bx.ryhi - bx.rylo;
+    const int rows = g.TY + bx.ryhi - bx.rylo + 1;
+    s.rowsH = rows + (rows & 1);
     s.colsH = T * (bx.bhi - bx.blo) + TX + T;
-    s.strideH = stride_4mod32(s.colsH);
+    s.strideP = stride_4mod32(2 * s.colsH);
     return s;
 }
 
 // ------------------------------------------------------------------------- pair math
+//
+// Packed FP32x2 arithmetic: the two halves of a float2 belong to two different position
+// rows (forward: rows iy, iy+1 of the tile; adjoint: rows lane, lane+32), so one FFMA2
+// issues the same step for two pairs.  The kernels are bound by the FP32 pipe (128 lane
+// operations per SM and clock; an FFMA2 counts twice) together with the MUFU reciprocal
+// (16 per SM and clock), so the pair math is chosen to balance the two:
+//   two pairs per reciprocal:  d = 1 + E'_x E_y (>= 1), r = 1 / (d_a d_b), s_a = d_b r,
+//       valid while every d <= 2^62 (|kappa M| <= lim);
+//   four pairs per reciprocal: p = d1 * d2, r = 1 / (p.x p.y), t = (p.y r, p.x r),
+//       s(d1) = t * d2, s(d2) = t * d1, valid while every d <= 1 + 2^31 (|kappa M| <= lim4);
+//   one pair per reciprocal:   s = 1 / d.
+// The forward accumulates u^2 with u = s + c3/c1 (so c1 u = f) folded into the s product;
+// the adjoint evaluates G h(s) by Horner.  Blocks with values beyond lim take the exact
+// per-pair form (one exponential per pair).
 
-enum { MODE_FAST = 0, MODE_SLOW = 1, MODE_IDENT = 2 };
+enum { MODE_FAST = 0, MODE_FAST2 = 1, MODE_SLOW = 2, MODE_IDENT = 3 };
 
-// 64 pairs of one chunk: tails x[0..8), tips y[0..16); pair (k, m) uses y[k+m].
-template <int MODE>
-__device__ __forceinline__ void fwd_chunk(const float (&x)[T], const float (&y)[2 * T], float (&r1)[T],
-                                          float (&r2)[T]) {
+// forward: of the T/2 shift pairs per tail column, how many use the four-pair form
+constexpr int FWD_QUAD_GROUPS = 0;
+// adjoint: shifts m < ADJ_SINGLE_SHIFTS of every block of 8 use one reciprocal per pair
+constexpr int ADJ_SINGLE_SHIFTS = 2;
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// exact form: e = cexp - kappa (M_x + M_y) per half
+__device__ __forceinline__ float2 sig_exact(float2 e) {
+    return make_float2(rcp_approx(ex2_approx(e.x) + 1.0f), rcp_approx(ex2_approx(e.y) + 1.0f));
+}
+
+// Forward, one chunk of a row pair: x2[k] tails at column k, y2[j] tips at column j; pair
+// (k, m) uses y2[k + m].  acc[m] += (s + beta)^2 per row (beta = c3 / c1, so c1 (s + beta) = f);
+// identity: acc[m] += a^2.  Columns k >= kv are outside the field (ragged last chunk).
+template <int MODE, bool FULL>
+__device__ __forceinline__ void fwd_chunk(const float2 (&x2)[T], const float2 (&y2)[2 * T], float2 (&acc)[T],
+                                          float beta, int kv) {
+    const float2 one2 = make_float2(1.0f, 1.0f);
+    const float2 b2 = make_float2(beta, beta);
 #pragma unroll
     for (int k = 0; k < T; ++k) {
-        if (MODE == MODE_FAST) {
-            // two pairs per reciprocal: s_a = d_b / (d_a d_b), s_b = d_a / (d_a d_b); on the fast
-            // path every d <= 2^62, so d_a d_b stays finite (d >= 1 always)
+        if (!FULL && k >= kv) continue;
 #pragma unroll
-            for (int m = 0; m < T / 2; ++m) {
-                const float da = fmaf(x[k], y[k + m], 1.0f);
-                const float db = fmaf(x[k], y[k + m + T / 2], 1.0f);
-                const float r = rcp_approx(da * db);
-                const float sa = db * r, sb = da * r;
-                r1[m] += sa;
-                r2[m] = fmaf(sa, sa, r2[m]);
-                r1[m + T / 2] += sb;
-                r2[m + T / 2] = fmaf(sb, sb, r2[m + T / 2]);
-            }
-        } else {
+        for (int m = 0; m < T; m += 2) {
+            if (MODE == MODE_FAST && m / 2 < FWD_QUAD_GROUPS) {
+                const float2 d1 = ffma2(x2[k], y2[k + m], one2);
+                const float2 d2 = ffma2(x2[k], y2[k + m + 1], one2);
+                const float2 p = fmul2(d1, d2);
+                const float r = rcp_approx(p.x * p.y);
+                const float2 t = make_float2(p.y * r, p.x * r);
+                const float2 u1 = ffma2(t, d2, b2);
+                const float2 u2 = ffma2(t, d1, b2);
+                acc[m] = ffma2(u1, u1, acc[m]);
+                acc[m + 1] = ffma2(u2, u2, acc[m + 1]);
+            } else {
 #pragma unroll
-            for (int m = 0; m < T; ++m) {
-                if (MODE == MODE_IDENT) {
-                    const float a = x[k] + y[k + m];
-                    r2[m] = fmaf(a, a, r2[m]);
-                } else {
-                    const float s = rcp_approx(ex2_approx(x[k] - y[k + m]) + 1.0f);
-                    r1[m] += s;
-                    r2[m] = fmaf(s, s, r2[m]);
+                for (int q = 0; q < 2; ++q) {
+                    float2 u;
+                    if (MODE == MODE_IDENT) {
+                        u = fadd2(x2[k], y2[k + m + q]);
+                    } else if (MODE == MODE_SLOW) {
+                        u = fadd2(sig_exact(fadd2(x2[k], y2[k + m + q])), b2);
+                    } else {
+                        const float2 d = ffma2(x2[k], y2[k + m + q], one2);
+                        const float r = rcp_approx(d.x * d.y);
+                        u = make_float2(fmaf(d.y, r, beta), fmaf(d.x, r, beta));
+                    }
+                    acc[m + q] = ffma2(u, u, acc[m + q]);
                 }
             }
         }
     }
 }
 
-// acc[k] += sum_m G[m] H(s_km) with H(s) = s (1 - s) (c1 s + c3), written with the
-// per-shift coefficients A = -c1 G, B = (c1 - c3) G, C = c3 G as  s (C + s (B + A s)).
-// Shared-memory coefficient layout per block of 8 shifts: for mp = 0..3 the two quads
-// (A, B, C, 0) of shifts mp and mp + 4, i.e. 32 floats.
+// Adjoint, one block of 8 shifts: x2[k] own values at column k (rows lane, lane+32),
+// y2[j] partners at column j; pair (k, m) uses y2[k + m].  acc[k] += G(r_m) h(s) per row with
+// h(s) written s (C + s (B + A s)), A = -c1 G, B = (c1 - c3) G, C = c3 G (identity: G a).
+// Coefficients per block: (A, A, B, B) for m = 0..7, then (C_m, C_m, C_m+1, C_m+1) for even m.
 template <int MODE>
-__device__ __forceinline__ void adj_chunk(const float (&x)[T], const float (&y)[2 * T], const float* gq,
-                                          float (&acc)[T]) {
-    // all 24 coefficients of the 8 shifts live in registers for the 8 positions
-    float4 ca[T / 2], cb[T / 2];
+__device__ __forceinline__ void adj_block(const float2 (&x2)[T], const float2 (&y2)[2 * T],
+                                          const float4* __restrict__ cf, float2 (&acc)[T]) {
+    const float2 one2 = make_float2(1.0f, 1.0f);
 #pragma unroll
-    for (int mp = 0; mp < T / 2; ++mp) {
-        ca[mp] = *reinterpret_cast<const float4*>(gq + 8 * mp);
-        cb[mp] = *reinterpret_cast<const float4*>(gq + 8 * mp + 4);
-    }
+    for (int m = 0; m < T; ++m) {
+        const float4 ab = cf[m];
+        const float4 cc = cf[T + m / 2];
+        const float2 A2 = make_float2(ab.x, ab.y);
+        const float2 B2 = make_float2(ab.z, ab.w);
+        const float2 C2 = (m & 1) ? make_float2(cc.z, cc.w) : make_float2(cc.x, cc.y);
 #pragma unroll
-    for (int k = 0; k < T; ++k) {
-#pragma unroll
-        for (int mp = 0; mp < T / 2; ++mp) {
-            if (MODE == MODE_FAST) {
-                const float da = fmaf(x[k], y[k + mp], 1.0f);
-                const float db = fmaf(x[k], y[k + mp + T / 2], 1.0f);
-                const float r = rcp_approx(da * db);
-                const float sa = db * r, sb = da * r;
-                float qa = fmaf(ca[mp].x, sa, ca[mp].y);
-                qa = fmaf(qa, sa, ca[mp].z);
-                acc[k] = fmaf(qa, sa, acc[k]);
-                float qb = fmaf(cb[mp].x, sb, cb[mp].y);
-                qb = fmaf(qb, sb, cb[mp].z);
-                acc[k] = fmaf(qb, sb, acc[k]);
-            } else if (MODE == MODE_IDENT) {
-                acc[k] = fmaf(ca[mp].x, x[k] + y[k + mp], acc[k]);
-                acc[k] = fmaf(cb[mp].x, x[k] + y[k + mp + T / 2], acc[k]);
-            } else {
-                const float sa = rcp_approx(ex2_approx(x[k] - y[k + mp]) + 1.0f);
-                const float sb = rcp_approx(ex2_approx(x[k] - y[k + mp + T / 2]) + 1.0f);
-                float qa = fmaf(ca[mp].x, sa, ca[mp].y);
-                qa = fmaf(qa, sa, ca[mp].z);
-                acc[k] = fmaf(qa, sa, acc[k]);
-                float qb = fmaf(cb[mp].x, sb, cb[mp].y);
-                qb = fmaf(qb, sb, cb[mp].z);
-                acc[k] = fmaf(qb, sb, acc[k]);
+        for (int k = 0; k < T; ++k) {
+            if (MODE == MODE_IDENT) {
+                acc[k] = ffma2(A2, fadd2(x2[k], y2[k + m]), acc[k]);
+                continue;
             }
+            float2 s;
+            if (MODE == MODE_SLOW) {
+                s = sig_exact(fadd2(x2[k], y2[k + m]));
+            } else {
+                const float2 d = ffma2(x2[k], y2[k + m], one2);
+                if (m < ADJ_SINGLE_SHIFTS) {
+                    s = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+                } else {
+                    const float r = rcp_approx(d.x * d.y);
+                    s = make_float2(d.y * r, d.x * r);
+                }
+            }
+            float2 q = ffma2(A2, s, B2);
+            q = ffma2(q, s, C2);
+            acc[k] = ffma2(q, s, acc[k]);
         }
     }
 }
 
-__device__ __forceinline__ void load8(const float* p, float (&v)[T]) {
-    const float4 a = *reinterpret_cast<const float4*>(p);
-    const float4 b = *reinterpret_cast<const float4*>(p + 4);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+__device__ __forceinline__ void load_pairs8(const float* p, float2 (&v)[T]) {
+#pragma unroll
+    for (int i = 0; i < T / 2; ++i) {
+        const float4 a = *reinterpret_cast<const float4*>(p + 4 * i);
+        v[2 * i] = make_float2(a.x, a.y);
+        v[2 * i + 1] = make_float2(a.z, a.w);
+    }
 }
 
-__device__ __forceinline__ void load16(const float* p, float (&v)[2 * T]) {
+__device__ __forceinline__ void load_pairs16(const float* p, float2 (&v)[2 * T]) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < T; ++i) {
         const float4 a = *reinterpret_cast<const float4*>(p + 4 * i);
-        v[4 * i + 0] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = a.z; v[4 * i + 3] = a.w;
+        v[2 * i] = make_float2(a.x, a.y);
+        v[2 * i + 1] = make_float2(a.z, a.w);
     }
+}
+
+// Asynchronous global -> shared copies (cp.async): the halo loads of a block are issued
+// back to back and waited for once, instead of one dependent round trip per column.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// waits for this thread's own copies (visible to this thread; other threads need a barrier)
+__device__ __forceinline__ void cp_async_wait_own() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// value stored in the shared tiles for one field value (tail side adds cexp)
+template <int MODE>
+__device__ __forceinline__ float tile_value(const ThreshConst& tc, float v, bool tail) {
+    if (MODE == MODE_IDENT) return 0.5f * v;
+    if (MODE == MODE_SLOW) return tail ? fmaf(-tc.kappa, v, tc.cexp) : -tc.kappa * v;
+    return ex2_approx(tail ? fmaf(-tc.kappa, v, tc.cexp) : -tc.kappa * v);
+}
+
+// 0: |kappa v| <= lim4, 1: <= lim, 2: larger (NaN counts as 0: it propagates on any path)
+__device__ __forceinline__ int range_class(const ThreshConst& tc, float v) {
+    const float a = fabsf(tc.kappa * v);
+    return (a <= tc.lim4 || isnan(v)) ? 0 : (a <= tc.lim ? 1 : 2);
 }
 
 // ------------------------------------------------------------------------- forward
 
-// One plane of the block's tile; row sums (<= 32 terms) are added to the block sums, which
-// hold at most 64 row sums (plans keep TY x planes-per-block <= 64).
+// One plane of the block's tile.  Row pairs q hold tail rows (2q + cls, 2q + cls + 1); the
+// second row of the last pair lies outside the tile when rowsValid is odd.  Per-pair sums
+// (<= 32 terms per row) are added to the block sums, which hold at most 64 row sums (plans
+// keep TY x planes-per-block <= 64).
 template <int MODE>
-__device__ __forceinline__ void fwd_plane(const float* xs, const float* ybase, int strideH, int rowsValid,
-                                          int chunksValid, float (&t1)[T], float (&t2)[T]) {
-    for (int iy = 0; iy < rowsValid; ++iy) {
-        float r1[T], r2[T];
+__device__ __forceinline__ void fwd_plane(const float* xbase, const float* ybase, int strideP, int rowsValid,
+                                          int colsValid, float beta, float (&tsum)[T]) {
+    const int nPairs = (rowsValid + 1) >> 1;
+    const int chunksFull = colsValid / T, kvLast = colsValid % T;
+    for (int q = 0; q < nPairs; ++q) {
+        float2 acc[T];
 #pragma unroll
-        for (int m = 0; m < T; ++m) { r1[m] = 0.f; r2[m] = 0.f; }
-        const float* xrow = xs + iy * TX;
-        const float* yrow = ybase + iy * strideH;
+        for (int m = 0; m < T; ++m) acc[m] = make_float2(0.f, 0.f);
+        const float* xrow = xbase + 2 * q * TX;
+        const float* yrow = ybase + q * strideP;
 #pragma unroll 1
-        for (int c = 0; c < chunksValid; ++c) {
-            float x[T], y[2 * T];
-            load8(xrow + c * T, x);
-            load16(yrow + c * T, y);
-            fwd_chunk<MODE>(x, y, r1, r2);
+        for (int c = 0; c < chunksFull; ++c) {
+            float2 x2[T], y2[2 * T];
+            load_pairs8(xrow + 2 * T * c, x2);
+            load_pairs16(yrow + 2 * T * c, y2);
+            fwd_chunk<MODE, true>(x2, y2, acc, beta, T);
         }
+        if (kvLast) {
+            float2 x2[T], y2[2 * T];
+            load_pairs8(xrow + 2 * T * chunksFull, x2);
+            load_pairs16(yrow + 2 * T * chunksFull, y2);
+            fwd_chunk<MODE, false>(x2, y2, acc, beta, kvLast);
+        }
+        const bool second = 2 * q + 1 < rowsValid;
 #pragma unroll
-        for (int m = 0; m < T; ++m) { t1[m] += r1[m]; t2[m] += r2[m]; }
+        for (int m = 0; m < T; ++m) tsum[m] += second ? acc[m].x + acc[m].y : acc[m].x;
     }
 }
 
 template <bool IDENT>
-__global__ void __launch_bounds__(FWD_THREADS, 5)
+__global__ void __launch_bounds__(FWD_THREADS, 4)
 corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
     const FwdSeg& sg = segs[si];
@@ -277,95 +355,145 @@ corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     const int64_t glast = min(gfirst + FWD_THREADS, g.NG) - 1;
     const GroupBox bx = group_box(g, gfirst, glast);
     const FwdSmem sh = fwd_smem_shape(g, bx);
+    const int pairRowsH = sh.rowsH / 2;
 
-    float* xs = smem;                       // TY x TX tails
-    float* ys = smem + g.TY * TX;           // planesH x rowsH x strideH tips
+    // tails: two tiles of TY/2 row pairs x TX columns (float2 per column), rows (2q, 2q+1)
+    // and (2q+1, 2q+2); tips: planesH x pairRowsH x strideP, rows (2p, 2p+1) of the halo
+    const int xtile = g.TY * TX + 4;
+    float* xs = smem;
+    float* ys = smem + 2 * xtile;
 
     const int64_t gi = gfirst + tid;
     const bool gvalid = gi < g.NG;
     int rz = bx.rzA, ry = bx.rylo, b = bx.blo;
     if (gvalid) decode_group(g, gi, rz, ry, b);
-    const float* ybase = ys + ((int64_t)(rz - bx.rzA) * sh.rowsH + (ry - bx.rylo)) * sh.strideH + T * (b - bx.blo);
+    // shifts at an odd row offset from the halo start take the tail rows shifted by one:
+    // positions are periodic, so rows y0+1 .. y0+TY cover the same set once over all tiles
+    const int cls = (ry - bx.rylo) & 1;
+    const int rrel = ry - bx.rylo + cls;
+    const float* ybase = ys + ((int64_t)(rz - bx.rzA) * pairRowsH + rrel / 2) * sh.strideP + 2 * T * (b - bx.blo);
+    const float* xbase = xs + cls * xtile;
 
     const int rowsValid = (int)min((int64_t)g.TY, n1 - y0);
     const int colsValid = (int)min((int64_t)TX, n2 - x0);
-    const int chunksValid = (colsValid + T - 1) / T;
+    const float beta = tc.beta;
 
-    float t1[T], t2[T];
+    float tsum[T];
 #pragma unroll
-    for (int m = 0; m < T; ++m) { t1[m] = 0.f; t2[m] = 0.f; }
+    for (int m = 0; m < T; ++m) tsum[m] = 0.f;
 
     const int warp = tid >> 5, lane = tid & 31;
     constexpr int NW = FWD_THREADS / 32;
-    const int rowsAll = sh.planesH * sh.rowsH;
+    const int prAll = sh.planesH * pairRowsH;
     const int64_t hx0 = x0 - g.P[2] + (int64_t)T * bx.blo;
-    const float kinf = __int_as_float(0x7f800000);
+    const bool colOk = x0 + lane < n2;
 
     for (int64_t z = z0; z < z1; ++z) {
         __syncthreads();
-        bool bad = false;
-        // tails: one row per warp, one column per lane; +inf marks positions outside the field (s = 0)
-        for (int iy = warp; iy < g.TY; iy += NW) {
-            const bool valid = (y0 + iy < n1) && (x0 + lane < n2);
-            const float v = valid ? field[(z * n1 + y0 + iy) * n2 + x0 + lane] : 0.f;
-            bad |= valid && !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
-            xs[iy * TX + lane] = IDENT ? (valid ? 0.5f * v : 0.f)
-                                       : (valid ? ex2_approx(fmaf(-tc.kappa, v, tc.cexp)) : 0x1p100f);
+        // tails (row rho of the tile is valid for class 0 when rho < rowsValid, for class 1
+        // when 1 <= rho <= rowsValid; invalid entries hold 0, i.e. d = 1) and the tips (the
+        // periodic halo, one pair of rows per warp, columns strided by the lanes): raw values
+        // copied asynchronously, then transformed in place by the thread that copied them
+        for (int pr = warp; pr < g.TY; pr += NW) {
+            const int t = pr / (g.TY / 2), q = pr - t * (g.TY / 2);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int rho = 2 * q + t + h;
+                const bool valid = colOk && (t == 0 ? rho < rowsValid : rho <= rowsValid);
+                float* d = xs + t * xtile + 2 * (q * TX + lane) + h;
+                if (valid) cp_async4(d, field + (z * n1 + wrap1(y0 + rho, n1)) * n2 + x0 + lane);
+                else *d = 0.f;
+            }
         }
-        // tips: the periodic halo, one row per warp, columns strided by the lanes
-        for (int pr = warp; pr < rowsAll; pr += NW) {
-            const int p = pr / sh.rowsH, r = pr - p * sh.rowsH;
-            const float* src = field + (wrap1(z + bx.rzA + p, n0) * n1 + wrap1(y0 + bx.rylo + r, n1)) * n2;
-            float* dst = ys + pr * sh.strideH;
+        for (int pr = warp; pr < prAll; pr += NW) {
+            const int p = pr / pairRowsH, r = pr - p * pairRowsH;
+            const int64_t zz = wrap1(z + bx.rzA + p, n0);
+            const float* srcA = field + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r, n1)) * n2;
+            const float* srcB = field + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r + 1, n1)) * n2;
+            float* dst = ys + (int64_t)pr * sh.strideP;
             int64_t gx = wrap1(hx0 + lane, n2);
             for (int c = lane; c < sh.colsH; c += 32) {
-                const float v = src[gx];
-                bad |= !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
-                dst[c] = IDENT ? 0.5f * v : ex2_approx(-tc.kappa * v);
+                cp_async4(dst + 2 * c, srcA + gx);
+                cp_async4(dst + 2 * c + 1, srcB + gx);
                 gx += 32;
                 while (gx >= n2) gx -= n2;
             }
         }
-        const int slow = __syncthreads_or(bad);
-        if (!IDENT && slow) {
-            // rare: the block holds values outside the fast range; rewrite both tiles in the
-            // exact form (exponents, combined per pair) from the field
-            for (int iy = warp; iy < g.TY; iy += NW) {
-                const bool valid = (y0 + iy < n1) && (x0 + lane < n2);
-                const float v = valid ? field[(z * n1 + y0 + iy) * n2 + x0 + lane] : 0.f;
-                xs[iy * TX + lane] = valid ? fmaf(-tc.kappa, v, tc.cexp) : kinf;
+        cp_async_wait_own();
+        int rc = 0;
+        for (int pr = warp; pr < g.TY; pr += NW) {
+            const int t = pr / (g.TY / 2), q = pr - t * (g.TY / 2);
+            float* d = xs + t * xtile + 2 * (q * TX + lane);
+            float e[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int rho = 2 * q + t + h;
+                const bool valid = colOk && (t == 0 ? rho < rowsValid : rho <= rowsValid);
+                const float v = d[h];
+                if (valid) rc = max(rc, range_class(tc, v));
+                e[h] = !valid ? 0.f : (IDENT ? 0.5f * v : tile_value<MODE_FAST>(tc, v, true));
             }
-            for (int pr = warp; pr < rowsAll; pr += NW) {
-                const int p = pr / sh.rowsH, r = pr - p * sh.rowsH;
-                const float* src = field + (wrap1(z + bx.rzA + p, n0) * n1 + wrap1(y0 + bx.rylo + r, n1)) * n2;
-                float* dst = ys + pr * sh.strideH;
+            *reinterpret_cast<float2*>(d) = make_float2(e[0], e[1]);
+        }
+        for (int pr = warp; pr < prAll; pr += NW) {
+            float* dst = ys + (int64_t)pr * sh.strideP;
+            for (int c = lane; c < sh.colsH; c += 32) {
+                const float2 v = *reinterpret_cast<const float2*>(dst + 2 * c);
+                rc = max(rc, max(range_class(tc, v.x), range_class(tc, v.y)));
+                float2 e;
+                if (IDENT) e = make_float2(0.5f * v.x, 0.5f * v.y);
+                else e = make_float2(tile_value<MODE_FAST>(tc, v.x, false), tile_value<MODE_FAST>(tc, v.y, false));
+                *reinterpret_cast<float2*>(dst + 2 * c) = e;
+            }
+        }
+        const int slow = __syncthreads_or(rc >= 2);
+        const int mid = FWD_QUAD_GROUPS > 0 ? __syncthreads_or(rc >= 1) : 0;
+        if (!IDENT && slow) {
+            // rare: values outside the product range; rewrite both tiles in exponent form
+            for (int pr = warp; pr < g.TY; pr += NW) {
+                const int t = pr / (g.TY / 2), q = pr - t * (g.TY / 2);
+                float e[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int rho = 2 * q + t + h;
+                    const bool valid = colOk && (t == 0 ? rho < rowsValid : rho <= rowsValid);
+                    const float v = valid ? field[(z * n1 + wrap1(y0 + rho, n1)) * n2 + x0 + lane] : 0.f;
+                    e[h] = valid ? tile_value<MODE_SLOW>(tc, v, true) : 0.f;
+                }
+                *reinterpret_cast<float2*>(xs + t * xtile + 2 * (q * TX + lane)) = make_float2(e[0], e[1]);
+            }
+            for (int pr = warp; pr < prAll; pr += NW) {
+                const int p = pr / pairRowsH, r = pr - p * pairRowsH;
+                const int64_t zz = wrap1(z + bx.rzA + p, n0);
+                const float* srcA = field + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r, n1)) * n2;
+                const float* srcB = field + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r + 1, n1)) * n2;
+                float* dst = ys + (int64_t)pr * sh.strideP;
                 int64_t gx = wrap1(hx0 + lane, n2);
                 for (int c = lane; c < sh.colsH; c += 32) {
-                    dst[c] = tc.kappa * src[gx];
+                    *reinterpret_cast<float2*>(dst + 2 * c) = make_float2(
+                        tile_value<MODE_SLOW>(tc, srcA[gx], false), tile_value<MODE_SLOW>(tc, srcB[gx], false));
                     gx += 32;
                     while (gx >= n2) gx -= n2;
                 }
             }
         }
         __syncthreads();
-        if (IDENT) fwd_plane<MODE_IDENT>(xs, ybase, sh.strideH, rowsValid, chunksValid, t1, t2);
-        else if (slow) fwd_plane<MODE_SLOW>(xs, ybase, sh.strideH, rowsValid, chunksValid, t1, t2);
-        else fwd_plane<MODE_FAST>(xs, ybase, sh.strideH, rowsValid, chunksValid, t1, t2);
+        if (IDENT) fwd_plane<MODE_IDENT>(xbase, ybase, sh.strideP, rowsValid, colsValid, beta, tsum);
+        else if (slow) fwd_plane<MODE_SLOW>(xbase, ybase, sh.strideP, rowsValid, colsValid, beta, tsum);
+        else if (FWD_QUAD_GROUPS > 0 && mid) fwd_plane<MODE_FAST2>(xbase, ybase, sh.strideP, rowsValid, colsValid, beta, tsum);
+        else fwd_plane<MODE_FAST>(xbase, ybase, sh.strideP, rowsValid, colsValid, beta, tsum);
     }
 
     if (!gvalid) return;
-    // sum_x f^2 = c1^2 sum s^2 + 2 c1 c3 sum s + n c3^2 (identity: sum a^2 directly)
-    const float nvalid = (float)((z1 - z0) * (int64_t)rowsValid * colsValid);
+    // sum_x f^2 = c1^2 sum (s + c3/c1)^2 (identity: sum a^2 directly)
+    const float c1sq = tc.c1 * tc.c1;
     float* out = partial + ts * g.Khalf;
 #pragma unroll
     for (int m = 0; m < T; ++m) {
         const int rx = -g.P[2] + T * b + m;
         const int64_t k = canon_index(g, rz, ry, rx);
         if (k < 0) continue;
-        float v;
-        if (IDENT) v = t2[m];
-        else v = fmaf(tc.c1 * tc.c1, t2[m], fmaf(2.f * tc.c1 * tc.c3, t1[m], nvalid * tc.c3 * tc.c3));
-        out[k] = v;
+        out[k] = IDENT ? tsum[m] : c1sq * tsum[m];
     }
 }
 
@@ -401,16 +529,16 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedSeg* __restric
 // ------------------------------------------------------------------------- adjoint
 
 template <int MODE>
-__device__ __forceinline__ void adj_rows(const float* ys, const float* Gs, int strideH, int NB, int ryN, int lane,
-                                         int strip, const float (&x)[T], float (&acc)[T]) {
+__device__ __forceinline__ void adj_rows(const float* ys, const float* Gs, int strideP, int NB, int ryN, int lane,
+                                         int strip, const float2 (&x2)[T], float2 (&acc)[T]) {
     for (int r = 0; r < ryN; ++r) {
-        const float* yrow = ys + (lane + r) * strideH + T * strip;
-        const float* grow = Gs + r * (NB * 4 * T);
+        const float* yrow = ys + (lane + r) * strideP + 2 * T * strip;
+        const float4* grow = reinterpret_cast<const float4*>(Gs + r * (NB * GBLOCK));
 #pragma unroll 1
         for (int bb = 0; bb < NB; ++bb) {
-            float y[2 * T];
-            load16(yrow + T * bb, y);
-            adj_chunk<MODE>(x, y, grow + 4 * T * bb, acc);
+            float2 y2[2 * T];
+            load_pairs16(yrow + 2 * T * bb, y2);
+            adj_block<MODE>(x2, y2, grow + (GBLOCK / 4) * bb, acc);
         }
     }
 }
@@ -432,105 +560,137 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     const int tx = (int)(tile % g.adjTilesX);
     const int ty = (int)((tile / g.adjTilesX) % g.adjTilesY);
     const int64_t z = tile / ((int64_t)g.adjTilesX * g.adjTilesY);
-    const int64_t x0 = (int64_t)tx * TX, y0 = (int64_t)ty * 32;
+    const int64_t x0 = (int64_t)tx * TX, y0 = (int64_t)ty * ADJ_ROWS;
     const int64_t n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    // shift chunk: (rz range, ry range, rx-block range), rx blocks fastest
     const int chunk = (int)(local / g.adjTiles);
-    const int zc = chunk / g.nYc, yc = chunk % g.nYc;
+    const int xc = chunk % g.nXc, yc = (chunk / g.nXc) % g.nYc, zc = chunk / (g.nXc * g.nYc);
     const int rzA = -g.P[0] + zc * g.RZ;
     const int rzB = min(rzA + g.RZ, g.P[0] + 1);
     const int ryA = -g.P[1] + yc * g.RY;
     const int ryB = min(ryA + g.RY, g.P[1] + 1);
     const int ryN = ryB - ryA;
-    const int WB = g.NB * T;
-    const int rowsH = 32 + ryN - 1;
-    const int colsH = WB + 3 * T + 2 * T;   // 8 NB + 32 (see strip/bb read extents)
-    const int strideH = stride_4mod32(colsH);
+    const int bbA = xc * g.NBc;
+    const int nbb = min(g.NBc, g.NB - bbA);
+    const int colsH = T * nbb + 4 * T;      // read extent: 8 strip + 8 bb + 16 columns
+    const int strideP = stride_4mod32(2 * colsH);
+    const int pairRows = 32 + ryN - 1;      // pair row i holds halo rows i and i + 32
     float* ys = smem;
-    float* Gs = smem + rowsH * strideH;
-    const int64_t hx0 = x0 - g.P[2];
+    float* Gs = smem + pairRows * strideP;
+    const int64_t hx0 = x0 - g.P[2] + (int64_t)T * bbA;
 
-    // own positions: row y0 + lane, columns x0 + 8 strip + k (values reloaded per rz plane)
-    const int64_t py = y0 + lane;
-    const float* xrow = field + (z * n1 + (py < n1 ? py : 0)) * n2;
-    bool xbad = false;
+    // own positions: rows y0 + lane and y0 + lane + 32, columns x0 + 8 strip + k
+    const int64_t pyA = y0 + lane, pyB = pyA + 32;
+    const float* xrowA = field + (z * n1 + (pyA < n1 ? pyA : 0)) * n2;
+    const float* xrowB = field + (z * n1 + (pyB < n1 ? pyB : 0)) * n2;
+    int xrc = 0;
 #pragma unroll
     for (int k = 0; k < T; ++k) {
         const int64_t px = x0 + T * strip + k;
-        const float v = (py < n1 && px < n2) ? xrow[px] : 0.f;
-        xbad |= !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
+        if (px < n2) {
+            if (pyA < n1) xrc = max(xrc, range_class(tc, xrowA[px]));
+            if (pyB < n1) xrc = max(xrc, range_class(tc, xrowB[px]));
+        }
     }
-    float acc[T];
+    float2 acc[T];
 #pragma unroll
-    for (int k = 0; k < T; ++k) acc[k] = 0.f;
+    for (int k = 0; k < T; ++k) acc[k] = make_float2(0.f, 0.f);
 
-    const int ng = ryN * 4 * WB;
+    const int rowG = nbb * GBLOCK;          // coefficient floats of one ry row of the chunk
     const int warp = threadIdx.x >> 5;
     constexpr int NW = ADJ_THREADS / 32;
     for (int rz = rzA; rz < rzB; ++rz) {
         __syncthreads();
         const int64_t gz = wrap1(z + rz, n0);
-        bool bad = xbad;
-        for (int r = warp; r < rowsH; r += NW) {
-            const float* src = field + (gz * n1 + wrap1(y0 + ryA + r, n1)) * n2;
-            float* dst = ys + r * strideH;
+        // raw halo (pair rows i, i + 32) and the chunk's coefficient rows, copied asynchronously
+        for (int i = warp; i < pairRows; i += NW) {
+            const float* srcA = field + (gz * n1 + wrap1(y0 + ryA + i, n1)) * n2;
+            const float* srcB = field + (gz * n1 + wrap1(y0 + ryA + i + 32, n1)) * n2;
+            float* dst = ys + i * strideP;
             int64_t gx = wrap1(hx0 + lane, n2);
             for (int c = lane; c < colsH; c += 32) {
-                const float v = src[gx];
-                bad |= !(fabsf(tc.kappa * v) <= tc.lim) && !isnan(v);
-                dst[c] = IDENT ? 0.5f * v : ex2_approx(-tc.kappa * v);
+                cp_async4(dst + 2 * c, srcA + gx);
+                cp_async4(dst + 2 * c + 1, srcB + gx);
                 gx += 32;
                 while (gx >= n2) gx -= n2;
             }
         }
-        const float4* grow0 = reinterpret_cast<const float4*>(
-            Gd + ((int64_t)(rz + g.P[0]) * (2 * g.P[1] + 1) + (ryA + g.P[1])) * 4 * WB);
-        for (int i = threadIdx.x; i < ng / 4; i += ADJ_THREADS) reinterpret_cast<float4*>(Gs)[i] = grow0[i];
-        const int slow = __syncthreads_or(bad);
+        const float* grow0 = Gd + (((int64_t)(rz + g.P[0]) * (2 * g.P[1] + 1) + (ryA + g.P[1])) * g.NB + bbA) * GBLOCK;
+        for (int i = threadIdx.x; i < ryN * (rowG / 4); i += ADJ_THREADS) {
+            const int r = i / (rowG / 4), c = i - r * (rowG / 4);
+            cp_async16(Gs + r * rowG + 4 * c, grow0 + (int64_t)r * g.NB * GBLOCK + 4 * c);
+        }
+        cp_async_wait_own();
+        // every thread transforms the halo entries it copied
+        int rc = xrc;
+        for (int i = warp; i < pairRows; i += NW) {
+            float* dst = ys + i * strideP;
+            for (int c = lane; c < colsH; c += 32) {
+                const float2 v = *reinterpret_cast<const float2*>(dst + 2 * c);
+                rc = max(rc, max(range_class(tc, v.x), range_class(tc, v.y)));
+                float2 e;
+                if (IDENT) e = make_float2(0.5f * v.x, 0.5f * v.y);
+                else e = make_float2(tile_value<MODE_FAST>(tc, v.x, false), tile_value<MODE_FAST>(tc, v.y, false));
+                *reinterpret_cast<float2*>(dst + 2 * c) = e;
+            }
+        }
+        const int slow = __syncthreads_or(rc >= 2);
         if (!IDENT && slow) {
-            for (int r = warp; r < rowsH; r += NW) {
-                const float* src = field + (gz * n1 + wrap1(y0 + ryA + r, n1)) * n2;
-                float* dst = ys + r * strideH;
+            for (int i = warp; i < pairRows; i += NW) {
+                const float* srcA = field + (gz * n1 + wrap1(y0 + ryA + i, n1)) * n2;
+                const float* srcB = field + (gz * n1 + wrap1(y0 + ryA + i + 32, n1)) * n2;
+                float* dst = ys + i * strideP;
                 int64_t gx = wrap1(hx0 + lane, n2);
                 for (int c = lane; c < colsH; c += 32) {
-                    dst[c] = tc.kappa * src[gx];
+                    *reinterpret_cast<float2*>(dst + 2 * c) = make_float2(
+                        tile_value<MODE_SLOW>(tc, srcA[gx], false), tile_value<MODE_SLOW>(tc, srcB[gx], false));
                     gx += 32;
                     while (gx >= n2) gx -= n2;
                 }
             }
         }
-        float x[T];
+        // own values; positions outside the field hold 0 (d = 1) and are not written back
+        float2 x2[T];
 #pragma unroll
         for (int k = 0; k < T; ++k) {
             const int64_t px = x0 + T * strip + k;
-            const float v = (py < n1 && px < n2) ? xrow[px] : 0.f;
-            const float u = fmaf(-tc.kappa, v, tc.cexp);
-            x[k] = IDENT ? 0.5f * v : (slow ? u : ex2_approx(u));
+            const float va = (pyA < n1 && px < n2) ? xrowA[px] : 0.f;
+            const float vb = (pyB < n1 && px < n2) ? xrowB[px] : 0.f;
+            if (IDENT) {
+                x2[k] = make_float2(0.5f * va, 0.5f * vb);
+            } else if (slow) {
+                x2[k] = make_float2(tile_value<MODE_SLOW>(tc, va, true), tile_value<MODE_SLOW>(tc, vb, true));
+            } else {
+                x2[k] = make_float2((pyA < n1 && px < n2) ? tile_value<MODE_FAST>(tc, va, true) : 0.f,
+                                    (pyB < n1 && px < n2) ? tile_value<MODE_FAST>(tc, vb, true) : 0.f);
+            }
         }
         __syncthreads();
-        if (IDENT) adj_rows<MODE_IDENT>(ys, Gs, strideH, g.NB, ryN, lane, strip, x, acc);
-        else if (slow) adj_rows<MODE_SLOW>(ys, Gs, strideH, g.NB, ryN, lane, strip, x, acc);
-        else adj_rows<MODE_FAST>(ys, Gs, strideH, g.NB, ryN, lane, strip, x, acc);
+        if (IDENT) adj_rows<MODE_IDENT>(ys, Gs, strideP, nbb, ryN, lane, strip, x2, acc);
+        else if (slow) adj_rows<MODE_SLOW>(ys, Gs, strideP, nbb, ryN, lane, strip, x2, acc);
+        else adj_rows<MODE_FAST>(ys, Gs, strideP, nbb, ryN, lane, strip, x2, acc);
     }
 
-    if (py >= n1) return;
-    float* out = part + (int64_t)chunk * g.N + (z * n1 + py) * n2;
 #pragma unroll
-    for (int k = 0; k < T; ++k) {
-        const int64_t px = x0 + T * strip + k;
-        if (px < n2) out[px] = acc[k];
+    for (int h = 0; h < 2; ++h) {
+        const int64_t py = h ? pyB : pyA;
+        if (py >= n1) continue;
+        float* out = part + (int64_t)chunk * g.N + (z * n1 + py) * n2;
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            const int64_t px = x0 + T * strip + k;
+            if (px < n2) out[px] = h ? acc[k].y : acc[k].x;
+        }
     }
 }
 
-// Dense full-window coefficient grid of one level:
-//   Gd[rz][ry][col], rx = col - P2 (zero where rx > P2),
-//   value = scale * (src[k] - sub[k]) * (2 if r = 0),  k = canonical index of +-r,
-//   scale = weight * (gscale from the loss, or 1) * (c1 alpha / N_l, or 1 / N_l for f(x)=x).
 // Dense full-window coefficient grid of one level, in adjoint order:
 //   G(r) = scale * (src[k] - sub[k]) * (2 if r = 0),  k = canonical index of +-r,
 //   scale = weight * (gscale from the loss, or 1) * (c1 alpha / N_l, or 1 / N_l for f(x)=x),
-//   quad (A, B, C, 0) = (-c1 G, (c1 - c3) G, c3 G, 0)   (f(x) = x: (G, 0, 0, 0)),
+//   (A, B, C) = (-c1 G, (c1 - c3) G, c3 G)   (f(x) = x: (G, 0, 0)),
 // zero where rx > P2 (padding of the last rx block).  Row (rz, ry) holds NB blocks of 8
-// shifts; a block stores for mp = 0..3 the quads of shifts mp and mp + 4 (32 floats).
+// shifts; a block of GBLOCK = 48 floats stores (A, A, B, B) for m = 0..7 and then
+// (C_m, C_m, C_m+1, C_m+1) for even m: both halves of a packed pair get the same coefficient.
 __global__ void gcoef_kernel(const GSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
     const GSeg& sg = segs[si];
@@ -555,11 +715,12 @@ __global__ void gcoef_kernel(const GSeg* __restrict__ segs, int nseg, ThreshCons
         v = sc * d;
     }
     const int b = col / T, m = col % T;
-    float4 q;
-    if (tc.identity) q = make_float4(v, 0.f, 0.f, 0.f);
-    else q = make_float4(-tc.c1 * v, (tc.c1 - tc.c3) * v, tc.c3 * v, 0.f);
-    float4* dst = reinterpret_cast<float4*>(sg.Gd + (row * g.NB + b) * (4 * T)) + (2 * (m % (T / 2)) + m / (T / 2));
-    *dst = q;
+    float A, B, C;
+    if (tc.identity) { A = v; B = 0.f; C = 0.f; }
+    else { A = -tc.c1 * v; B = (tc.c1 - tc.c3) * v; C = tc.c3 * v; }
+    float* blk = sg.Gd + (row * g.NB + b) * GBLOCK;
+    *reinterpret_cast<float4*>(blk + 4 * m) = make_float4(A, A, B, B);
+    *reinterpret_cast<float2*>(blk + gblock_c(m)) = make_float2(C, C);
 }
 
 // ------------------------------------------------------------------------- launchers
@@ -571,7 +732,7 @@ size_t fwd_smem_bytes(const LevelGeom& g) {
         const int64_t glast = std::min<int64_t>(gfirst + FWD_THREADS, g.NG) - 1;
         const GroupBox bx = group_box(g, gfirst, glast);
         const FwdSmem sh = fwd_smem_shape(g, bx);
-        const int f = g.TY * TX + sh.planesH * sh.rowsH * sh.strideH;
+        const int f = 2 * (g.TY * TX + 4) + sh.planesH * (sh.rowsH / 2) * sh.strideP;
         if (f > maxFloats) maxFloats = f;
     }
     return (size_t)maxFloats * sizeof(float);
@@ -590,10 +751,9 @@ void launch_fwd_reduce(const RedSeg* segs, int nseg, int64_t blocks, cudaStream_
 }
 
 size_t adj_smem_bytes(const LevelGeom& g) {
-    const int WB = g.NB * T;
-    const int rowsH = 32 + g.RY - 1;
-    const int colsH = WB + 5 * T;
-    return (size_t)(rowsH * stride_4mod32(colsH) + 4 * g.RY * WB) * sizeof(float);
+    const int pairRows = 32 + g.RY - 1;
+    const int colsH = T * g.NBc + 4 * T;
+    return (size_t)(pairRows * stride_4mod32(2 * colsH) + g.RY * g.NBc * GBLOCK) * sizeof(float);
 }
 
 void launch_corr_adj(const AdjSeg* segs, int nseg, int64_t blocks, size_t smem, const ThreshConst& tc,

@@ -223,7 +223,7 @@ __global__ void fft_embed_kernel(LevelGeom g, const float* __restrict__ Gd, doub
                 const int64_t row = (rz + g.P[0]) * wy + (ry + g.P[1]);
                 const int col = (int)(rx + g.P[2]);
                 const int blk = col / T, m = col % T;
-                acc += (double)Gd[(row * g.NB + blk) * (4 * T) + (2 * (m % (T / 2)) + m / (T / 2)) * 4];
+                acc += (double)Gd[(row * g.NB + blk) * GBLOCK + 4 * m];
             }
         }
     }

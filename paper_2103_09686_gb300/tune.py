@@ -1,13 +1,14 @@
 """Autotuner for the launch shapes of the fused correlation kernels.
 
-The plan's built-in choices (forward tile rows, adjoint shift-chunk rows and chunk count)
-are heuristics.  ``tuned(params)`` measures one descriptor + loss + gradient evaluation
-(``dmcr_loss_grad``, CUDA events, median of 3 after a warm-up) for candidate shapes by
-coordinate descent -- forward tile rows first (they only affect the forward kernel), then
-the adjoint's rows per chunk, then its chunk limit -- and returns the params with the
-fastest shape in ``tune``.  Results are cached in a JSON file keyed by the problem class
-and the GPU, so a shape is measured once per machine.  Shapes change only the blocking and
-summation order: results agree to rounding.
+The plan's built-in choices (forward tile rows; adjoint rx blocks, ry rows and count of the
+shift chunks) are heuristics.  ``tuned(params)`` measures one descriptor + loss + gradient
+evaluation (``dmcr_loss_grad``, CUDA events, median of 3 after a warm-up) for candidate
+shapes by coordinate descent -- forward tile rows first (they only affect the forward
+kernel), then the adjoint's rx blocks per chunk (they set how many ry rows fit in shared
+memory), its ry rows, and its chunk limit -- and returns the params with the fastest shape
+in ``tune``.  Results are cached in a JSON file keyed by the problem class and the GPU, so a
+shape is measured once per machine.  Shapes change only the blocking and summation order:
+results agree to rounding.
 """
 from __future__ import annotations
 
@@ -24,6 +25,7 @@ from . import _lib
 FWD_ROWS = (8, 16, 32)
 ADJ_ROWS = (0, 2, 4, 8, 12, 16)
 ADJ_CHUNKS = (0, 8, 16, 64)
+ADJ_XBLOCKS = (0, 3, 5, 12, 32)
 _lock = threading.Lock()
 
 
@@ -72,7 +74,7 @@ def search(p: _lib.Params, seed: int = 0) -> tuple[tuple, float, list]:
 
     best = (0, 0, 0, 0)
     best_ms = run(best)
-    for axis, values in ((0, FWD_ROWS), (1, ADJ_ROWS), (2, ADJ_CHUNKS)):
+    for axis, values in ((0, FWD_ROWS), (3, ADJ_XBLOCKS), (1, ADJ_ROWS), (2, ADJ_CHUNKS)):
         for v in values:
             t = list(best)
             t[axis] = v

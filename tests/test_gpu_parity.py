@@ -42,6 +42,12 @@ CASES = [
     ((12, 16, 24), (2, 4, 5), 1, "binary"),   # ragged 3-D
     ((64, 64), (16, 16), 1, "extreme"),       # values far outside [0, 1]: exact slow path
     ((40, 64), (6, 6), 1, "relaxed"),
+    ((33, 40), (9, 7), 1, "uniform"),         # odd row count: the last row pair is half
+    ((7, 9), (3, 4), 1, "relaxed"),           # tile larger than the field, ragged columns
+    ((9, 11, 13), (2, 3, 4), 1, "uniform"),   # odd 3-D
+    ((64, 64), (16, 16), 1, "mid"),           # |M| up to 3: the two-pair product form
+    ((96, 64), (12, 9), 2, "mixed"),          # a few out-of-range pixels: per-block mode mix
+    ((80, 96), (10, 44), 1, "uniform"),       # 12 rx blocks: adjoint chunks split the rx range
 ]
 
 
@@ -53,6 +59,14 @@ def _field(kind, shape, seed):
         return (rng.random(shape) < 0.35).astype(np.float64)
     if kind == "extreme":
         return rng.uniform(-30, 30, shape)
+    if kind == "mid":
+        return rng.uniform(-3, 3, shape)
+    if kind == "mixed":
+        M = synthetic.uniform_field(shape, seed).copy()
+        flat = M.reshape(-1)
+        idx = rng.choice(flat.size, 6, replace=False)
+        flat[idx] = [2.5, -2.0, 3.0, 9.0, -6.0, 2.2]
+        return M
     return rng.uniform(-0.4, 1.4, shape)
 
 

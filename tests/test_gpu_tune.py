@@ -25,7 +25,7 @@ def test_tuner_picks_valid_shape_and_caches(cuda_lib, tmp_path):
     np.testing.assert_allclose(b, a, rtol=1e-5, atol=1e-9)
 
 
-@pytest.mark.parametrize("tune_", [(8, 2, 8, 0), (32, 16, 64, 0), (16, 1, 1, 0)])
+@pytest.mark.parametrize("tune_", [(8, 2, 8, 1), (32, 16, 64, 0), (16, 1, 1, 2), (0, 3, 0, 32)])
 def test_explicit_shapes_agree(cuda_lib, tune_):
     dm = cuda_lib
     p = dm.Params(shape=(96, 64), window=(12, 9), levels=2)

@@ -46,8 +46,9 @@ def test_noalloc_matches_workspace_entry_point_twice(cuda_lib, shape, window, le
 
 def test_noalloc_rejects_problems_beyond_its_scratch(cuda_lib):
     dm = cuda_lib
-    p = dm.Params(shape=(512, 512), window=(64, 64), levels=3)
-    field = torch.zeros(512, 512, device="cuda")
+    # 1024^2 +-64: 1024 forward tiles x 8321 shifts of partial sums alone exceed 16 MiB
+    p = dm.Params(shape=(1024, 1024), window=(64, 64), levels=1)
+    field = torch.zeros(1024, 1024, device="cuda")
     desc = torch.empty(dm.dmcr_descriptor_length(p), device="cuda")
     st, err = _call_noalloc(dm, p, field, desc)
     assert st == 2 and "scratch" in err
