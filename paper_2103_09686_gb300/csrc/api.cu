@@ -328,10 +328,9 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         tc.alpha = (float)a;
         tc.kappa = (float)(0.5 * a * log2e);
         tc.cexp = (float)(0.75 * a * log2e);
-        // product forms: every pair factor d = 1 + E'_x E_y stays <= 2^62 (two factors share
-        // one reciprocal) or <= 1 + 2^31 (four factors share one, product < 2^126)
+        // product form: every pair factor d = 1 + E'_x E_y stays <= 2^62, so the product of
+        // two factors that share one reciprocal is finite
         tc.lim = (float)std::max(0.0, 0.5 * (61.0 - 0.75 * a * log2e));
-        tc.lim4 = (float)std::max(0.0, 0.5 * (31.0 - 0.75 * a * log2e));
         tc.beta = (float)(-s0);
         const double fh = c1 / (1.0 + exp(0.25 * a)) - c1 * s0;
         pl.fh2 = fh * fh;

@@ -49,8 +49,7 @@ struct ThreshConst {
     float cexp;      // 0.75 alpha log2(e)
     float c1, c3;
     float alpha;
-    float lim;       // two-pair product form when |kappa M| <= lim everywhere in a block
-    float lim4;      // four-pair product form when |kappa M| <= lim4 everywhere in a block
+    float lim;       // product form when |kappa M| <= lim everywhere in a block
     float beta;      // c3 / c1: f = c1 (s + beta)
     int identity;    // f(x) = x
 };

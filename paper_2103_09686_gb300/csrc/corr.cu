@@ -136,35 +136,32 @@ __host__ __device__ inline FwdSmem fwd_smem_shape(const LevelGeom& g, const Grou
 // rows (forward: rows iy, iy+1 of the tile; adjoint: rows lane, lane+32), so one FFMA2
 // issues the same step for two pairs.  The kernels are bound by the FP32 pipe (128 lane
 // operations per SM and clock; an FFMA2 counts twice) together with the MUFU reciprocal
-// (16 per SM and clock), so the pair math is chosen to balance the two:
-//   two pairs per reciprocal:  d = 1 + E'_x E_y (>= 1), r = 1 / (d_a d_b), s_a = d_b r,
-//       valid while every d <= 2^62 (|kappa M| <= lim);
-//   four pairs per reciprocal: p = d1 * d2, r = 1 / (p.x p.y), t = (p.y r, p.x r),
-//       s(d1) = t * d2, s(d2) = t * d1, valid while every d <= 1 + 2^31 (|kappa M| <= lim4);
-//   one pair per reciprocal:   s = 1 / d.
-// The forward accumulates u^2 with u = s + c3/c1 (so c1 u = f) folded into the s product;
-// the adjoint evaluates G h(s) by Horner.  Blocks with values beyond lim take the exact
-// per-pair form (one exponential per pair).
+// (16 per SM and clock).  Two pairs share one reciprocal: with d = 1 + E'_x E_y >= 1,
+//     r = 1 / (d_a d_b),   (d_a, d_b) * (r, r) = (1/d_b, 1/d_a) = (s_b, s_a),
+// valid while every d <= 2^62 (|kappa M| <= lim); the product lands with the halves
+// swapped, which the accumulators absorb (they read the rows back crosswise).  The
+// adjoint gives a few positions one reciprocal per pair (s = 1/d), which moves work from
+// the FP32 pipe to the otherwise idle share of the MUFU.  Blocks with values beyond lim
+// take the exact per-pair form (one exponential per pair).
 
-enum { MODE_FAST = 0, MODE_FAST2 = 1, MODE_SLOW = 2, MODE_IDENT = 3 };
+enum { MODE_FAST = 0, MODE_SLOW = 1, MODE_IDENT = 2 };
 
-// forward: of the T/2 shift pairs per tail column, how many use the four-pair form
-constexpr int FWD_QUAD_GROUPS = 0;
-// adjoint: shifts m < ADJ_SINGLE_SHIFTS of every block of 8 use one reciprocal per pair
-constexpr int ADJ_SINGLE_SHIFTS = 2;
+// adjoint: positions k < ADJ_SINGLE of every 8 use one reciprocal per pair
+constexpr int ADJ_SINGLE = 3;
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
-// exact form: e = cexp - kappa (M_x + M_y) per half
-__device__ __forceinline__ float2 sig_exact(float2 e) {
-    return make_float2(rcp_approx(ex2_approx(e.x) + 1.0f), rcp_approx(ex2_approx(e.y) + 1.0f));
+// exact form, halves swapped like the product form: e = cexp - kappa (M_x + M_y) per half
+__device__ __forceinline__ float2 sig_exact_swapped(float2 e) {
+    return make_float2(rcp_approx(ex2_approx(e.y) + 1.0f), rcp_approx(ex2_approx(e.x) + 1.0f));
 }
 
 // Forward, one chunk of a row pair: x2[k] tails at column k, y2[j] tips at column j; pair
 // (k, m) uses y2[k + m].  acc[m] += (s + beta)^2 per row (beta = c3 / c1, so c1 (s + beta) = f);
-// identity: acc[m] += a^2.  Columns k >= kv are outside the field (ragged last chunk).
+// identity: acc[m] += a^2.  The soft modes leave the rows swapped in acc (row iy in .y).
+// Columns k >= kv are outside the field (ragged last chunk).
 template <int MODE, bool FULL>
 __device__ __forceinline__ void fwd_chunk(const float2 (&x2)[T], const float2 (&y2)[2 * T], float2 (&acc)[T],
                                           float beta, int kv) {
@@ -174,33 +171,18 @@ __device__ __forceinline__ void fwd_chunk(const float2 (&x2)[T], const float2 (&
     for (int k = 0; k < T; ++k) {
         if (!FULL && k >= kv) continue;
 #pragma unroll
-        for (int m = 0; m < T; m += 2) {
-            if (MODE == MODE_FAST && m / 2 < FWD_QUAD_GROUPS) {
-                const float2 d1 = ffma2(x2[k], y2[k + m], one2);
-                const float2 d2 = ffma2(x2[k], y2[k + m + 1], one2);
-                const float2 p = fmul2(d1, d2);
-                const float r = rcp_approx(p.x * p.y);
-                const float2 t = make_float2(p.y * r, p.x * r);
-                const float2 u1 = ffma2(t, d2, b2);
-                const float2 u2 = ffma2(t, d1, b2);
-                acc[m] = ffma2(u1, u1, acc[m]);
-                acc[m + 1] = ffma2(u2, u2, acc[m + 1]);
+        for (int m = 0; m < T; ++m) {
+            float2 u;
+            if (MODE == MODE_IDENT) {
+                u = fadd2(x2[k], y2[k + m]);
+            } else if (MODE == MODE_SLOW) {
+                u = fadd2(sig_exact_swapped(fadd2(x2[k], y2[k + m])), b2);
             } else {
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    float2 u;
-                    if (MODE == MODE_IDENT) {
-                        u = fadd2(x2[k], y2[k + m + q]);
-                    } else if (MODE == MODE_SLOW) {
-                        u = fadd2(sig_exact(fadd2(x2[k], y2[k + m + q])), b2);
-                    } else {
-                        const float2 d = ffma2(x2[k], y2[k + m + q], one2);
-                        const float r = rcp_approx(d.x * d.y);
-                        u = make_float2(fmaf(d.y, r, beta), fmaf(d.x, r, beta));
-                    }
-                    acc[m + q] = ffma2(u, u, acc[m + q]);
-                }
+                const float2 d = ffma2(x2[k], y2[k + m], one2);
+                const float r = rcp_approx(d.x * d.y);
+                u = ffma2(d, make_float2(r, r), b2);
             }
+            acc[m] = ffma2(u, u, acc[m]);
         }
     }
 }
@@ -208,7 +190,8 @@ __device__ __forceinline__ void fwd_chunk(const float2 (&x2)[T], const float2 (&
 // Adjoint, one block of 8 shifts: x2[k] own values at column k (rows lane, lane+32),
 // y2[j] partners at column j; pair (k, m) uses y2[k + m].  acc[k] += G(r_m) h(s) per row with
 // h(s) written s (C + s (B + A s)), A = -c1 G, B = (c1 - c3) G, C = c3 G (identity: G a).
-// Coefficients per block: (A, A, B, B) for m = 0..7, then (C_m, C_m, C_m+1, C_m+1) for even m.
+// The soft modes leave the rows swapped in acc (row lane in .y).  Coefficients per block:
+// (A, A, B, B) for m = 0..7, then (C_m, C_m, C_m+1, C_m+1) for even m.
 template <int MODE>
 __device__ __forceinline__ void adj_block(const float2 (&x2)[T], const float2 (&y2)[2 * T],
                                           const float4* __restrict__ cf, float2 (&acc)[T]) {
@@ -228,14 +211,14 @@ __device__ __forceinline__ void adj_block(const float2 (&x2)[T], const float2 (&
             }
             float2 s;
             if (MODE == MODE_SLOW) {
-                s = sig_exact(fadd2(x2[k], y2[k + m]));
+                s = sig_exact_swapped(fadd2(x2[k], y2[k + m]));
             } else {
                 const float2 d = ffma2(x2[k], y2[k + m], one2);
-                if (m < ADJ_SINGLE_SHIFTS) {
-                    s = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+                if (k < ADJ_SINGLE) {
+                    s = make_float2(rcp_approx(d.y), rcp_approx(d.x));
                 } else {
                     const float r = rcp_approx(d.x * d.y);
-                    s = make_float2(d.y * r, d.x * r);
+                    s = fmul2(d, make_float2(r, r));
                 }
             }
             float2 q = ffma2(A2, s, B2);
@@ -288,10 +271,10 @@ __device__ __forceinline__ float tile_value(const ThreshConst& tc, float v, bool
     return ex2_approx(tail ? fmaf(-tc.kappa, v, tc.cexp) : -tc.kappa * v);
 }
 
-// 0: |kappa v| <= lim4, 1: <= lim, 2: larger (NaN counts as 0: it propagates on any path)
-__device__ __forceinline__ int range_class(const ThreshConst& tc, float v) {
-    const float a = fabsf(tc.kappa * v);
-    return (a <= tc.lim4 || isnan(v)) ? 0 : (a <= tc.lim ? 1 : 2);
+// 1 when |kappa v| > lim (the block takes the exact form); NaN counts as in range: it
+// propagates on any path
+__device__ __forceinline__ int out_of_range(const ThreshConst& tc, float v) {
+    return fabsf(tc.kappa * v) > tc.lim;
 }
 
 // ------------------------------------------------------------------------- forward
@@ -324,9 +307,11 @@ __device__ __forceinline__ void fwd_plane(const float* xbase, const float* ybase
             load_pairs16(yrow + 2 * T * chunksFull, y2);
             fwd_chunk<MODE, false>(x2, y2, acc, beta, kvLast);
         }
+        // the first row of the pair sits in .y in the soft modes (halves swapped), in .x otherwise
         const bool second = 2 * q + 1 < rowsValid;
 #pragma unroll
-        for (int m = 0; m < T; ++m) tsum[m] += second ? acc[m].x + acc[m].y : acc[m].x;
+        for (int m = 0; m < T; ++m)
+            tsum[m] += second ? acc[m].x + acc[m].y : (MODE == MODE_IDENT ? acc[m].x : acc[m].y);
     }
 }
 
@@ -430,7 +415,7 @@ corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
                 const int rho = 2 * q + t + h;
                 const bool valid = colOk && (t == 0 ? rho < rowsValid : rho <= rowsValid);
                 const float v = d[h];
-                if (valid) rc = max(rc, range_class(tc, v));
+                if (valid) rc |= out_of_range(tc, v);
                 e[h] = !valid ? 0.f : (IDENT ? 0.5f * v : tile_value<MODE_FAST>(tc, v, true));
             }
             *reinterpret_cast<float2*>(d) = make_float2(e[0], e[1]);
@@ -439,15 +424,14 @@ corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
             float* dst = ys + (int64_t)pr * sh.strideP;
             for (int c = lane; c < sh.colsH; c += 32) {
                 const float2 v = *reinterpret_cast<const float2*>(dst + 2 * c);
-                rc = max(rc, max(range_class(tc, v.x), range_class(tc, v.y)));
+                rc |= out_of_range(tc, v.x) | out_of_range(tc, v.y);
                 float2 e;
                 if (IDENT) e = make_float2(0.5f * v.x, 0.5f * v.y);
                 else e = make_float2(tile_value<MODE_FAST>(tc, v.x, false), tile_value<MODE_FAST>(tc, v.y, false));
                 *reinterpret_cast<float2*>(dst + 2 * c) = e;
             }
         }
-        const int slow = __syncthreads_or(rc >= 2);
-        const int mid = FWD_QUAD_GROUPS > 0 ? __syncthreads_or(rc >= 1) : 0;
+        const int slow = __syncthreads_or(rc);
         if (!IDENT && slow) {
             // rare: values outside the product range; rewrite both tiles in exponent form
             for (int pr = warp; pr < g.TY; pr += NW) {
@@ -480,7 +464,6 @@ corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
         __syncthreads();
         if (IDENT) fwd_plane<MODE_IDENT>(xbase, ybase, sh.strideP, rowsValid, colsValid, beta, tsum);
         else if (slow) fwd_plane<MODE_SLOW>(xbase, ybase, sh.strideP, rowsValid, colsValid, beta, tsum);
-        else if (FWD_QUAD_GROUPS > 0 && mid) fwd_plane<MODE_FAST2>(xbase, ybase, sh.strideP, rowsValid, colsValid, beta, tsum);
         else fwd_plane<MODE_FAST>(xbase, ybase, sh.strideP, rowsValid, colsValid, beta, tsum);
     }
 
@@ -588,8 +571,8 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     for (int k = 0; k < T; ++k) {
         const int64_t px = x0 + T * strip + k;
         if (px < n2) {
-            if (pyA < n1) xrc = max(xrc, range_class(tc, xrowA[px]));
-            if (pyB < n1) xrc = max(xrc, range_class(tc, xrowB[px]));
+            if (pyA < n1) xrc |= out_of_range(tc, xrowA[px]);
+            if (pyB < n1) xrc |= out_of_range(tc, xrowB[px]);
         }
     }
     float2 acc[T];
@@ -627,14 +610,14 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
             float* dst = ys + i * strideP;
             for (int c = lane; c < colsH; c += 32) {
                 const float2 v = *reinterpret_cast<const float2*>(dst + 2 * c);
-                rc = max(rc, max(range_class(tc, v.x), range_class(tc, v.y)));
+                rc |= out_of_range(tc, v.x) | out_of_range(tc, v.y);
                 float2 e;
                 if (IDENT) e = make_float2(0.5f * v.x, 0.5f * v.y);
                 else e = make_float2(tile_value<MODE_FAST>(tc, v.x, false), tile_value<MODE_FAST>(tc, v.y, false));
                 *reinterpret_cast<float2*>(dst + 2 * c) = e;
             }
         }
-        const int slow = __syncthreads_or(rc >= 2);
+        const int slow = __syncthreads_or(rc);
         if (!IDENT && slow) {
             for (int i = warp; i < pairRows; i += NW) {
                 const float* srcA = field + (gz * n1 + wrap1(y0 + ryA + i, n1)) * n2;
@@ -679,7 +662,8 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
 #pragma unroll
         for (int k = 0; k < T; ++k) {
             const int64_t px = x0 + T * strip + k;
-            if (px < n2) out[px] = h ? acc[k].y : acc[k].x;
+            // soft modes hold row lane in .y and row lane + 32 in .x (halves swapped)
+            if (px < n2) out[px] = (h != 0) == IDENT ? acc[k].y : acc[k].x;
         }
     }
 }
