@@ -33,16 +33,20 @@ import synthetic  # noqa: E402
 
 METRIC = "S2+adjoint voxel-shifts/s"
 UNIT = "voxel-shifts/s"
+FP32_LANES_PER_CLK_PER_SM = 128   # FP32 FMA lanes per SM per clock (an FFMA2/FMUL2 takes two lane slots)
 MUFU_RCP_PER_CLK_PER_SM = 16      # MUFU.RCP throughput per SM per clock (measured, sm_103a)
-ISSUE_PER_CLK_PER_SM = 128        # 4 schedulers x 32 lanes: thread-instructions issued per SM per clock
-# Instructions per (position, shift) pair of the implemented soft-threshold formulation (two
-# pairs share one reciprocal): forward 2 FFMA + FMUL + MUFU.RCP + 2 FMUL + 2 FADD + 2 FFMA per
-# 2 pairs; adjoint 2 FFMA + FMUL + MUFU.RCP + 2 FMUL + 6 FFMA per 2 pairs.
-INSTR_PER_PAIR = {"corr_fwd": 5.0, "corr_adj": 6.0}
+# FP32 lane operations and MUFU reciprocals per (position, shift) pair of the implemented
+# soft-threshold formulation:
+#   forward: d = 1 + E'E (1), product d_a d_b of two pairs sharing a reciprocal (1/2),
+#            u = s + c3/c1 (1), acc += u^2 (1); one reciprocal per two pairs;
+#   adjoint: d (1), Horner G h(s) (3); 5 of every 8 positions share a reciprocal between two
+#            pairs (product 1/2, s 1), 3 of 8 take one reciprocal per pair.
+LANE_OPS_PER_PAIR = {"corr_fwd": 3.5, "corr_adj": 4.0 + 5.0 / 8.0 * 1.5}
+RCP_PER_PAIR = {"corr_fwd": 0.5, "corr_adj": 5.0 / 8.0 * 0.5 + 3.0 / 8.0}
 # DRAM bytes (read + write) per launch of the current kernels on the 512^2, +-64, 3-level
 # workload, from the ncu full-set capture summarised in profiles/corr_kernels_grf512_w64_L3.md
-# (set to None whenever the kernels change until they are captured again).
-NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2255360 + 0, ("grf512", "corr_fwd"): 1651968 + 225024}
+# (None whenever the kernels changed since the last capture).
+NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2694912 + 36096, ("grf512", "corr_fwd"): 1450752 + 256}
 
 WORKLOADS = {
     "grf512": dict(shape=(512, 512), window=(64, 64), levels=3,
@@ -465,17 +469,20 @@ def main():
     roofline = None
     if pairs is not None:
         kind = "corr_adj" if name.startswith("corr_adj") else "corr_fwd"
-        peak = sm_count * ISSUE_PER_CLK_PER_SM * max_mhz * 1e6 / 1e12                 # T thread-instr/s
-        achieved = pairs * INSTR_PER_PAIR[kind] / (avg_ms / 1e3) / 1e12
-        mufu_peak = sm_count * MUFU_RCP_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9          # Gpair/s at 1 rcp/pair
-        roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+        t = avg_ms / 1e3
+        peak = sm_count * FP32_LANES_PER_CLK_PER_SM * max_mhz * 1e6 / 1e12          # T lane-op/s
+        achieved = pairs * LANE_OPS_PER_PAIR[kind] / t / 1e12
+        mufu_peak = sm_count * MUFU_RCP_PER_CLK_PER_SM * max_mhz * 1e6 / 1e12       # T rcp/s
+        mufu = pairs * RCP_PER_PAIR[kind] / t / 1e12
+        roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
                     "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get((args.workload, kind)),
-                    "peak_basis": "issue slots: %d SMs x %d thread-instructions/clk x %.0f MHz (max SM clock); "
-                                  "achieved = algorithmic pairs x %.0f instructions/pair / launch time"
-                                  % (sm_count, ISSUE_PER_CLK_PER_SM, max_mhz, INSTR_PER_PAIR[kind]),
-                    "pairs_per_launch": pairs, "pairs_per_s": pairs / (avg_ms / 1e3),
-                    "mufu_view": {"peak_Gpair_s_at_1_rcp_per_pair": mufu_peak,
-                                  "frac": pairs / (avg_ms / 1e3) / 1e9 / mufu_peak},
+                    "peak_basis": "FP32 pipe: %d SMs x %d FMA lanes/clk x %.0f MHz (max SM clock); achieved = "
+                                  "algorithmic pairs x %.4g FP32 lane-ops/pair / launch time"
+                                  % (sm_count, FP32_LANES_PER_CLK_PER_SM, max_mhz, LANE_OPS_PER_PAIR[kind]),
+                    "mufu": {"achieved": mufu, "peak": mufu_peak, "unit": "Trcp/s", "frac": mufu / mufu_peak,
+                             "rcp_per_pair": RCP_PER_PAIR[kind]},
+                    "binding_frac": max(achieved / peak, mufu / mufu_peak),
+                    "pairs_per_launch": pairs, "pairs_per_s": pairs / t,
                     "avg_launch_ms": avg_ms, "launches": kcnt}
     launches = int(sum(c for _, c in prof.values()))
 
