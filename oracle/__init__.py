@@ -25,6 +25,14 @@ What each function follows (sections and equations of the paper):
 * ``adam_step`` / ``reconstruct`` -- Eq. M-update with Adam at the TensorFlow defaults
   (App. B): lr 1e-3, beta1 0.9, beta2 0.999; epsilon 1e-7 (Keras form; the paper does
   not print epsilon).
+* ``ensemble`` / ``s3bar`` / ``s3_descriptor`` / ``s3_loss_grad`` -- the ensemble
+  e_x(r) = f(a_x(r)) of Sec. 3.2.2-3.2.4 as an explicit N x K matrix and its quadratic
+  reduction, Eq. s3: S_bar3(r_a, r_b) = (1/N) sum_x e_x(r_a) e_x(r_b), the Gram matrix of
+  the ensemble (Sec. 3.4's footnote), on the half window of every level; the exact gradient
+  of a loss on it by the chain rule.
+* ``s2_count`` / ``s3_count`` / ``s3_from_s3bar`` -- exact two- and three-point
+  probabilities of a binary field by counting (Sec. 3.2.1) and App. A's mapping from
+  S_bar3 back to S3 (Eq. s3rfroms3rbar).
 """
 from __future__ import annotations
 
@@ -385,3 +393,115 @@ def reconstruct(M0, D_des, p: Params, iters: int, tol_rel: float = 0.0, lr=1e-3,
 def round_field(M) -> np.ndarray:
     """Rounding for evaluation (Sec. 4.1): values >= 0.5 become phase 1."""
     return (np.asarray(M) >= 0.5).astype(np.float64)
+
+
+# ----------------------------------------------------------------------------- three-point
+
+def ensemble(M_level, shifts, kind: str = "soft", alpha: float = 10.0):
+    """The ensemble of one level as explicit (N, K) arrays: e_x(r) = f(a_x(r)) and f'(a_x(r)),
+    a_x(r) = (M_x + M_{x+r}) / 2 for r != 0 and a_x(0) = M_x (the masks of Sec. 3.2.3 hold
+    1/2 at tip and tail, a single 1 at r = 0), periodic in every axis; x in C order."""
+    M = np.asarray(M_level, dtype=np.float64)
+    shifts = np.asarray(shifts, dtype=np.int64).reshape(-1, M.ndim)
+    N = M.size
+    E = np.empty((N, shifts.shape[0]))
+    dE = np.empty((N, shifts.shape[0]))
+    for k, r in enumerate(shifts):
+        if np.any(r != 0):
+            tip = np.roll(M, shift=tuple(-int(c) for c in r), axis=tuple(range(M.ndim)))
+            a = 0.5 * (M + tip)
+        else:
+            a = M
+        f, df = threshold(a.ravel(), kind, alpha)
+        E[:, k] = f
+        dE[:, k] = df
+    return E, dE
+
+
+def s3bar(M_level, shifts, kind: str = "soft", alpha: float = 10.0) -> np.ndarray:
+    """Eq. s3 on one level: the K x K matrix S_bar3(r_a, r_b) = (1/N) sum_x e_x(r_a) e_x(r_b)."""
+    E, _ = ensemble(M_level, shifts, kind, alpha)
+    return (E.T @ E) / E.shape[0]
+
+
+def s3_descriptor(M, p: Params, levels_out: bool = False):
+    """Multigrid form (Eq. mg) of the three-point descriptor: per level the K x K matrix on
+    the half window, multiplied by w_l; flattened row-major and concatenated, finest first."""
+    H = half_window(p.ndim, p.window)
+    pyr = pyramid(M, p.levels)
+    w = p.weights()
+    blocks = [w[l] * s3bar(pyr[l], H, p.threshold, p.alpha) for l in range(p.levels)]
+    D = np.concatenate([b.ravel() for b in blocks])
+    return (D, blocks) if levels_out else D
+
+
+def s3_level_vjp(M_level, p: Params, G) -> np.ndarray:
+    """g_y = sum_{a,b} G[a, b] dS_bar3(r_a, r_b)/dM_y for one level: with
+    V = f'(a) * (E (G + G^T) / N), every entry a_x(r) depends on M_x and M_{x+r} with
+    weight 1/2 (weight 1 for r = 0)."""
+    M = np.asarray(M_level, dtype=np.float64)
+    H = half_window(p.ndim, p.window)
+    E, dE = ensemble(M, H, p.threshold, p.alpha)
+    G = np.asarray(G, dtype=np.float64)
+    V = dE * ((E @ (G + G.T)) / E.shape[0])
+    g = np.zeros(M.shape)
+    axes = tuple(range(M.ndim))
+    for k, r in enumerate(H):
+        Vk = V[:, k].reshape(M.shape)
+        if np.any(r != 0):
+            g += 0.5 * Vk + 0.5 * np.roll(Vk, shift=tuple(int(c) for c in r), axis=axes)
+        else:
+            g += Vk
+    return g
+
+
+def s3_loss_grad(M, D_des, p: Params, mode: str = "norm", lambda0: float | None = None, bc: bool = True):
+    """Eq. L_func_dMCR with the three-point descriptor (Frobenius norm over every level's
+    K x K matrix) and its gradient, through all levels at once (Sec. 3.3)."""
+    M = np.asarray(M, dtype=np.float64)
+    N = M.size
+    D = s3_descriptor(M, p)
+    out = loss(M, D_des, p, mode, lambda0, bc, D=D)
+    lam0 = out["lambda0"]
+    rho, E, Ebc = out["rho"], out["E"], out["Ebc"]
+    if mode == "norm":
+        dphi_dD = rho / E if E > 0 else np.zeros_like(rho)
+        phi = E
+    else:
+        dphi_dD = 2.0 * rho
+        phi = out["E2"]
+    gD = dphi_dD * (1.0 + lam0 * Ebc)
+    K = half_window(p.ndim, p.window).shape[0]
+    pyr = pyramid(M, p.levels)
+    w = p.weights()
+    g = None
+    for l in reversed(range(p.levels)):
+        Gl = w[l] * gD[l * K * K:(l + 1) * K * K].reshape(K, K)
+        gl = s3_level_vjp(pyr[l], p, Gl)
+        g = gl if g is None else gl + prolongate_adjoint(g)
+    ex = box_excess(M)
+    dex = np.where(M - 1.0 > 0, 1.0, 0.0) - np.where(-M > 0, 1.0, 0.0)
+    g = g + lam0 * phi * 2.0 * (ex / N) * dex / N
+    return out, g
+
+
+def s2_count(M, r) -> float:
+    """Binary field: the probability that x and x + r are both in phase 1 (any vector r)."""
+    M = np.asarray(M)
+    tip = np.roll(M, shift=tuple(-int(c) for c in r), axis=tuple(range(M.ndim)))
+    return float(np.mean((M == 1) & (tip == 1)))
+
+
+def s3_count(M, ra, rb) -> float:
+    """Binary field: the probability that x, x + r_a and x + r_b are all in phase 1."""
+    M = np.asarray(M)
+    axes = tuple(range(M.ndim))
+    ta = np.roll(M, shift=tuple(-int(c) for c in ra), axis=axes)
+    tb = np.roll(M, shift=tuple(-int(c) for c in rb), axis=axes)
+    return float(np.mean((M == 1) & (ta == 1) & (tb == 1)))
+
+
+def s3_from_s3bar(s3b: float, s2a: float, s2b: float, s20: float, s2ab: float, fh: float) -> float:
+    """App. A, Eq. s3rfroms3rbar, general case 0 != r_a != r_b != 0: S3 from S_bar3 and the
+    exact two-point values S2(r_a), S2(r_b), S2(0) and S2(r_a - r_b), with fh = f(1/2)."""
+    return (s3b - fh * (s2a + s2b) - fh * fh * (s20 - s2a - s2b + s2ab)) / (1.0 - 2.0 * fh)
