@@ -66,6 +66,13 @@ enum { DMCR_SOFT = 0, DMCR_IDENTITY = 1 };           /* threshold (Sec. 3.2.4; f
 enum { DMCR_PATH_AUTO = 0, DMCR_PATH_DIRECT = 1, DMCR_PATH_FFT = 2 };
 enum { DMCR_LOSS_NORM = 0, DMCR_LOSS_SQUARED = 1 };  /* L = E(1 + lambda0 E_bc)  |  E^2 (1 + lambda0 E_bc) */
 enum { DMCR_PROLONG_ADJOINT_ACCUMULATE = 0, DMCR_PROLONG_INJECT = 1 };
+/* Descriptor.  S2: the two-point S_bar2(r) on the half window, K_half floats per level
+ * (Sec. 3.2.4).  S3: the full quadratic reduction of the ensemble, Eq. s3,
+ * S_bar3(r_a, r_b) = (1/N) sum_x e_x(r_a) e_x(r_b) for every pair of half-window shifts: a
+ * K_half x K_half matrix per level, row-major, whose diagonal is S_bar2 (the Gram matrix of
+ * the ensemble, Sec. 3.4 footnote).  S3 is computed on the tensor cores (TF32 operands
+ * split in three products, FP32 accumulation) and needs the DIRECT or AUTO path. */
+enum { DMCR_DESC_S2 = 0, DMCR_DESC_S3 = 1 };
 enum { DMCR_INIT_CALLER = 0, DMCR_INIT_UNIFORM_SEEDED = 1 };
 
 /* Problem statement (Sec. 3.3): field size, window P_a per axis, multigrid levels. */
@@ -82,6 +89,7 @@ typedef struct {
                                 adjoint ry rows per shift chunk (1..16), adjoint chunk target
                                 limit (1..64), adjoint rx blocks of 8 shifts per chunk at most
                                 (1..32).  Results agree to rounding across shapes. */
+    int descriptor;          /* DMCR_DESC_S2 (default) or DMCR_DESC_S3 */
 } dmcr_params;
 
 /* Loss options (Sec. 3.1).  lambda = lambda0 * E (NORM) or lambda0 * E^2 (SQUARED). */

@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libdmcr.so")
 BUILD_DIR = os.path.join(PKG, "_build")
-SOURCES = ["corr.cu", "aux.cu", "fft.cu", "api.cu", "probe.cu"]
+SOURCES = ["corr.cu", "aux.cu", "fft.cu", "gram.cu", "api.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -23,6 +23,7 @@ c_int, c_int64, c_float, c_void_p, c_uint64, c_size_t = (ctypes.c_int, ctypes.c_
 DMCR_OK, DMCR_EINVAL, DMCR_ENOMEM, DMCR_ECUDA, DMCR_ENONFINITE, DMCR_ETIMEOUT, DMCR_ENOTSUP = range(7)
 DMCR_SOFT, DMCR_IDENTITY = 0, 1
 DMCR_PATH_AUTO, DMCR_PATH_DIRECT, DMCR_PATH_FFT = 0, 1, 2
+DMCR_DESC_S2, DMCR_DESC_S3 = 0, 1
 DMCR_LOSS_NORM, DMCR_LOSS_SQUARED = 0, 1
 DMCR_PROLONG_ADJOINT_ACCUMULATE, DMCR_PROLONG_INJECT = 0, 1
 DMCR_INIT_CALLER, DMCR_INIT_UNIFORM_SEEDED = 0, 1
@@ -32,7 +33,7 @@ OUT_NAMES = ("E", "E2", "Ebc", "lambda", "L", "rel_err")
 class dmcr_params(ctypes.Structure):
     _fields_ = [("ndim", c_int), ("n", c_int64 * 3), ("window", c_int * 3), ("levels", c_int),
                 ("threshold", c_int), ("alpha", c_float), ("level_weight_exp", c_float), ("path", c_int),
-                ("tune", c_int * 4)]
+                ("tune", c_int * 4), ("descriptor", c_int)]
 
 
 class dmcr_loss_opts(ctypes.Structure):
@@ -152,6 +153,7 @@ class Params:
     level_weight_exp: float = -1.0
     path: int = DMCR_PATH_AUTO
     tune: tuple = (0, 0, 0, 0)     # launch shape; 0 = built-in choice (see tune.py)
+    descriptor: int = DMCR_DESC_S2  # DMCR_DESC_S3: the K x K three-point matrix per level
 
     @property
     def ndim(self) -> int:
@@ -171,6 +173,7 @@ class Params:
         p.path = int(self.path)
         for i, t in enumerate(tuple(self.tune)[:4]):
             p.tune[i] = int(t)
+        p.descriptor = int(self.descriptor)
         return p
 
 

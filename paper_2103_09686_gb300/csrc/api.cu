@@ -137,6 +137,11 @@ struct Plan {
     size_t o_fx[MAX_LEVELS] = {}, o_fh[MAX_LEVELS] = {}, o_tw[MAX_LEVELS] = {}, o_dc[MAX_LEVELS] = {};
     bool any_fft = false;
     double fh2 = 0.0;          // f(1/2)^2 of the soft threshold (App. A mapping of the FFT path)
+    // three-point descriptor: per level E, E^T, W^T (hi/lo where split) and G hi/lo
+    int desc_kind = DMCR_DESC_S2;
+    int64_t s3Kpad = 0, s3Npad[MAX_LEVELS] = {};
+    size_t o_eh[MAX_LEVELS] = {}, o_el[MAX_LEVELS] = {}, o_eth[MAX_LEVELS] = {}, o_etl[MAX_LEVELS] = {},
+           o_w[MAX_LEVELS] = {}, o_gh[MAX_LEVELS] = {}, o_gl[MAX_LEVELS] = {};
     size_t bytes = 0;
 };
 
@@ -257,6 +262,11 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         return fail(DMCR_EINVAL, "tune = {0|8|16|32, 0..16, 0..64, 0..32} expected");
     if (p->threshold == DMCR_SOFT && !(p->alpha > 0.f && isfinite(p->alpha)))
         return fail(DMCR_EINVAL, "alpha must be positive and finite");
+    if (p->descriptor != DMCR_DESC_S2 && p->descriptor != DMCR_DESC_S3)
+        return fail(DMCR_EINVAL, "unknown descriptor %d", p->descriptor);
+    if (p->descriptor == DMCR_DESC_S3 && p->path == DMCR_PATH_FFT)
+        return fail(DMCR_ENOTSUP, "the three-point descriptor has no FFT path");
+    pl.desc_kind = p->descriptor;
     pl.ndim = p->ndim;
     pl.levels = p->levels;
     int64_t n[3];
@@ -299,20 +309,30 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         } else if (p->path == DMCR_PATH_AUTO && p->threshold == DMCR_IDENTITY && fft_sizes && fft_cheaper(g)) {
             g.fft = 1;
         }
+        if (pl.desc_kind == DMCR_DESC_S3) {
+            g.fft = 0;
+            g.nChunks = 1;   // the gather kernel writes the whole level gradient
+        }
         if (g.fft) {
             g.nChunks = 1;
             pl.any_fft = true;
         }
-        if (!g.fft && p->threshold == DMCR_IDENTITY && g.n[2] % T != 0)
+        const bool direct2 = !g.fft && pl.desc_kind == DMCR_DESC_S2;
+        if (direct2 && p->threshold == DMCR_IDENTITY && g.n[2] % T != 0)
             return fail(DMCR_ENOTSUP, "the direct identity path needs the last axis of every level divisible by 8");
-        if (!g.fft && (fwd_smem_bytes(g) > (size_t)MAX_DYN_SMEM || adj_smem_bytes(g) > (size_t)MAX_DYN_SMEM))
+        if (direct2 && (fwd_smem_bytes(g) > (size_t)MAX_DYN_SMEM || adj_smem_bytes(g) > (size_t)MAX_DYN_SMEM))
             return fail(DMCR_ENOTSUP, "window too large for the shared-memory tiles of this build");
         pl.w[l] = (float)pow(2.0, we * l);
         pl.off[l] = off;
-        off += g.Khalf;
+        off += pl.desc_kind == DMCR_DESC_S3 ? g.Khalf * g.Khalf : g.Khalf;
     }
     pl.Ktot = off;
     pl.N1 = pl.g[0].N;
+    if (pl.desc_kind == DMCR_DESC_S3) {
+        if (pl.g[0].Khalf > 16384) return fail(DMCR_ENOTSUP, "three-point descriptor: at most 16384 shifts");
+        pl.s3Kpad = (pl.g[0].Khalf + 127) / 128 * 128;
+        for (int l = 0; l < pl.levels; ++l) pl.s3Npad[l] = (pl.g[l].N + 127) / 128 * 128;
+    }
     // threshold constants (FP64 on the host, rounded once)
     ThreshConst& tc = pl.tc;
     memset(&tc, 0, sizeof(tc));
@@ -351,10 +371,20 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             pl.o_fh[l] = o; o = align_up(o + (size_t)g.N * 16);
             pl.o_tw[l] = o; o = align_up(o + (size_t)(g.n[0] + g.n[1] + g.n[2]) * 16);
             pl.o_dc[l] = o; o = align_up(o + 16);
+        } else if (pl.desc_kind == DMCR_DESC_S3) {
+            const size_t Kp = (size_t)pl.s3Kpad, Np = (size_t)pl.s3Npad[l];
+            pl.o_eh[l] = o; o = align_up(o + Np * Kp * sizeof(float));
+            pl.o_el[l] = o; o = align_up(o + Np * Kp * sizeof(float));
+            pl.o_eth[l] = o; o = align_up(o + Np * Kp * sizeof(float));
+            pl.o_etl[l] = o; o = align_up(o + Np * Kp * sizeof(float));
+            pl.o_w[l] = o; o = align_up(o + Np * Kp * sizeof(float));
+            pl.o_gh[l] = o; o = align_up(o + Kp * Kp * sizeof(float));
+            pl.o_gl[l] = o; o = align_up(o + Kp * Kp * sizeof(float));
         } else {
             pl.o_fwd[l] = o; o = align_up(o + (size_t)g.fwdTiles * g.Khalf * sizeof(float));
         }
-        pl.o_gd[l] = o; o = align_up(o + (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * GBLOCK * sizeof(float));
+        if (pl.desc_kind == DMCR_DESC_S2)
+            pl.o_gd[l] = o, o = align_up(o + (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * GBLOCK * sizeof(float));
         pl.o_adj[l] = o; o = align_up(o + (size_t)g.nChunks * g.N * sizeof(float));
     }
     pl.bytes = o;
@@ -370,6 +400,7 @@ dmcr_status prepare_device() {
     if (std::find(ready.begin(), ready.end(), dev) != ready.end()) return DMCR_OK;
     set_kernel_attributes();
     set_fft_attributes();
+    set_gram_attributes();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute");
     ready.push_back(dev);
@@ -459,6 +490,7 @@ struct Prepared {
         float* part;
     };
     std::vector<FftJob> fftf, fftb;
+    std::vector<S3Job> s3f, s3b;
     template <typename S>
     const S* at(size_t off) const { return reinterpret_cast<const S*>(tab + off); }
 };
@@ -485,6 +517,32 @@ Prepared::FftJob fft_job(const Inst& x, int l) {
     j.weight = pl.w[l];
     j.mode = pl.tc.identity ? 0 : 1;
     j.fh2 = pl.fh2;
+    return j;
+}
+
+S3Job s3_job(const Inst& x, int l, bool loss) {
+    const Plan& pl = *x.pl;
+    S3Job j{};
+    j.g = pl.g[l];
+    j.field = x.lv[l];
+    j.K = pl.g[l].Khalf;
+    j.Kpad = pl.s3Kpad;
+    j.Npad = pl.s3Npad[l];
+    j.Eh = reinterpret_cast<float*>(x.ws + pl.o_eh[l]);
+    j.El = reinterpret_cast<float*>(x.ws + pl.o_el[l]);
+    j.Eth = reinterpret_cast<float*>(x.ws + pl.o_eth[l]);
+    j.Etl = reinterpret_cast<float*>(x.ws + pl.o_etl[l]);
+    j.W = reinterpret_cast<float*>(x.ws + pl.o_w[l]);
+    j.Gh = reinterpret_cast<float*>(x.ws + pl.o_gh[l]);
+    j.Gl = reinterpret_cast<float*>(x.ws + pl.o_gl[l]);
+    j.desc = x.desc + pl.off[l];
+    j.src = loss ? x.desc + pl.off[l] : x.target + pl.off[l];
+    j.sub = loss ? x.target + pl.off[l] : nullptr;
+    j.sc = loss ? x.sc : nullptr;
+    j.weight = pl.w[l];
+    j.part = reinterpret_cast<float*>(x.ws + pl.o_adj[l]);
+    j.done = x.use_done ? &x.sc->done : nullptr;
+    j.err = &x.sc->err;
     return j;
 }
 
@@ -543,6 +601,10 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         for (const Inst& x : in)
             for (int l = 0; l < x.pl->levels; ++l) {
                 const LevelGeom& g = x.pl->g[l];
+                if (x.pl->desc_kind == DMCR_DESC_S3) {
+                    P.s3f.push_back(s3_job(x, l, true));
+                    continue;
+                }
                 if (g.fft) {
                     P.fftf.push_back(fft_job(x, l));
                     continue;
@@ -616,8 +678,18 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
             for (int a = 0; a < 3; ++a) fa.n1[a] = x.pl->g[0].n[a];
             for (int l = 0; l < x.pl->levels; ++l) {
                 const LevelGeom& g = x.pl->g[l];
-                float* Gd = reinterpret_cast<float*>(x.ws + x.pl->o_gd[l]);
                 float* part = reinterpret_cast<float*>(x.ws + x.pl->o_adj[l]);
+                if (x.pl->desc_kind == DMCR_DESC_S3) {
+                    S3Job j = s3_job(x, l, !vjp);
+                    j.ens = (flags & F_FWD) ? 0 : 1;
+                    P.s3b.push_back(j);
+                    fa.parts[l] = part;
+                    fa.nChunks[l] = 1;
+                    fa.Nl[l] = g.N;
+                    for (int a = 0; a < 3; ++a) fa.nl[l][a] = g.n[a];
+                    continue;
+                }
+                float* Gd = reinterpret_cast<float*>(x.ws + x.pl->o_gd[l]);
                 GSeg gs{};
                 gs.g = g;
                 gs.src = vjp ? x.target + x.pl->off[l] : x.desc + x.pl->off[l];
@@ -785,6 +857,10 @@ void run(const Prepared& P, cudaStream_t s) {
             ProfScope ps("fft_descriptor", -1, s);
             for (const Prepared::FftJob& j : P.fftf) fft_descriptor(j, s);
         }
+        if (!P.s3f.empty()) {
+            ProfScope ps("s3_gram", -1, s);
+            for (const S3Job& j : P.s3f) launch_s3_forward(j, P.tc, j.err, s);
+        }
     }
     if (P.flags & F_LOSS) {
         {
@@ -806,6 +882,10 @@ void run(const Prepared& P, cudaStream_t s) {
         if (!P.fftb.empty()) {
             ProfScope ps("fft_vjp", -1, s);
             for (const Prepared::FftJob& j : P.fftb) fft_vjp(j, s);
+        }
+        if (!P.s3b.empty()) {
+            ProfScope ps("s3_adjoint", -1, s);
+            for (const S3Job& j : P.s3b) launch_s3_backward(j, P.tc, j.err, s);
         }
         ProfScope ps((P.flags & F_ADAM) ? "grad_adam" : "grad_assemble", -1, s);
         launch_final(P.at<FinalSeg>(P.fin.off), P.fin.nseg, P.fin.blocks, s);
@@ -969,9 +1049,11 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
             r.iterations = (int)(hs[i].adam_step - states[i].step);
             r.converged = hs[i].done == 1;
             for (int k = 0; k < DMCR_OUT_COUNT; ++k) r.loss[k] = hs[i].loss[k];
-            r.status = hs[i].done == 2 ? DMCR_ENONFINITE : DMCR_OK;
+            r.status = hs[i].err ? DMCR_ETIMEOUT : (hs[i].done == 2 ? DMCR_ENONFINITE : DMCR_OK);
             states[i].step = hs[i].adam_step;
-            if (hs[i].done == 2 && !per_instance_status)
+            if (hs[i].err && !per_instance_status)
+                st = fail(DMCR_ETIMEOUT, "a bounded tensor-core wait timed out in instance %d", i);
+            else if (hs[i].done == 2 && !per_instance_status)
                 st = fail(DMCR_ENONFINITE, "loss became non-finite in instance %d", i);
         }
     } while (0);
@@ -1366,6 +1448,8 @@ extern "C" dmcr_status dmcr_descriptor_noalloc(const dmcr_params* p, const float
     Plan pl;
     DMCR_TRY(validate_and_plan(p, pl));
     if (field == nullptr || desc == nullptr) return fail(DMCR_EINVAL, "field/desc is NULL");
+    if (pl.desc_kind != DMCR_DESC_S2 || pl.any_fft)
+        return fail(DMCR_ENOTSUP, "dmcr_descriptor_noalloc computes the direct two-point descriptor only");
     // compact layout: segment tables, pyramid levels 2.. and the forward partials of every level
     Plan cp = pl;
     size_t o = 0;

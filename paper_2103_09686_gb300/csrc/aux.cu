@@ -252,6 +252,7 @@ __global__ void scalars_init_kernel(const InitSeg* __restrict__ segs, int nseg) 
     sc->adam_step = segs[i].step;
     sc->b1t = segs[i].b1t;
     sc->b2t = segs[i].b2t;
+    sc->err = 0;
 }
 
 void launch_scalars_init(const InitSeg* segs, int nseg, cudaStream_t s) {

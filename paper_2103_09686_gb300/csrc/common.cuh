@@ -64,6 +64,7 @@ struct Scalars {
     int iter;             // iterations evaluated in this call
     int64_t adam_step;    // Adam steps taken (global, for bias correction)
     double b1t, b2t;      // beta1^adam_step, beta2^adam_step (running products)
+    int err;              // set when a bounded tensor-core wait timed out
 };
 
 struct LossParams {
@@ -170,6 +171,41 @@ struct InitSeg {
     double b1t, b2t;
 };
 
+// Three-point descriptor, one (instance, level) (gram.cu).  K = half-window shifts,
+// Kpad and Npad = K and the level's position count rounded up to 128.
+struct S3Job {
+    LevelGeom g;
+    const float* field;     // this level's field
+    int64_t K, Kpad, Npad;
+    float *Eh, *El;         // E (Npad x Kpad), TF32-exact high part and remainder
+    float *Eth, *Etl;       // E^T (Kpad x Npad)
+    float* W;               // W^T (Kpad x Npad)
+    float *Gh, *Gl;         // G (Kpad x Kpad)
+    float* desc;            // this level's K x K block of the descriptor (w * S_bar3)
+    const float* src;       // G = weight * (sc ? gscale : 1) * (src - sub): src = desc (loss) or
+    const float* sub;       //   the upstream gradient (VJP, sub = null, sc = null)
+    const Scalars* sc;
+    float weight;
+    float* part;            // this level's gradient
+    const int* done;
+    int ens;                // backward: build E first (no forward ran in this call)
+    int* err;               // set on a tensor-core wait timeout
+};
+
+// C = scale * A B^T on the tensor cores (gram.cu); see tc_gemm_kernel.
+struct GemmArgs {
+    const float *Ah, *Al, *Bh, *Bl;
+    int64_t lda, ldb;
+    int M, N, K;
+    float scale;
+    float* C;
+    int64_t ldc;
+    int mode;               // 0 C[m][n], 1 symmetric Gram (upper tiles, mirrored), 2 C[n][m]
+    int Mvalid, Nvalid;
+    const int* done;
+    int* err;
+};
+
 // One mixed-radix Stockham pass over the lines of one axis (fft.cu).
 struct FftPass {
     double2* data;            // complex grid, transformed in place
@@ -203,6 +239,11 @@ void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, cudaStream_t s
 void launch_init_uniform(float* field, int64_t count, uint64_t seed, cudaStream_t s);
 void launch_scalars_init(const InitSeg* segs, int nseg, cudaStream_t s);
 void set_kernel_attributes();
+void set_gram_attributes();
+size_t gemm_smem_bytes();
+void launch_tc_gemm(const GemmArgs& a, cudaStream_t s);
+void launch_s3_forward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s);
+void launch_s3_backward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s);
 void set_fft_attributes();
 size_t fft_smem_bytes(int len, int L);
 int fft_lines_per_block(int len);

@@ -1,0 +1,454 @@
+// Three-point descriptor (sm_103a): the quadratic reduction of the ensemble, Eq. s3,
+//     S_bar3(r_a, r_b) = (1/N) sum_x e_x(r_a) e_x(r_b),   e_x(r) = f((M_x + M_{x+r}) / 2),
+// i.e. the Gram matrix E^T E / N of the N x K ensemble (paper, Sec. 3.2.2-3.2.4 and the
+// footnote of Sec. 3.4), and the gradient of a loss on it.
+//
+//   ens_kernel      e and f' never leave the chip except as the GEMM operands: E (N x K)
+//                   and E^T (K x N), each split into a TF32-exact high part and the FP32
+//                   remainder (e = hi + lo exactly);
+//   tc_gemm_kernel  C = A B^T on the 5th-generation tensor cores: tcgen05.mma kind::tf32
+//                   from shared memory, FP32 accumulators in TMEM drained every 256
+//                   reduction steps into FP32 registers, three products
+//                   hi*hi + hi*lo + lo*hi per k-step (error ~2^-21 relative per product),
+//                   operands staged by cp.async in two stages, one thread issues the MMAs
+//                   and commits them to an mbarrier per stage;
+//                   Gram:  S_bar3 = Et Et^T w/N (upper-triangle tiles, mirrored);
+//                   W:     W^T = (2/N) G E^T  as  E G^T with a transposed epilogue;
+//   g3_split_kernel G = w * gscale * (D3 - D3_des) symmetrised (or the upstream gradient),
+//                   split like E;
+//   s3_gather_kernel g_y = sum_r 1/2 [W(r, y) f'(a_y(r)) + W(r, y - r) f'(a_{y-r}(r))]
+//                   (weight 1 at r = 0), the two ends of every shift vector.
+// Every wait on an mbarrier is bounded; a timeout sets an error flag that the host reads.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace dmcr {
+
+namespace {
+
+constexpr int GM = 128, GN = 128, GK = 32;            // tile: 128 x 128 outputs, 32 reduction steps
+constexpr int TILE_BYTES = GM * GK * 4;                // one operand tile, 16 KB
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;            // A hi, A lo, B hi, B lo
+constexpr int GSTAGES = 2;
+constexpr int GEMM_THREADS = 128;
+constexpr uint32_t TMEM_COLS = 256;                    // two FP32 accumulators of 128 lanes x 128 columns
+// The tensor core adds into its FP32 accumulator without round-to-nearest: over a long
+// reduction the error is biased toward zero (~4e-8 relative per accumulation measured on
+// GB300).  So TMEM accumulates at most FLUSH k-blocks (FLUSH * 32 reduction steps) before the
+// partial sums are added, rounded to nearest, into FP32 registers; the small cross terms
+// hi*lo + lo*hi accumulate separately from hi*hi.
+constexpr int FLUSH = 8;
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+// instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2),
+// both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(GN >> 3) << 17) |
+                                ((uint32_t)(GM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// bounded wait for the completion of the mbarrier phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// whole warp: allocate TMEM columns, address written to shared memory
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// shared-memory matrix descriptor, no swizzle: start address, LBO (next 16-byte chunk along
+// K), SBO (next group of 8 rows), descriptor version 1
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(IDESC_TF32), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 16 columns of 32 bits: thread i of the warp gets lane (lane base + i)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void split_tf32(float e, float& hi, float& lo) {
+    hi = __uint_as_float(__float_as_uint(e) & 0xFFFFE000u);
+    lo = e - hi;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------- GEMM
+
+// C = scale * A B^T with A (M x K) and B (N x K) row-major (K contiguous), each given as
+// hi + lo.  M, N multiples of 128, K a multiple of 32, strides multiples of 4 floats.
+// mode 0: C[m][n]; mode 1 (Gram, A = B): only tiles bn >= bm, written to C[m][n] and C[n][m];
+// mode 2: C[n][m].  Entries with m >= Mvalid or n >= Nvalid are not written.
+__global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g) {
+    if (g.done != nullptr && *g.done) return;
+    extern __shared__ __align__(1024) uint8_t gsm[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + GSTAGES * STAGE_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + GSTAGES + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tilesM = g.M / GM;
+    int bm, bn;
+    if (g.mode == 1) {
+        // upper triangle, row by row: tiles (bm, bn >= bm)
+        int64_t t = blockIdx.x;
+        bm = 0;
+        while (t >= tilesM - bm) {
+            t -= tilesM - bm;
+            ++bm;
+        }
+        bn = bm + (int)t;
+    } else {
+        bm = (int)(blockIdx.x % tilesM);
+        bn = (int)(blockIdx.x / tilesM);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < GSTAGES + 1; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    const int nk = g.K / GK;
+    const float* srcs[4] = {g.Ah + (int64_t)bm * GM * g.lda, g.Al + (int64_t)bm * GM * g.lda,
+                            g.Bh + (int64_t)bn * GN * g.ldb, g.Bl + (int64_t)bn * GN * g.ldb};
+    // stage layout per operand tile: 16-byte chunk (row r, k-chunk kc) at
+    // ((r / 8) * 8 + kc) * 128 + (r % 8) * 16 bytes: core matrices of 8 rows x 16 bytes,
+    // LBO = 128 (next k-chunk), SBO = 1024 (next 8 rows)
+    auto load_stage = [&](int kb, int s) {
+        uint8_t* st = gsm + s * STAGE_BYTES;
+        const int64_t k0 = (int64_t)kb * GK;
+        for (int i = tid; i < 4 * (TILE_BYTES / 16); i += GEMM_THREADS) {
+            const int t = i / (TILE_BYTES / 16), c = i % (TILE_BYTES / 16);
+            const int r8 = c & 7, kc = (c >> 3) & 7, rg = c >> 6;
+            const int row = rg * 8 + r8;
+            const int64_t ld = t < 2 ? g.lda : g.ldb;
+            cp16(smem_u32(st + t * TILE_BYTES + (rg * 8 + kc) * 128 + r8 * 16), srcs[t] + row * ld + k0 + 4 * kc);
+        }
+        cp_commit();
+    };
+
+    bool ok = true;
+    float acc[GN];
+#pragma unroll
+    for (int c = 0; c < GN; ++c) acc[c] = 0.f;
+    uint64_t* fbar = bars + GSTAGES;   // flush barrier
+    const uint32_t t_main = tmem, t_cross = tmem + GN;
+    int flushes = 0;
+    load_stage(0, 0);
+    for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb & 1;
+        if (kb + 1 < nk) {
+            // the stage about to be refilled was read by the MMAs of step kb - 1
+            if (kb >= 1) ok = mbar_wait(&bars[s ^ 1], ((kb - 1) >> 1) & 1) && ok;
+            load_stage(kb + 1, s ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        fence_async_smem();
+        __syncthreads();
+        const bool flush = (kb % FLUSH == FLUSH - 1) || kb == nk - 1;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t st = smem_u32(gsm + s * STAGE_BYTES);
+#pragma unroll
+            for (int ks = 0; ks < GK / 8; ++ks) {
+                const uint32_t off = ks * 256;   // 8 TF32 = two 16-byte chunks per k-step
+                const uint64_t ah = smem_desc(st + 0 * TILE_BYTES + off, 128, 1024);
+                const uint64_t al = smem_desc(st + 1 * TILE_BYTES + off, 128, 1024);
+                const uint64_t bh = smem_desc(st + 2 * TILE_BYTES + off, 128, 1024);
+                const uint64_t bl = smem_desc(st + 3 * TILE_BYTES + off, 128, 1024);
+                const uint32_t more = (kb % FLUSH != 0) || ks != 0;
+                mma_tf32(t_main, ah, bh, more);
+                mma_tf32(t_cross, ah, bl, more);
+                mma_tf32(t_cross, al, bh, 1);
+            }
+            mma_commit(&bars[s]);
+            if (flush) mma_commit(fbar);
+        }
+        if (flush) {
+            ok = mbar_wait(fbar, flushes & 1) && ok;
+            ++flushes;
+            tc_fence_after();
+            if (ok) {
+#pragma unroll
+                for (int c = 0; c < GN; c += 16) {
+                    float vm[16], vc[16];
+                    tmem_ld16(t_main + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, vm);
+                    tmem_ld16(t_cross + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, vc);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[c + j] += vm[j] + vc[j];
+                }
+            }
+            tc_fence_before();
+            __syncthreads();   // TMEM is read before the next period overwrites it
+        }
+    }
+    // every stage commit has completed (the last flush waited for all MMAs); consume the
+    // outstanding stage-barrier phases so no arrival is pending at exit
+    if (nk >= 2) ok = mbar_wait(&bars[(nk - 2) & 1], ((nk - 2) >> 1) & 1) && ok;
+    ok = mbar_wait(&bars[(nk - 1) & 1], ((nk - 1) >> 1) & 1) && ok;
+
+    if (ok) {
+        const int m = bm * GM + 32 * warp + lane;
+        if (m < g.Mvalid) {
+#pragma unroll
+            for (int c = 0; c < GN; ++c) {
+                const int n = bn * GN + c;
+                if (n >= g.Nvalid) continue;
+                const float x = g.scale * acc[c];
+                if (g.mode == 2) {
+                    g.C[(int64_t)n * g.ldc + m] = x;
+                } else {
+                    g.C[(int64_t)m * g.ldc + n] = x;
+                    if (g.mode == 1 && bm != bn) g.C[(int64_t)n * g.ldc + m] = x;
+                }
+            }
+        }
+    } else if (tid == 0 && g.err != nullptr) {
+        atomicExch(g.err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ------------------------------------------------------------------------- ensemble
+
+// shift k of the canonical half window -> (rz, ry, rx); inverse of canon_index
+__host__ __device__ inline void decode_shift(const LevelGeom& g, int64_t k, int& rz, int& ry, int& rx) {
+    const int Px = g.P[2], Py = g.P[1];
+    const int64_t wx = 2 * Px + 1, wy = 2 * Py + 1;
+    if (k <= Px) {
+        rz = 0; ry = 0; rx = (int)k;
+        return;
+    }
+    k -= Px + 1;
+    if (k < (int64_t)Py * wx) {
+        rz = 0; ry = 1 + (int)(k / wx); rx = (int)(k % wx) - Px;
+        return;
+    }
+    k -= (int64_t)Py * wx;
+    rz = 1 + (int)(k / (wy * wx));
+    k %= wy * wx;
+    ry = (int)(k / wx) - Py;
+    rx = (int)(k % wx) - Px;
+}
+
+__device__ __forceinline__ int64_t partner(const LevelGeom& g, int64_t x, int rz, int ry, int rx) {
+    const int64_t n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    const int64_t z = x / (n1 * n2), y = (x / n2) % n1, c = x % n2;
+    int64_t pz = (z + rz) % n0, py = (y + ry) % n1, pc = (c + rx) % n2;
+    if (pz < 0) pz += n0;
+    if (py < 0) py += n1;
+    if (pc < 0) pc += n2;
+    return (pz * n1 + py) * n2 + pc;
+}
+
+// s = sigma(alpha (a - 0.75)) for a = (u + v) / 2, exact form (any finite range)
+__device__ __forceinline__ float sig_pair(const ThreshConst& tc, float u, float v) {
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fmaf(-tc.kappa, u + v, tc.cexp)));
+    float s;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(e + 1.0f));
+    return s;
+}
+
+// one block: 32 positions x 32 shifts, written to E^T (coalesced over positions) and E
+// (coalesced over shifts) through a shared transpose; padding entries are 0
+__global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
+    if (j.done != nullptr && *j.done) return;
+    __shared__ float th[32][33], tl[32][33];
+    const LevelGeom& g = j.g;
+    const int64_t x0 = (int64_t)(blockIdx.x % (j.Npad / 32)) * 32;
+    const int64_t k0 = (int64_t)(blockIdx.x / (j.Npad / 32)) * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    const int64_t x = x0 + tx;
+    for (int kk = ty; kk < 32; kk += 8) {
+        const int64_t k = k0 + kk;
+        float e = 0.f;
+        if (x < g.N && k < j.K) {
+            int rz, ry, rx;
+            decode_shift(g, k, rz, ry, rx);
+            const float u = j.field[x], v = j.field[partner(g, x, rz, ry, rx)];
+            e = tc.identity ? 0.5f * (u + v) : fmaf(tc.c1, sig_pair(tc, u, v), tc.c3);
+        }
+        float hi, lo;
+        split_tf32(e, hi, lo);
+        j.Eth[k * j.Npad + x] = hi;
+        j.Etl[k * j.Npad + x] = lo;
+        th[kk][tx] = hi;
+        tl[kk][tx] = lo;
+    }
+    __syncthreads();
+    for (int xx = ty; xx < 32; xx += 8) {
+        j.Eh[(x0 + xx) * j.Kpad + k0 + tx] = th[tx][xx];
+        j.El[(x0 + xx) * j.Kpad + k0 + tx] = tl[tx][xx];
+    }
+}
+
+// G = w * gscale * sym(D3 - D3_des) on the level's K x K block (zero padding to Kpad), split
+__global__ void g3_split_kernel(S3Job j) {
+    if (j.done != nullptr && *j.done) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)j.Kpad * j.Kpad) return;
+    const int64_t a = i / j.Kpad, b = i % j.Kpad;
+    float v = 0.f;
+    if (a < j.K && b < j.K) {
+        // d<G, E^T E>/dE = E (G + G^T): symmetrise (the loss gradient already is symmetric)
+        const float dab = j.src[a * j.K + b] - (j.sub != nullptr ? j.sub[a * j.K + b] : 0.f);
+        const float dba = j.src[b * j.K + a] - (j.sub != nullptr ? j.sub[b * j.K + a] : 0.f);
+        v = j.weight * (j.sc != nullptr ? j.sc->gscale : 1.f) * 0.5f * (dab + dba);
+    }
+    float hi, lo;
+    split_tf32(v, hi, lo);
+    j.Gh[i] = hi;
+    j.Gl[i] = lo;
+}
+
+// g_y = sum_k c_k [W(k, y) f'(a_y(r_k)) + W(k, y - r_k) f'(a_{y - r_k}(r_k))], c_0 = 1/2 (the two
+// terms coincide at r = 0), c_k = 1/2 otherwise; f' = c1 alpha s (1 - s), or 1 for f(x) = x
+__global__ void __launch_bounds__(256) s3_gather_kernel(S3Job j, ThreshConst tc) {
+    if (j.done != nullptr && *j.done) return;
+    const LevelGeom& g = j.g;
+    const int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= g.N) return;
+    const float c1a = tc.c1 * tc.alpha;
+    const float my = j.field[y];
+    float acc = 0.f;
+    for (int64_t k = 0; k < j.K; ++k) {
+        int rz, ry, rx;
+        decode_shift(g, k, rz, ry, rx);
+        const int64_t yp = partner(g, y, rz, ry, rx);      // y + r
+        const int64_t ym = partner(g, y, -rz, -ry, -rx);   // y - r
+        float d1 = 1.f, d2 = 1.f;
+        if (!tc.identity) {
+            const float s1 = sig_pair(tc, my, j.field[yp]);
+            const float s2 = sig_pair(tc, j.field[ym], my);
+            d1 = c1a * s1 * (1.f - s1);
+            d2 = c1a * s2 * (1.f - s2);
+        }
+        acc = fmaf(0.5f * j.W[k * j.Npad + y], d1, acc);
+        acc = fmaf(0.5f * j.W[k * j.Npad + ym], d2, acc);
+    }
+    j.part[y] = acc;
+}
+
+// ------------------------------------------------------------------------- launchers
+
+size_t gemm_smem_bytes() { return (size_t)GSTAGES * STAGE_BYTES + 256; }
+
+void set_gram_attributes() {
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
+}
+
+void launch_tc_gemm(const GemmArgs& a, cudaStream_t s) {
+    const int64_t tm = a.M / GM, tn = a.N / GN;
+    const int64_t blocks = a.mode == 1 ? tm * (tm + 1) / 2 : tm * tn;
+    if (blocks <= 0) return;
+    tc_gemm_kernel<<<(unsigned)blocks, GEMM_THREADS, gemm_smem_bytes(), s>>>(a);
+}
+
+void launch_s3_forward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s) {
+    ens_kernel<<<(unsigned)((j.Npad / 32) * (j.Kpad / 32)), 256, 0, s>>>(j, tc);
+    GemmArgs a{};
+    a.Ah = j.Eth; a.Al = j.Etl; a.Bh = j.Eth; a.Bl = j.Etl;
+    a.lda = a.ldb = j.Npad;
+    a.M = a.N = (int)j.Kpad;
+    a.K = (int)j.Npad;
+    a.scale = (float)((double)j.weight / (double)j.g.N);
+    a.C = j.desc;
+    a.ldc = j.K;
+    a.mode = 1;
+    a.Mvalid = a.Nvalid = (int)j.K;
+    a.done = j.done;
+    a.err = err;
+    launch_tc_gemm(a, s);
+}
+
+void launch_s3_backward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s) {
+    if (j.ens) ens_kernel<<<(unsigned)((j.Npad / 32) * (j.Kpad / 32)), 256, 0, s>>>(j, tc);
+    const int64_t nG = j.Kpad * j.Kpad;
+    g3_split_kernel<<<(unsigned)((nG + 255) / 256), 256, 0, s>>>(j);
+    GemmArgs a{};
+    a.Ah = j.Eh; a.Al = j.El; a.Bh = j.Gh; a.Bl = j.Gl;
+    a.lda = j.Kpad;
+    a.ldb = j.Kpad;
+    a.M = (int)j.Npad;
+    a.N = (int)j.Kpad;
+    a.K = (int)j.Kpad;
+    a.scale = (float)(2.0 / (double)j.g.N);
+    a.C = j.W;
+    a.ldc = j.Npad;
+    a.mode = 2;
+    a.Mvalid = (int)j.Npad;
+    a.Nvalid = (int)j.Kpad;
+    a.done = j.done;
+    a.err = err;
+    launch_tc_gemm(a, s);
+    s3_gather_kernel<<<(unsigned)((j.g.N + 255) / 256), 256, 0, s>>>(j, tc);
+}
+
+}  // namespace dmcr
