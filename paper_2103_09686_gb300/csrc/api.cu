@@ -311,7 +311,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         }
         if (pl.desc_kind == DMCR_DESC_S3) {
             g.fft = 0;
-            g.nChunks = 1;   // the gather kernel writes the whole level gradient
+            g.nChunks = (int)ceil_div(g.Khalf, S3_SHIFTS);   // gather partials, one per shift chunk
         }
         if (g.fft) {
             g.nChunks = 1;
@@ -684,7 +684,7 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
                     j.ens = (flags & F_FWD) ? 0 : 1;
                     P.s3b.push_back(j);
                     fa.parts[l] = part;
-                    fa.nChunks[l] = 1;
+                    fa.nChunks[l] = g.nChunks;
                     fa.Nl[l] = g.N;
                     for (int a = 0; a < 3; ++a) fa.nl[l][a] = g.n[a];
                     continue;

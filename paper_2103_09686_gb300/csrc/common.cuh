@@ -11,6 +11,7 @@ constexpr int FWD_THREADS = 128;
 constexpr int ADJ_THREADS = 128;   // 32 row pairs (lane, lane + 32) x 4 strips of 8 positions
 constexpr int ADJ_ROWS = 64;       // adjoint tile rows
 constexpr int GBLOCK = 48;         // coefficient floats per block of 8 shifts (packed pairs)
+constexpr int S3_SHIFTS = 64;      // three-point gradient gather: shifts per partial sum
 
 // offset of C_m inside a coefficient block: (C_m, C_m, C_m+1, C_m+1) after the 8 (A, A, B, B)
 __host__ __device__ inline int gblock_c(int m) { return 4 * T + 2 * m; }

@@ -369,16 +369,20 @@ __global__ void g3_split_kernel(S3Job j) {
 }
 
 // g_y = sum_k c_k [W(k, y) f'(a_y(r_k)) + W(k, y - r_k) f'(a_{y - r_k}(r_k))], c_0 = 1/2 (the two
-// terms coincide at r = 0), c_k = 1/2 otherwise; f' = c1 alpha s (1 - s), or 1 for f(x) = x
+// terms coincide at r = 0), c_k = 1/2 otherwise; f' = c1 alpha s (1 - s), or 1 for f(x) = x.
+// Block (position block, shift chunk of S3_SHIFTS): per-chunk partials, summed in a fixed order
+// by the gradient assembly.
 __global__ void __launch_bounds__(256) s3_gather_kernel(S3Job j, ThreshConst tc) {
     if (j.done != nullptr && *j.done) return;
     const LevelGeom& g = j.g;
     const int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= g.N) return;
+    const int64_t kA = (int64_t)blockIdx.y * S3_SHIFTS;
+    const int64_t kB = min(kA + (int64_t)S3_SHIFTS, j.K);
     const float c1a = tc.c1 * tc.alpha;
     const float my = j.field[y];
     float acc = 0.f;
-    for (int64_t k = 0; k < j.K; ++k) {
+    for (int64_t k = kA; k < kB; ++k) {
         int rz, ry, rx;
         decode_shift(g, k, rz, ry, rx);
         const int64_t yp = partner(g, y, rz, ry, rx);      // y + r
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(256) s3_gather_kernel(S3Job j, ThreshConst tc)
         acc = fmaf(0.5f * j.W[k * j.Npad + y], d1, acc);
         acc = fmaf(0.5f * j.W[k * j.Npad + ym], d2, acc);
     }
-    j.part[y] = acc;
+    j.part[(int64_t)blockIdx.y * g.N + y] = acc;
 }
 
 // ------------------------------------------------------------------------- launchers
@@ -448,7 +452,8 @@ void launch_s3_backward(const S3Job& j, const ThreshConst& tc, int* err, cudaStr
     a.done = j.done;
     a.err = err;
     launch_tc_gemm(a, s);
-    s3_gather_kernel<<<(unsigned)((j.g.N + 255) / 256), 256, 0, s>>>(j, tc);
+    const dim3 grid((unsigned)((j.g.N + 255) / 256), (unsigned)((j.K + S3_SHIFTS - 1) / S3_SHIFTS));
+    s3_gather_kernel<<<grid, 256, 0, s>>>(j, tc);
 }
 
 }  // namespace dmcr
