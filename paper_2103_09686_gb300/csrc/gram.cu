@@ -10,7 +10,8 @@
 //                   from shared memory, FP32 accumulators in TMEM drained every 256
 //                   reduction steps into FP32 registers, three products
 //                   hi*hi + hi*lo + lo*hi per k-step (error ~2^-21 relative per product),
-//                   operands staged by cp.async in two stages, one thread issues the MMAs
+//                   operands staged by cp.async in three stages (128-byte swizzled
+//                   K-major layout), one thread issues the MMAs
 //                   and commits them to an mbarrier per stage;
 //                   Gram:  S_bar3 = Et Et^T w/N (upper-triangle tiles, mirrored);
 //                   W:     W^T = (2/N) G E^T  as  E G^T with a transposed epilogue;
@@ -30,7 +31,7 @@ namespace {
 constexpr int GM = 128, GN = 128, GK = 32;            // tile: 128 x 128 outputs, 32 reduction steps
 constexpr int TILE_BYTES = GM * GK * 4;                // one operand tile, 16 KB
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;            // A hi, A lo, B hi, B lo
-constexpr int GSTAGES = 2;
+constexpr int GSTAGES = 3;
 constexpr int GEMM_THREADS = 128;
 constexpr uint32_t TMEM_COLS = 256;                    // two FP32 accumulators of 128 lanes x 128 columns
 // The tensor core adds into its FP32 accumulator without round-to-nearest: over a long
@@ -90,11 +91,14 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// shared-memory matrix descriptor, no swizzle: start address, LBO (next 16-byte chunk along
-// K), SBO (next group of 8 rows), descriptor version 1
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-           (1ull << 46);
+// shared-memory matrix descriptor, K-major with the 128-byte swizzle: each operand row is
+// one 128-byte line (32 TF32) whose 16-byte chunks are stored at chunk ^ (row % 8); atoms of
+// 8 rows (1024 bytes, 1024-byte aligned) follow each other at SBO = 1024; LBO is unused by
+// this layout (encoded 1); descriptor version 1, layout type 2 (SWIZZLE_128B).  A k-step of
+// 8 TF32 starts 32 bytes further into the line.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
@@ -141,7 +145,9 @@ __device__ __forceinline__ void split_tf32(float e, float& hi, float& lo) {
 // mode 2: C[n][m].  Entries with m >= Mvalid or n >= Nvalid are not written.
 __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g) {
     if (g.done != nullptr && *g.done) return;
-    extern __shared__ __align__(1024) uint8_t gsm[];
+    extern __shared__ __align__(1024) uint8_t gsm_raw[];
+    // the swizzle atoms need 1024-byte aligned tiles
+    uint8_t* gsm = gsm_raw + ((1024 - (smem_u32(gsm_raw) & 1023)) & 1023);
     uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + GSTAGES * STAGE_BYTES);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + GSTAGES + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -173,18 +179,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g) {
     const int nk = g.K / GK;
     const float* srcs[4] = {g.Ah + (int64_t)bm * GM * g.lda, g.Al + (int64_t)bm * GM * g.lda,
                             g.Bh + (int64_t)bn * GN * g.ldb, g.Bl + (int64_t)bn * GN * g.ldb};
-    // stage layout per operand tile: 16-byte chunk (row r, k-chunk kc) at
-    // ((r / 8) * 8 + kc) * 128 + (r % 8) * 16 bytes: core matrices of 8 rows x 16 bytes,
-    // LBO = 128 (next k-chunk), SBO = 1024 (next 8 rows)
+    // stage layout per operand tile: row r (32 TF32 = 128 bytes) at r * 128, its 16-byte chunk
+    // kc at ((kc ^ (r % 8)) * 16): eight consecutive threads copy one row (a full 128-byte line
+    // from global memory) into eight distinct bank groups
     auto load_stage = [&](int kb, int s) {
         uint8_t* st = gsm + s * STAGE_BYTES;
         const int64_t k0 = (int64_t)kb * GK;
         for (int i = tid; i < 4 * (TILE_BYTES / 16); i += GEMM_THREADS) {
             const int t = i / (TILE_BYTES / 16), c = i % (TILE_BYTES / 16);
-            const int r8 = c & 7, kc = (c >> 3) & 7, rg = c >> 6;
-            const int row = rg * 8 + r8;
+            const int row = c >> 3, kc = c & 7;
             const int64_t ld = t < 2 ? g.lda : g.ldb;
-            cp16(smem_u32(st + t * TILE_BYTES + (rg * 8 + kc) * 128 + r8 * 16), srcs[t] + row * ld + k0 + 4 * kc);
+            cp16(smem_u32(st + t * TILE_BYTES + row * 128 + ((kc ^ (row & 7)) << 4)), srcs[t] + row * ld + k0 + 4 * kc);
         }
         cp_commit();
     };
@@ -196,17 +201,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g) {
     uint64_t* fbar = bars + GSTAGES;   // flush barrier
     const uint32_t t_main = tmem, t_cross = tmem + GN;
     int flushes = 0;
-    load_stage(0, 0);
+    // prologue: steps 0 .. GSTAGES-2 in flight (one commit group each, possibly empty)
+    for (int p = 0; p < GSTAGES - 1; ++p) {
+        if (p < nk) load_stage(p, p);
+        else cp_commit();
+    }
     for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb & 1;
-        if (kb + 1 < nk) {
-            // the stage about to be refilled was read by the MMAs of step kb - 1
-            if (kb >= 1) ok = mbar_wait(&bars[s ^ 1], ((kb - 1) >> 1) & 1) && ok;
-            load_stage(kb + 1, s ^ 1);
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
+        const int s = kb % GSTAGES;
+        cp_wait<GSTAGES - 2>();   // step kb's group has landed
         fence_async_smem();
         __syncthreads();
         const bool flush = (kb % FLUSH == FLUSH - 1) || kb == nk - 1;
@@ -215,11 +217,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g) {
             const uint32_t st = smem_u32(gsm + s * STAGE_BYTES);
 #pragma unroll
             for (int ks = 0; ks < GK / 8; ++ks) {
-                const uint32_t off = ks * 256;   // 8 TF32 = two 16-byte chunks per k-step
-                const uint64_t ah = smem_desc(st + 0 * TILE_BYTES + off, 128, 1024);
-                const uint64_t al = smem_desc(st + 1 * TILE_BYTES + off, 128, 1024);
-                const uint64_t bh = smem_desc(st + 2 * TILE_BYTES + off, 128, 1024);
-                const uint64_t bl = smem_desc(st + 3 * TILE_BYTES + off, 128, 1024);
+                const uint32_t off = ks * 32;   // 8 TF32 = 32 bytes per k-step
+                const uint64_t ah = smem_desc_sw128(st + 0 * TILE_BYTES + off);
+                const uint64_t al = smem_desc_sw128(st + 1 * TILE_BYTES + off);
+                const uint64_t bh = smem_desc_sw128(st + 2 * TILE_BYTES + off);
+                const uint64_t bl = smem_desc_sw128(st + 3 * TILE_BYTES + off);
                 const uint32_t more = (kb % FLUSH != 0) || ks != 0;
                 mma_tf32(t_main, ah, bh, more);
                 mma_tf32(t_cross, ah, bl, more);
@@ -227,6 +229,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g) {
             }
             mma_commit(&bars[s]);
             if (flush) mma_commit(fbar);
+        }
+        // refill the stage read by step kb - 1 with step kb + GSTAGES - 1 while step kb's MMAs
+        // are queued on the tensor core
+        const int kn = kb + GSTAGES - 1;
+        if (kn < nk) {
+            if (kb >= 1) ok = mbar_wait(&bars[(kb - 1) % GSTAGES], ((kb - 1) / GSTAGES) & 1) && ok;
+            load_stage(kn, kn % GSTAGES);
+        } else {
+            cp_commit();   // one group per step keeps the wait above uniform
         }
         if (flush) {
             ok = mbar_wait(fbar, flushes & 1) && ok;
@@ -247,9 +258,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g) {
         }
     }
     // every stage commit has completed (the last flush waited for all MMAs); consume the
-    // outstanding stage-barrier phases so no arrival is pending at exit
-    if (nk >= 2) ok = mbar_wait(&bars[(nk - 2) & 1], ((nk - 2) >> 1) & 1) && ok;
-    ok = mbar_wait(&bars[(nk - 1) & 1], ((nk - 1) >> 1) & 1) && ok;
+    // stage-barrier phases not yet waited for so no arrival is pending at exit
+    // (the loop waited for steps 0 .. nk - GSTAGES - 1; each of the last GSTAGES steps sits on
+    // its own barrier, one phase ahead of the last one waited for)
+    for (int kb = nk > GSTAGES ? nk - GSTAGES : 0; kb < nk; ++kb)
+        ok = mbar_wait(&bars[kb % GSTAGES], (kb / GSTAGES) & 1) && ok;
+    cp_wait<0>();
 
     if (ok) {
         const int m = bm * GM + 32 * warp + lane;
@@ -402,7 +416,7 @@ __global__ void __launch_bounds__(256) s3_gather_kernel(S3Job j, ThreshConst tc)
 
 // ------------------------------------------------------------------------- launchers
 
-size_t gemm_smem_bytes() { return (size_t)GSTAGES * STAGE_BYTES + 256; }
+size_t gemm_smem_bytes() { return (size_t)GSTAGES * STAGE_BYTES + 1024 + 256; }
 
 void set_gram_attributes() {
     cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
