@@ -160,6 +160,67 @@ def main_crossover(args):
     return 0
 
 
+def main_s3(args):
+    """Three-point descriptor (Eq. s3) at the paper's App. B configurations, P = 31:
+    64^2 (one level), 128^2 (two) and 256^2 (three).  A step is one descriptor + loss +
+    gradient + Adam iteration (dmcr_adam_step), timed with CUDA events after warm-up, L2
+    flushed before every step.  The tensor-core rate counts the executed TF32 MMA flops of
+    the two GEMMs (Gram on the upper-triangle tiles, W), three split products each, over
+    the step time; the peak is the measured bf16 burst peak x the nominal TF32 / BF16 ratio
+    1.1 / 2.25."""
+    import torch
+    import paper_2103_09686_gb300 as dm
+    dm.load()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    tf32_peak = bf16 * 1.1 / 2.25
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = []
+    for n, levels in ((64, 1), (128, 2), (256, 3)):
+        P = 31
+        p = dm.Params(shape=(n, n), window=(P, P), levels=levels, descriptor=dm.DMCR_DESC_S3)
+        ws = dm.workspace(p)
+        T = torch.tensor(synthetic.checkerboard(n, 8), dtype=torch.float32, device="cuda")
+        D = dm.descriptor(T, p, ws)
+        f = torch.tensor(synthetic.uniform_field((n, n), 1), dtype=torch.float32, device="cuda")
+        m = torch.zeros_like(f)
+        v = torch.zeros_like(f)
+        opts = dm.ReconOpts(lr=1e-3)
+        st = 0
+        for _ in range(3):
+            st = dm.dmcr_adam_step(p, opts, D, f, m, v, st, None, ws)
+        steps = 20 if n < 256 else 8
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            st = dm.dmcr_adam_step(p, opts, D, f, m, v, st, None, ws)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        ms = float(np.median(times))
+        K = (2 * P + 1) * (2 * P + 1) // 2 + 1
+        Kp = (K + 127) // 128 * 128
+        flops = 0.0
+        for l in range(levels):
+            Np = ((n >> l) ** 2 + 127) // 128 * 128
+            t = Kp // 128
+            flops += 3 * 2.0 * (t * (t + 1) // 2) * 128 * 128 * Np      # Gram, upper tiles
+            flops += 3 * 2.0 * Np * Kp * Kp                               # W = E G
+        achieved = flops / (ms / 1e3) / 1e12
+        out.append({"workload": "%dx%d, P=%d, %d level(s), K=%d" % (n, n, P, levels, K), "ms_per_step": ms,
+                    "steps_per_s": 1e3 / ms,
+                    "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                                 "frac": achieved / tf32_peak,
+                                 "basis": "executed TF32 MMA flops of both GEMMs (3 split products) / step time; "
+                                          "peak = measured bf16 %.0f TF/s x 1.1/2.25" % bf16}})
+    print(json.dumps({"metric": "three-point descriptor Adam steps/s", "unit": "steps/s", "dtype": "tf32x3",
+                      "data": "synthetic", "l2": "flushed before every timed step", "runs": out}))
+    return 0
+
+
 def main_checkerboard(args):
     """Sec. 4.1 checkerboard experiments on 64 x 64 with P = 31 (App. B), 8-pixel squares:
     iterations until the rounded field's descriptor equals the target (relative error
@@ -346,6 +407,7 @@ def main():
     ap.add_argument("--pipes", action="store_true", help="measured MUFU / FMA rates per SM per clock")
     ap.add_argument("--tune", action="store_true", help="launch shapes from the autotuner (measured, cached)")
     ap.add_argument("--checkerboard", action="store_true", help="Sec. 4.1 checkerboard E1/E2 reconstructions")
+    ap.add_argument("--s3", action="store_true", help="three-point descriptor steps at the paper's P = 31 configurations")
     args = ap.parse_args()
     if args.pipes:
         import ctypes
@@ -362,6 +424,8 @@ def main():
         return main_crossover(args)
     if args.checkerboard:
         return main_checkerboard(args)
+    if args.s3:
+        return main_s3(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
