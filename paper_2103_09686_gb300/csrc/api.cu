@@ -266,6 +266,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         return fail(DMCR_EINVAL, "unknown descriptor %d", p->descriptor);
     if (p->descriptor == DMCR_DESC_S3 && p->path == DMCR_PATH_FFT)
         return fail(DMCR_ENOTSUP, "the three-point descriptor has no FFT path");
+
     pl.desc_kind = p->descriptor;
     pl.ndim = p->ndim;
     pl.levels = p->levels;
@@ -558,6 +559,9 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         x.lv[0] = x.field;
         for (int l = 1; l < x.pl->levels; ++l) x.lv[l] = reinterpret_cast<const float*>(x.ws + x.pl->o_pyr[l]);
     }
+    for (const Inst& x : in)
+        if (x.pl->desc_kind == DMCR_DESC_S3 && !gram_ready())
+            return fail(DMCR_ENOTSUP, "the three-point descriptor needs the driver's TMA tensor-map encoder");
     const bool need_pyr = (flags & (F_FWD | F_BACK)) != 0;
     if ((flags & (F_LOSS | F_BACK)) != 0)
         for (const Inst& x : in)

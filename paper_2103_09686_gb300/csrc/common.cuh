@@ -193,20 +193,6 @@ struct S3Job {
     int* err;               // set on a tensor-core wait timeout
 };
 
-// C = scale * A B^T on the tensor cores (gram.cu); see tc_gemm_kernel.
-struct GemmArgs {
-    const float *Ah, *Al, *Bh, *Bl;
-    int64_t lda, ldb;
-    int M, N, K;
-    float scale;
-    float* C;
-    int64_t ldc;
-    int mode;               // 0 C[m][n], 1 symmetric Gram (upper tiles, mirrored), 2 C[n][m]
-    int Mvalid, Nvalid;
-    const int* done;
-    int* err;
-};
-
 // One mixed-radix Stockham pass over the lines of one axis (fft.cu).
 struct FftPass {
     double2* data;            // complex grid, transformed in place
@@ -242,7 +228,7 @@ void launch_scalars_init(const InitSeg* segs, int nseg, cudaStream_t s);
 void set_kernel_attributes();
 void set_gram_attributes();
 size_t gemm_smem_bytes();
-void launch_tc_gemm(const GemmArgs& a, cudaStream_t s);
+bool gram_ready();   // the TMA tensor-map encoder is available
 void launch_s3_forward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s);
 void launch_s3_backward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s);
 void set_fft_attributes();

@@ -20,11 +20,43 @@
 //   s3_gather_kernel g_y = sum_r 1/2 [W(r, y) f'(a_y(r)) + W(r, y - r) f'(a_{y-r}(r))]
 //                   (weight 1 at r = 0), the two ends of every shift vector.
 // Every wait on an mbarrier is bounded; a timeout sets an error flag that the host reads.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <cstdio>
+#include <mutex>
 
 #include "common.cuh"
 
 namespace dmcr {
+
+// C = scale * A B^T on the tensor cores (see tc_gemm_kernel): operands as TMA tensor maps
+struct GemmArgs {
+    CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+    int M, N, K;
+    float scale;
+    float* C;
+    int64_t ldc;
+    int mode;               // 0 C[m][n], 1 symmetric Gram (upper tiles, mirrored), 2 C[n][m]
+    int Mvalid, Nvalid;
+    const int* done;
+    int* err;
+};
+
+// the same with plain device pointers (host side)
+struct GemmOperands {
+    const float *Ah, *Al, *Bh, *Bl;
+    int64_t lda, ldb;
+    int M, N, K;
+    float scale;
+    float* C;
+    int64_t ldc;
+    int mode;
+    int Mvalid, Nvalid;
+    const int* done;
+    int* err;
+};
 
 namespace {
 
@@ -32,8 +64,8 @@ constexpr int GM = 128, GN = 128, GK = 32;            // tile: 128 x 128 outputs
 constexpr int TILE_BYTES = GM * GK * 4;                // one operand tile, 16 KB
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;            // A hi, A lo, B hi, B lo
 constexpr int GSTAGES = 3;
-constexpr int GEMM_THREADS = 128;
-constexpr uint32_t TMEM_COLS = 256;                    // two FP32 accumulators of 128 lanes x 128 columns
+constexpr int GEMM_THREADS = 192;                     // warps 0-3 epilogue, 4 TMA, 5 MMA
+constexpr uint32_t TMEM_COLS = 512;                    // 2 buffers x (main + cross) FP32, 128 lanes x 128 columns each
 // The tensor core adds into its FP32 accumulator without round-to-nearest: over a long
 // reduction the error is biased toward zero (~4e-8 relative per accumulation measured on
 // GB300).  So TMEM accumulates at most FLUSH k-blocks (FLUSH * 32 reduction steps) before the
@@ -49,12 +81,21 @@ constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void cp16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// 2-D tiled TMA load of one box into shared memory, completion counted on an mbarrier
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -76,7 +117,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -140,16 +180,26 @@ __device__ __forceinline__ void split_tf32(float e, float& hi, float& lo) {
 // ------------------------------------------------------------------------- GEMM
 
 // C = scale * A B^T with A (M x K) and B (N x K) row-major (K contiguous), each given as
-// hi + lo.  M, N multiples of 128, K a multiple of 32, strides multiples of 4 floats.
-// mode 0: C[m][n]; mode 1 (Gram, A = B): only tiles bn >= bm, written to C[m][n] and C[n][m];
-// mode 2: C[n][m].  Entries with m >= Mvalid or n >= Nvalid are not written.
-__global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g) {
+// hi + lo through four TMA tensor maps (box 32 x 128, 128-byte swizzle).  M, N multiples of
+// 128, K a multiple of 32.  mode 0: C[m][n]; mode 1 (Gram, A = B): only tiles bn >= bm,
+// written to C[m][n] and C[n][m]; mode 2: C[n][m].  Entries with m >= Mvalid or
+// n >= Nvalid are not written.
+//
+// Warp roles: warp 4 (one lane) loads the stages with TMA; warp 5 (one lane) issues the MMAs
+// and commits them; warps 0-3 drain the TMEM accumulators every FLUSH k-blocks into FP32
+// registers (TMEM is double-buffered: two periods of main + cross accumulators, 512
+// columns) and write the tile.  Barriers: full[s] (TMA bytes landed), empty[s] (MMAs done
+// reading stage s), tfull[b] (period finished in TMEM buffer b), tempty[b] (buffer b read).
+__global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_constant__ GemmArgs g) {
     if (g.done != nullptr && *g.done) return;
     extern __shared__ __align__(1024) uint8_t gsm_raw[];
     // the swizzle atoms need 1024-byte aligned tiles
     uint8_t* gsm = gsm_raw + ((1024 - (smem_u32(gsm_raw) & 1023)) & 1023);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + GSTAGES * STAGE_BYTES);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + GSTAGES + 1);
+    uint64_t* full = reinterpret_cast<uint64_t*>(gsm + GSTAGES * STAGE_BYTES);
+    uint64_t* empty = full + GSTAGES;
+    uint64_t* tfull = empty + GSTAGES;
+    uint64_t* tempty = tfull + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tilesM = g.M / GM;
     int bm, bn;
@@ -167,107 +217,100 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g) {
         bn = (int)(blockIdx.x / tilesM);
     }
     if (tid == 0) {
-        for (int s = 0; s < GSTAGES + 1; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < GSTAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4 * 32);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(tslot, TMEM_COLS);
+    if (warp == 5) tmem_alloc(tslot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-
     const int nk = g.K / GK;
-    const float* srcs[4] = {g.Ah + (int64_t)bm * GM * g.lda, g.Al + (int64_t)bm * GM * g.lda,
-                            g.Bh + (int64_t)bn * GN * g.ldb, g.Bl + (int64_t)bn * GN * g.ldb};
-    // stage layout per operand tile: row r (32 TF32 = 128 bytes) at r * 128, its 16-byte chunk
-    // kc at ((kc ^ (r % 8)) * 16): eight consecutive threads copy one row (a full 128-byte line
-    // from global memory) into eight distinct bank groups
-    auto load_stage = [&](int kb, int s) {
-        uint8_t* st = gsm + s * STAGE_BYTES;
-        const int64_t k0 = (int64_t)kb * GK;
-        for (int i = tid; i < 4 * (TILE_BYTES / 16); i += GEMM_THREADS) {
-            const int t = i / (TILE_BYTES / 16), c = i % (TILE_BYTES / 16);
-            const int row = c >> 3, kc = c & 7;
-            const int64_t ld = t < 2 ? g.lda : g.ldb;
-            cp16(smem_u32(st + t * TILE_BYTES + row * 128 + ((kc ^ (row & 7)) << 4)), srcs[t] + row * ld + k0 + 4 * kc);
-        }
-        cp_commit();
-    };
-
+    const int nper = (nk + FLUSH - 1) / FLUSH;
     bool ok = true;
-    float acc[GN];
-#pragma unroll
-    for (int c = 0; c < GN; ++c) acc[c] = 0.f;
-    uint64_t* fbar = bars + GSTAGES;   // flush barrier
-    const uint32_t t_main = tmem, t_cross = tmem + GN;
-    int flushes = 0;
-    // prologue: steps 0 .. GSTAGES-2 in flight (one commit group each, possibly empty)
-    for (int p = 0; p < GSTAGES - 1; ++p) {
-        if (p < nk) load_stage(p, p);
-        else cp_commit();
-    }
-    for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % GSTAGES;
-        cp_wait<GSTAGES - 2>();   // step kb's group has landed
-        fence_async_smem();
-        __syncthreads();
-        const bool flush = (kb % FLUSH == FLUSH - 1) || kb == nk - 1;
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t st = smem_u32(gsm + s * STAGE_BYTES);
-#pragma unroll
-            for (int ks = 0; ks < GK / 8; ++ks) {
-                const uint32_t off = ks * 32;   // 8 TF32 = 32 bytes per k-step
-                const uint64_t ah = smem_desc_sw128(st + 0 * TILE_BYTES + off);
-                const uint64_t al = smem_desc_sw128(st + 1 * TILE_BYTES + off);
-                const uint64_t bh = smem_desc_sw128(st + 2 * TILE_BYTES + off);
-                const uint64_t bl = smem_desc_sw128(st + 3 * TILE_BYTES + off);
-                const uint32_t more = (kb % FLUSH != 0) || ks != 0;
-                mma_tf32(t_main, ah, bh, more);
-                mma_tf32(t_cross, ah, bl, more);
-                mma_tf32(t_cross, al, bh, 1);
+
+    if (warp == 4) {
+        // ---- TMA producer
+        if (lane == 0) {
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % GSTAGES;
+                if (kb >= GSTAGES) ok = mbar_wait(&empty[s], ((kb / GSTAGES) - 1) & 1);
+                if (!ok) break;
+                uint8_t* st = gsm + s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                const int k0 = kb * GK;
+                tma_load_2d(st + 0 * TILE_BYTES, &g.ta_hi, k0, bm * GM, &full[s]);
+                tma_load_2d(st + 1 * TILE_BYTES, &g.ta_lo, k0, bm * GM, &full[s]);
+                tma_load_2d(st + 2 * TILE_BYTES, &g.tb_hi, k0, bn * GN, &full[s]);
+                tma_load_2d(st + 3 * TILE_BYTES, &g.tb_lo, k0, bn * GN, &full[s]);
             }
-            mma_commit(&bars[s]);
-            if (flush) mma_commit(fbar);
+            // no copy may still be in flight at exit: the last stages' bytes have landed
+            for (int kb = nk > GSTAGES ? nk - GSTAGES : 0; kb < nk; ++kb)
+                mbar_wait(&full[kb % GSTAGES], (kb / GSTAGES) & 1);
         }
-        // refill the stage read by step kb - 1 with step kb + GSTAGES - 1 while step kb's MMAs
-        // are queued on the tensor core
-        const int kn = kb + GSTAGES - 1;
-        if (kn < nk) {
-            if (kb >= 1) ok = mbar_wait(&bars[(kb - 1) % GSTAGES], ((kb - 1) / GSTAGES) & 1) && ok;
-            load_stage(kn, kn % GSTAGES);
-        } else {
-            cp_commit();   // one group per step keeps the wait above uniform
-        }
-        if (flush) {
-            ok = mbar_wait(fbar, flushes & 1) && ok;
-            ++flushes;
-            tc_fence_after();
-            if (ok) {
+        __syncwarp();
+    } else if (warp == 5) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % GSTAGES;
+                const int p = kb / FLUSH, buf = p & 1;
+                // TMEM buffer buf was last used by period p - 2: wait until it was read
+                if (kb % FLUSH == 0 && p >= 2) ok = mbar_wait(&tempty[buf], ((p / 2) - 1) & 1);
+                if (ok) ok = mbar_wait(&full[s], (kb / GSTAGES) & 1);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t st = smem_u32(gsm + s * STAGE_BYTES);
+                const uint32_t t_main = tmem + (uint32_t)buf * (2 * GN), t_cross = t_main + GN;
 #pragma unroll
-                for (int c = 0; c < GN; c += 16) {
-                    float vm[16], vc[16];
-                    tmem_ld16(t_main + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, vm);
-                    tmem_ld16(t_cross + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, vc);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[c + j] += vm[j] + vc[j];
+                for (int ks = 0; ks < GK / 8; ++ks) {
+                    const uint32_t off = ks * 32;   // 8 TF32 = 32 bytes per k-step
+                    const uint64_t ah = smem_desc_sw128(st + 0 * TILE_BYTES + off);
+                    const uint64_t al = smem_desc_sw128(st + 1 * TILE_BYTES + off);
+                    const uint64_t bh = smem_desc_sw128(st + 2 * TILE_BYTES + off);
+                    const uint64_t bl = smem_desc_sw128(st + 3 * TILE_BYTES + off);
+                    const uint32_t more = (kb % FLUSH != 0) || ks != 0;
+                    mma_tf32(t_main, ah, bh, more);
+                    mma_tf32(t_cross, ah, bl, more);
+                    mma_tf32(t_cross, al, bh, 1);
                 }
+                mma_commit(&empty[s]);
+                if (kb % FLUSH == FLUSH - 1 || kb == nk - 1) mma_commit(&tfull[buf]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warps 0-3 own TMEM lanes 32 w .. 32 w + 31 = tile rows
+        float acc[GN];
+#pragma unroll
+        for (int c = 0; c < GN; ++c) acc[c] = 0.f;
+        for (int p = 0; p < nper; ++p) {
+            const int buf = p & 1;
+            // warp-uniform decision: tcgen05.ld below is .sync.aligned
+            ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], (p / 2) & 1));
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t t_main = tmem + (uint32_t)buf * (2 * GN) + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+            for (int c = 0; c < GN; c += 16) {
+                float vm[16], vc[16];
+                tmem_ld16(t_main + (uint32_t)c, vm);
+                tmem_ld16(t_main + GN + (uint32_t)c, vc);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[c + j] += vm[j] + vc[j];
             }
             tc_fence_before();
-            __syncthreads();   // TMEM is read before the next period overwrites it
+            mbar_arrive(&tempty[buf]);
         }
-    }
-    // every stage commit has completed (the last flush waited for all MMAs); consume the
-    // stage-barrier phases not yet waited for so no arrival is pending at exit
-    // (the loop waited for steps 0 .. nk - GSTAGES - 1; each of the last GSTAGES steps sits on
-    // its own barrier, one phase ahead of the last one waited for)
-    for (int kb = nk > GSTAGES ? nk - GSTAGES : 0; kb < nk; ++kb)
-        ok = mbar_wait(&bars[kb % GSTAGES], (kb / GSTAGES) & 1) && ok;
-    cp_wait<0>();
-
-    if (ok) {
         const int m = bm * GM + 32 * warp + lane;
-        if (m < g.Mvalid) {
+        if (ok && m < g.Mvalid) {
 #pragma unroll
             for (int c = 0; c < GN; ++c) {
                 const int n = bn * GN + c;
@@ -281,12 +324,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g) {
                 }
             }
         }
-    } else if (tid == 0 && g.err != nullptr) {
-        atomicExch(g.err, 1);
     }
+    if (!ok && g.err != nullptr) atomicExch(g.err, 1);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    if (warp == 5) tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // ------------------------------------------------------------------------- ensemble
@@ -422,16 +464,66 @@ void set_gram_attributes() {
     cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
 }
 
-void launch_tc_gemm(const GemmArgs& a, cudaStream_t s) {
-    const int64_t tm = a.M / GM, tn = a.N / GN;
-    const int64_t blocks = a.mode == 1 ? tm * (tm + 1) / 2 : tm * tn;
+__global__ void set_flag_kernel(int* flag, int v) {
+    if (flag != nullptr) *flag = v;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// rows x cols FP32 row-major (row stride ld elements), boxes of 128 rows x 32 columns
+bool make_map(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, int64_t ld) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (enc == nullptr) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)GK, (cuuint32_t)GM};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool gram_ready() { return tensor_map_encoder() != nullptr; }
+
+void launch_tc_gemm(const GemmOperands& o, cudaStream_t s) {
+    const int64_t tm = o.M / GM, tn = o.N / GN;
+    const int64_t blocks = o.mode == 1 ? tm * (tm + 1) / 2 : tm * tn;
     if (blocks <= 0) return;
+    GemmArgs a{};
+    const bool ok = make_map(&a.ta_hi, o.Ah, o.M, o.K, o.lda) && make_map(&a.ta_lo, o.Al, o.M, o.K, o.lda) &&
+                    make_map(&a.tb_hi, o.Bh, o.N, o.K, o.ldb) && make_map(&a.tb_lo, o.Bl, o.N, o.K, o.ldb);
+    if (!ok) {
+        // no valid tensor map: never launch TMA on it; report through the error word
+        set_flag_kernel<<<1, 1, 0, s>>>(o.err, 2);
+        return;
+    }
+    a.M = o.M; a.N = o.N; a.K = o.K;
+    a.scale = o.scale;
+    a.C = o.C;
+    a.ldc = o.ldc;
+    a.mode = o.mode;
+    a.Mvalid = o.Mvalid; a.Nvalid = o.Nvalid;
+    a.done = o.done;
+    a.err = o.err;
     tc_gemm_kernel<<<(unsigned)blocks, GEMM_THREADS, gemm_smem_bytes(), s>>>(a);
 }
 
 void launch_s3_forward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s) {
     ens_kernel<<<(unsigned)((j.Npad / 32) * (j.Kpad / 32)), 256, 0, s>>>(j, tc);
-    GemmArgs a{};
+    GemmOperands a{};
     a.Ah = j.Eth; a.Al = j.Etl; a.Bh = j.Eth; a.Bl = j.Etl;
     a.lda = a.ldb = j.Npad;
     a.M = a.N = (int)j.Kpad;
@@ -450,7 +542,7 @@ void launch_s3_backward(const S3Job& j, const ThreshConst& tc, int* err, cudaStr
     if (j.ens) ens_kernel<<<(unsigned)((j.Npad / 32) * (j.Kpad / 32)), 256, 0, s>>>(j, tc);
     const int64_t nG = j.Kpad * j.Kpad;
     g3_split_kernel<<<(unsigned)((nG + 255) / 256), 256, 0, s>>>(j);
-    GemmArgs a{};
+    GemmOperands a{};
     a.Ah = j.Eh; a.Al = j.El; a.Bh = j.Gh; a.Bl = j.Gl;
     a.lda = j.Kpad;
     a.ldb = j.Kpad;
