@@ -107,25 +107,33 @@ __global__ void stats_kernel(const PenSeg* __restrict__ segs) {
     __shared__ double sh[256];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double r2 = 0.0, t2 = 0.0, e2 = 0.0;
+    // per-thread compensated (Kahan) FP32 sums in a fixed order -- FP64 arithmetic is slow on
+    // this part and a thread sums only K / 65536 terms -- then FP64 across the block
+    float r2 = 0.f, r2c = 0.f, t2 = 0.f, t2c = 0.f, e2 = 0.f, e2c = 0.f;
+    auto kahan = [](float& sum, float& comp, float v) {
+        const float y = v - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    };
     for (int64_t k = i0; k < sg.K; k += stride) {
-        const double t = (double)sg.target[k];
-        const double r = (double)sg.desc[k] - t;
-        r2 += r * r;
-        t2 += t * t;
+        const float t = sg.target[k];
+        const float r = sg.desc[k] - t;
+        kahan(r2, r2c, r * r);
+        kahan(t2, t2c, t * t);
     }
     if (sg.field != nullptr)
         for (int64_t i = i0; i < sg.N; i += stride) {
-            const double e = (double)box_excess(sg.field[i]);
-            e2 += e * e;
+            const float e = box_excess(sg.field[i]);
+            kahan(e2, e2c, e * e);
         }
-    r2 = block_sum_d(r2, sh);
-    t2 = block_sum_d(t2, sh);
-    e2 = block_sum_d(e2, sh);
+    const double R2 = block_sum_d((double)r2 - (double)r2c, sh);
+    const double T2 = block_sum_d((double)t2 - (double)t2c, sh);
+    const double E2 = block_sum_d((double)e2 - (double)e2c, sh);
     if (threadIdx.x == 0) {
-        sg.partials[3 * blockIdx.x + 0] = r2;
-        sg.partials[3 * blockIdx.x + 1] = t2;
-        sg.partials[3 * blockIdx.x + 2] = e2;
+        sg.partials[3 * blockIdx.x + 0] = R2;
+        sg.partials[3 * blockIdx.x + 1] = T2;
+        sg.partials[3 * blockIdx.x + 2] = E2;
     }
 }
 

@@ -333,34 +333,54 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
 
 // ------------------------------------------------------------------------- ensemble
 
-// shift k of the canonical half window -> (rz, ry, rx); inverse of canon_index
-__host__ __device__ inline void decode_shift(const LevelGeom& g, int64_t k, int& rz, int& ry, int& rx) {
+// shift k of the canonical half window -> (rz, ry, rx); inverse of canon_index (32-bit: the
+// half window holds at most 2^14 shifts here)
+__device__ __forceinline__ void decode_shift(const LevelGeom& g, int k, int& rz, int& ry, int& rx) {
     const int Px = g.P[2], Py = g.P[1];
-    const int64_t wx = 2 * Px + 1, wy = 2 * Py + 1;
+    const int wx = 2 * Px + 1, wy = 2 * Py + 1;
     if (k <= Px) {
-        rz = 0; ry = 0; rx = (int)k;
+        rz = 0; ry = 0; rx = k;
         return;
     }
     k -= Px + 1;
-    if (k < (int64_t)Py * wx) {
-        rz = 0; ry = 1 + (int)(k / wx); rx = (int)(k % wx) - Px;
+    if (k < Py * wx) {
+        rz = 0; ry = 1 + k / wx; rx = k % wx - Px;
         return;
     }
-    k -= (int64_t)Py * wx;
-    rz = 1 + (int)(k / (wy * wx));
+    k -= Py * wx;
+    rz = 1 + k / (wy * wx);
     k %= wy * wx;
-    ry = (int)(k / wx) - Py;
-    rx = (int)(k % wx) - Px;
+    ry = k / wx - Py;
+    rx = k % wx - Px;
 }
 
-__device__ __forceinline__ int64_t partner(const LevelGeom& g, int64_t x, int rz, int ry, int rx) {
-    const int64_t n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
-    const int64_t z = x / (n1 * n2), y = (x / n2) % n1, c = x % n2;
-    int64_t pz = (z + rz) % n0, py = (y + ry) % n1, pc = (c + rx) % n2;
-    if (pz < 0) pz += n0;
-    if (py < 0) py += n1;
-    if (pc < 0) pc += n2;
-    return (pz * n1 + py) * n2 + pc;
+// position coordinates of a level (z, y, c), 32-bit (levels hold < 2^31 positions)
+struct Pos3 {
+    int z, y, c;
+};
+
+__device__ __forceinline__ Pos3 pos_of(const LevelGeom& g, int64_t x) {
+    const int n12 = (int)(g.n[1] * g.n[2]), n2 = (int)g.n[2];
+    const int xi = (int)x;
+    Pos3 p;
+    p.z = xi / n12;
+    const int r = xi - p.z * n12;
+    p.y = r / n2;
+    p.c = r - p.y * n2;
+    return p;
+}
+
+// v + d wrapped into [0, n) for |d| <= n (windows never exceed half a level)
+__device__ __forceinline__ int wrap_add(int v, int d, int n) {
+    int w = v + d;
+    w = w >= n ? w - n : w;
+    return w < 0 ? w + n : w;
+}
+
+// linear index of p + (rz, ry, rx), periodic
+__device__ __forceinline__ int64_t partner(const LevelGeom& g, const Pos3& p, int rz, int ry, int rx) {
+    const int n0 = (int)g.n[0], n1 = (int)g.n[1], n2 = (int)g.n[2];
+    return ((int64_t)wrap_add(p.z, rz, n0) * n1 + wrap_add(p.y, ry, n1)) * n2 + wrap_add(p.c, rx, n2);
 }
 
 // s = sigma(alpha (a - 0.75)) for a = (u + v) / 2, exact form (any finite range)
@@ -382,13 +402,16 @@ __global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
     const int64_t k0 = (int64_t)(blockIdx.x / (j.Npad / 32)) * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     const int64_t x = x0 + tx;
+    const bool xin = x < g.N;
+    const Pos3 px = pos_of(g, xin ? x : 0);
+    const float u = xin ? j.field[x] : 0.f;
     for (int kk = ty; kk < 32; kk += 8) {
         const int64_t k = k0 + kk;
         float e = 0.f;
-        if (x < g.N && k < j.K) {
+        if (xin && k < j.K) {
             int rz, ry, rx;
-            decode_shift(g, k, rz, ry, rx);
-            const float u = j.field[x], v = j.field[partner(g, x, rz, ry, rx)];
+            decode_shift(g, (int)k, rz, ry, rx);
+            const float v = j.field[partner(g, px, rz, ry, rx)];
             e = tc.identity ? 0.5f * (u + v) : fmaf(tc.c1, sig_pair(tc, u, v), tc.c3);
         }
         float hi, lo;
@@ -437,12 +460,13 @@ __global__ void __launch_bounds__(256) s3_gather_kernel(S3Job j, ThreshConst tc)
     const int64_t kB = min(kA + (int64_t)S3_SHIFTS, j.K);
     const float c1a = tc.c1 * tc.alpha;
     const float my = j.field[y];
+    const Pos3 py = pos_of(g, y);
     float acc = 0.f;
     for (int64_t k = kA; k < kB; ++k) {
         int rz, ry, rx;
-        decode_shift(g, k, rz, ry, rx);
-        const int64_t yp = partner(g, y, rz, ry, rx);      // y + r
-        const int64_t ym = partner(g, y, -rz, -ry, -rx);   // y - r
+        decode_shift(g, (int)k, rz, ry, rx);
+        const int64_t yp = partner(g, py, rz, ry, rx);      // y + r
+        const int64_t ym = partner(g, py, -rz, -ry, -rx);   // y - r
         float d1 = 1.f, d2 = 1.f;
         if (!tc.identity) {
             const float s1 = sig_pair(tc, my, j.field[yp]);
