@@ -30,6 +30,11 @@ What each function follows (sections and equations of the paper):
   reduction, Eq. s3: S_bar3(r_a, r_b) = (1/N) sum_x e_x(r_a) e_x(r_b), the Gram matrix of
   the ensemble (Sec. 3.4's footnote), on the half window of every level; the exact gradient
   of a loss on it by the chain rule.
+* ``s2tilde_map`` / ``descriptor_tilde`` / ``tilde_loss_grad`` -- the corrected two-point
+  descriptor of App. A, Eq. s2rfroms2rbar: S_tilde(0) = S_bar(0) and
+  S_tilde(r) = (S_bar(r) - 2 f(1/2)^2 S_bar(0)) / (1 - 2 f(1/2)^2), a linear map of every
+  level's block, and the gradient of a loss on it (the map's transpose, then the S_bar
+  gradient).
 * ``s2_count`` / ``s3_count`` / ``s3_from_s3bar`` -- exact two- and three-point
   probabilities of a binary field by counting (Sec. 3.2.1) and App. A's mapping from
   S_bar3 back to S3 (Eq. s3rfroms3rbar).
@@ -505,3 +510,54 @@ def s3_from_s3bar(s3b: float, s2a: float, s2b: float, s20: float, s2ab: float, f
     """App. A, Eq. s3rfroms3rbar, general case 0 != r_a != r_b != 0: S3 from S_bar3 and the
     exact two-point values S2(r_a), S2(r_b), S2(0) and S2(r_a - r_b), with fh = f(1/2)."""
     return (s3b - fh * (s2a + s2b) - fh * fh * (s20 - s2a - s2b + s2ab)) / (1.0 - 2.0 * fh)
+
+
+# ----------------------------------------------------------------------------- corrected S2
+
+def half_value(p: Params) -> float:
+    """f(1/2) of the threshold (1/2 for f(x) = x)."""
+    return float(threshold(np.array([0.5]), p.threshold, p.alpha)[0][0])
+
+
+def s2tilde_map(K: int, fh: float) -> np.ndarray:
+    """The K x K matrix A of App. A (Eq. s2rfroms2rbar) on one level's half-window block,
+    S_tilde = A S_bar: row 0 keeps S_bar(0); row k >= 1 is (e_k - 2 fh^2 e_0) / (1 - 2 fh^2)."""
+    q = 2.0 * fh * fh
+    A = np.eye(K) / (1.0 - q)
+    A[0, 0] = 1.0
+    A[1:, 0] = -q / (1.0 - q)
+    return A
+
+
+def descriptor_tilde(M, p: Params) -> np.ndarray:
+    """The corrected descriptor: every level block of ``descriptor`` mapped by A."""
+    D = descriptor(M, p)
+    K = half_window(p.ndim, p.window).shape[0]
+    A = s2tilde_map(K, half_value(p))
+    return np.concatenate([A @ D[l * K:(l + 1) * K] for l in range(p.levels)])
+
+
+def tilde_loss_grad(M, D_des, p: Params, mode: str = "norm", lambda0: float | None = None, bc: bool = True):
+    """Eq. L_func_dMCR on the corrected descriptor and its gradient: dL/dS_bar = A^T dL/dS_tilde
+    per level, then the two-point chain rule through all levels."""
+    M = np.asarray(M, dtype=np.float64)
+    N = M.size
+    D = descriptor_tilde(M, p)
+    out = loss(M, D_des, p, mode, lambda0, bc, D=D)
+    lam0 = out["lambda0"]
+    rho, E, Ebc = out["rho"], out["E"], out["Ebc"]
+    if mode == "norm":
+        dphi_dD = rho / E if E > 0 else np.zeros_like(rho)
+        phi = E
+    else:
+        dphi_dD = 2.0 * rho
+        phi = out["E2"]
+    gD = dphi_dD * (1.0 + lam0 * Ebc)
+    K = half_window(p.ndim, p.window).shape[0]
+    A = s2tilde_map(K, half_value(p))
+    gbar = np.concatenate([A.T @ gD[l * K:(l + 1) * K] for l in range(p.levels)])
+    g = descriptor_vjp(M, p, gbar)
+    ex = box_excess(M)
+    dex = np.where(M - 1.0 > 0, 1.0, 0.0) - np.where(-M > 0, 1.0, 0.0)
+    g = g + lam0 * phi * 2.0 * (ex / N) * dex / N
+    return out, g

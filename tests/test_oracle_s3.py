@@ -1,5 +1,6 @@
-"""Pins of the three-point oracle (CPU): the quadratic reduction of the ensemble (Eq. s3),
-checked against quantities that do not go through it."""
+"""Pins of the three-point oracle (the quadratic reduction of the ensemble, Eq. s3) and of
+the corrected two-point descriptor (App. A, Eq. s2rfroms2rbar), on the CPU, checked
+against quantities that do not go through them."""
 import itertools
 
 import numpy as np
@@ -104,5 +105,56 @@ def test_gradient_matches_central_differences(mode, shape, window, levels):
         Mm[i] -= h
         Lp = oracle.loss(Mp.reshape(shape), D_des, p, mode, D=oracle.s3_descriptor(Mp.reshape(shape), p))["L"]
         Lm = oracle.loss(Mm.reshape(shape), D_des, p, mode, D=oracle.s3_descriptor(Mm.reshape(shape), p))["L"]
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(g.ravel()[i] - fd) <= 1e-6 * max(1.0, abs(fd)), (i, g.ravel()[i], fd)
+
+
+# ----------------------------------------------------------------------------- corrected S2
+
+@pytest.mark.parametrize("kind", ["soft", "identity"])
+@pytest.mark.parametrize("seed", [8, 9])
+def test_corrected_descriptor_recovers_counted_two_point_probabilities(kind, seed):
+    # App. A: on binary fields S_tilde(r) equals the exact S2(r) counted directly, for the
+    # soft threshold and (the paper's footnote) for f(x) = x
+    shape = (14, 12)
+    M = (np.random.default_rng(seed).random(shape) < 0.45).astype(np.float64)
+    p = oracle.Params(ndim=2, window=(3, 4), threshold=kind)
+    Dt = oracle.descriptor_tilde(M, p)
+    H = oracle.half_window(2, p.window)
+    want = np.array([oracle.s2_count(M, r) for r in H])
+    assert np.max(np.abs(Dt - want)) < 1e-13
+
+
+def test_corrected_descriptor_multigrid_blocks_and_weights():
+    M = np.random.default_rng(10).random((16, 16))
+    p = oracle.Params(ndim=2, window=(2, 2), levels=2)
+    K = oracle.half_window(2, p.window).shape[0]
+    Dt = oracle.descriptor_tilde(M, p)
+    D = oracle.descriptor(M, p)
+    fh = oracle.half_value(p)
+    q = 2 * fh * fh
+    for l in range(2):
+        b, t = D[l * K:(l + 1) * K], Dt[l * K:(l + 1) * K]
+        assert abs(t[0] - b[0]) < 1e-15
+        np.testing.assert_allclose(t[1:], (b[1:] - q * b[0]) / (1 - q), rtol=1e-13)
+
+
+@pytest.mark.parametrize("mode", ["norm", "squared"])
+def test_corrected_gradient_matches_central_differences(mode):
+    rng = np.random.default_rng(11)
+    shape = (8, 8)
+    p = oracle.Params(ndim=2, window=(2, 3), levels=2)
+    T = (rng.random(shape) < 0.4).astype(np.float64)
+    D_des = oracle.descriptor_tilde(T, p)
+    M = rng.uniform(-0.2, 1.2, shape)
+    _, g = oracle.tilde_loss_grad(M, D_des, p, mode=mode)
+    h = 1e-5
+    flat = M.ravel()
+    for i in rng.choice(flat.size, 8, replace=False):
+        Mp, Mm = flat.copy(), flat.copy()
+        Mp[i] += h
+        Mm[i] -= h
+        Lp = oracle.loss(Mp.reshape(shape), D_des, p, mode, D=oracle.descriptor_tilde(Mp.reshape(shape), p))["L"]
+        Lm = oracle.loss(Mm.reshape(shape), D_des, p, mode, D=oracle.descriptor_tilde(Mm.reshape(shape), p))["L"]
         fd = (Lp - Lm) / (2 * h)
         assert abs(g.ravel()[i] - fd) <= 1e-6 * max(1.0, abs(fd)), (i, g.ravel()[i], fd)
