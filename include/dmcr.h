@@ -72,7 +72,10 @@ enum { DMCR_PROLONG_ADJOINT_ACCUMULATE = 0, DMCR_PROLONG_INJECT = 1 };
  * K_half x K_half matrix per level, row-major, whose diagonal is S_bar2 (the Gram matrix of
  * the ensemble, Sec. 3.4 footnote).  S3 is computed on the tensor cores (TF32 operands
  * split in three products, FP32 accumulation) and needs the DIRECT or AUTO path. */
-enum { DMCR_DESC_S2 = 0, DMCR_DESC_S3 = 1 };
+/* S2_TILDE: the corrected two-point descriptor of App. A (Eq. s2rfroms2rbar), per level
+ * S_tilde(0) = S_bar(0) and S_tilde(r) = (S_bar(r) - 2 f(1/2)^2 S_bar(0)) / (1 - 2 f(1/2)^2),
+ * K_half floats per level (equal to the exact S2 of binary fields); any path. */
+enum { DMCR_DESC_S2 = 0, DMCR_DESC_S3 = 1, DMCR_DESC_S2_TILDE = 2 };
 enum { DMCR_INIT_CALLER = 0, DMCR_INIT_UNIFORM_SEEDED = 1 };
 
 /* Problem statement (Sec. 3.3): field size, window P_a per axis, multigrid levels. */
@@ -89,7 +92,7 @@ typedef struct {
                                 adjoint ry rows per shift chunk (1..16), adjoint chunk target
                                 limit (1..64), adjoint rx blocks of 8 shifts per chunk at most
                                 (1..32).  Results agree to rounding across shapes. */
-    int descriptor;          /* DMCR_DESC_S2 (default) or DMCR_DESC_S3 */
+    int descriptor;          /* DMCR_DESC_S2 (default), DMCR_DESC_S3 or DMCR_DESC_S2_TILDE */
 } dmcr_params;
 
 /* Loss options (Sec. 3.1).  lambda = lambda0 * E (NORM) or lambda0 * E^2 (SQUARED). */

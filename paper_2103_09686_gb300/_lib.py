@@ -23,7 +23,7 @@ c_int, c_int64, c_float, c_void_p, c_uint64, c_size_t = (ctypes.c_int, ctypes.c_
 DMCR_OK, DMCR_EINVAL, DMCR_ENOMEM, DMCR_ECUDA, DMCR_ENONFINITE, DMCR_ETIMEOUT, DMCR_ENOTSUP = range(7)
 DMCR_SOFT, DMCR_IDENTITY = 0, 1
 DMCR_PATH_AUTO, DMCR_PATH_DIRECT, DMCR_PATH_FFT = 0, 1, 2
-DMCR_DESC_S2, DMCR_DESC_S3 = 0, 1
+DMCR_DESC_S2, DMCR_DESC_S3, DMCR_DESC_S2_TILDE = 0, 1, 2
 DMCR_LOSS_NORM, DMCR_LOSS_SQUARED = 0, 1
 DMCR_PROLONG_ADJOINT_ACCUMULATE, DMCR_PROLONG_INJECT = 0, 1
 DMCR_INIT_CALLER, DMCR_INIT_UNIFORM_SEEDED = 0, 1
@@ -153,7 +153,7 @@ class Params:
     level_weight_exp: float = -1.0
     path: int = DMCR_PATH_AUTO
     tune: tuple = (0, 0, 0, 0)     # launch shape; 0 = built-in choice (see tune.py)
-    descriptor: int = DMCR_DESC_S2  # DMCR_DESC_S3: the K x K three-point matrix per level
+    descriptor: int = DMCR_DESC_S2  # DMCR_DESC_S3: K x K three-point matrix; S2_TILDE: App. A corrected S2
 
     @property
     def ndim(self) -> int:

@@ -139,6 +139,8 @@ struct Plan {
     double fh2 = 0.0;          // f(1/2)^2 of the soft threshold (App. A mapping of the FFT path)
     // three-point descriptor: per level E, E^T, W^T (hi/lo where split) and G hi/lo
     int desc_kind = DMCR_DESC_S2;
+    float q_tilde = 0.f;       // corrected descriptor: 2 f(1/2)^2
+    size_t o_tsum = 0;         // corrected descriptor: per-level residual sums (floats)
     int64_t s3Kpad = 0, s3Npad[MAX_LEVELS] = {};
     size_t o_eh[MAX_LEVELS] = {}, o_el[MAX_LEVELS] = {}, o_eth[MAX_LEVELS] = {}, o_etl[MAX_LEVELS] = {},
            o_w[MAX_LEVELS] = {}, o_gh[MAX_LEVELS] = {}, o_gl[MAX_LEVELS] = {};
@@ -166,7 +168,9 @@ bool fft_cheaper(const LevelGeom& g) {
 
 // Upper bound of the segment-table bytes of one instance (every phase, 16-B aligned arrays).
 size_t table_bound(int levels) {
-    return (size_t)levels * (sizeof(FwdSeg) + sizeof(RedSeg) + sizeof(GSeg) + sizeof(AdjSeg) + sizeof(RestrictSeg)) +
+    return (size_t)levels *
+               (sizeof(FwdSeg) + sizeof(RedSeg) + sizeof(GSeg) + sizeof(AdjSeg) + sizeof(RestrictSeg) +
+                2 * sizeof(TildeSeg)) +
            sizeof(PenSeg) + sizeof(LossSeg) + sizeof(FinalSeg) + sizeof(InitSeg);
 }
 size_t table_slack() { return (size_t)(16 + MAX_LEVELS) * 16 + 256; }
@@ -262,7 +266,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         return fail(DMCR_EINVAL, "tune = {0|8|16|32, 0..16, 0..64, 0..32} expected");
     if (p->threshold == DMCR_SOFT && !(p->alpha > 0.f && isfinite(p->alpha)))
         return fail(DMCR_EINVAL, "alpha must be positive and finite");
-    if (p->descriptor != DMCR_DESC_S2 && p->descriptor != DMCR_DESC_S3)
+    if (p->descriptor != DMCR_DESC_S2 && p->descriptor != DMCR_DESC_S3 && p->descriptor != DMCR_DESC_S2_TILDE)
         return fail(DMCR_EINVAL, "unknown descriptor %d", p->descriptor);
     if (p->descriptor == DMCR_DESC_S3 && p->path == DMCR_PATH_FFT)
         return fail(DMCR_ENOTSUP, "the three-point descriptor has no FFT path");
@@ -318,7 +322,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             g.nChunks = 1;
             pl.any_fft = true;
         }
-        const bool direct2 = !g.fft && pl.desc_kind == DMCR_DESC_S2;
+        const bool direct2 = !g.fft && pl.desc_kind != DMCR_DESC_S3;
         if (direct2 && p->threshold == DMCR_IDENTITY && g.n[2] % T != 0)
             return fail(DMCR_ENOTSUP, "the direct identity path needs the last axis of every level divisible by 8");
         if (direct2 && (fwd_smem_bytes(g) > (size_t)MAX_DYN_SMEM || adj_smem_bytes(g) > (size_t)MAX_DYN_SMEM))
@@ -357,6 +361,8 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         const double fh = c1 / (1.0 + exp(0.25 * a)) - c1 * s0;
         pl.fh2 = fh * fh;
     }
+    // App. A: f(1/2) of the threshold (1/2 for f(x) = x)
+    pl.q_tilde = (float)(tc.identity ? 0.5 : 2.0 * pl.fh2);
     // workspace layout
     size_t o = 0;
     pl.tab_bytes = align_up(table_bound(pl.levels) + table_slack());
@@ -364,6 +370,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
     pl.o_scal = o; o = align_up(o + sizeof(Scalars));
     pl.o_pen = o; o = align_up(o + 3 * NPEN_BLOCKS * sizeof(double));
     pl.o_desc = o; o = align_up(o + (size_t)pl.Ktot * sizeof(float));
+    pl.o_tsum = o; o = align_up(o + (size_t)MAX_LEVELS * sizeof(float));
     for (int l = 0; l < pl.levels; ++l) {
         const LevelGeom& g = pl.g[l];
         if (l > 0) { pl.o_pyr[l] = o; o = align_up(o + (size_t)g.N * sizeof(float)); }
@@ -384,7 +391,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         } else {
             pl.o_fwd[l] = o; o = align_up(o + (size_t)g.fwdTiles * g.Khalf * sizeof(float));
         }
-        if (pl.desc_kind == DMCR_DESC_S2)
+        if (pl.desc_kind != DMCR_DESC_S3)
             pl.o_gd[l] = o, o = align_up(o + (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * GBLOCK * sizeof(float));
         pl.o_adj[l] = o; o = align_up(o + (size_t)g.nChunks * g.N * sizeof(float));
     }
@@ -474,7 +481,7 @@ struct Prepared {
     };
     std::vector<R> restricts;
     R fwd{0, 0, 0}, red{0, 0, 0}, pen{0, 0, 0}, loss{0, 0, 0}, gco{0, 0, 0}, adj{0, 0, 0}, fin{0, 0, 0},
-        init{0, 0, 0};
+        init{0, 0, 0}, tmap{0, 0, 0}, tsum{0, 0, 0};
     size_t smem_fwd = 0, smem_adj = 0;
     struct FftJob {
         LevelGeom g;
@@ -643,6 +650,23 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         }
         P.fwd = {push(P.tb, fv), (int)fv.size(), b};
         P.red = {push(P.tb, rv), (int)rv.size(), rb};
+        // corrected descriptor: map every level block once the whole block is written
+        std::vector<TildeSeg> tv;
+        int64_t tb = 0;
+        for (const Inst& x : in) {
+            if (x.pl->desc_kind != DMCR_DESC_S2_TILDE) continue;
+            for (int l = 0; l < x.pl->levels; ++l) {
+                TildeSeg t{};
+                t.desc = x.desc + x.pl->off[l];
+                t.K = x.pl->g[l].Khalf;
+                t.q = x.pl->q_tilde;
+                t.done = x.use_done ? &x.sc->done : nullptr;
+                t.blockStart = tb;
+                tb += ceil_div(t.K, ELEM_TH);
+                tv.push_back(t);
+            }
+        }
+        P.tmap = {push(P.tb, tv), (int)tv.size(), tb};
     }
     if (flags & F_LOSS) {
         std::vector<PenSeg> pv;
@@ -671,6 +695,7 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         };
         std::vector<Item> items;
         std::vector<GSeg> gv;
+        std::vector<TildeSeg> tsv;
         std::vector<FinalSeg> fv;
         int64_t gb = 0, fb = 0;
         const bool vjp = !(flags & F_LOSS);
@@ -702,6 +727,17 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
                 gs.scale = gcoef_scale(g, x.pl->tc, x.pl->w[l]);
                 gs.Gd = Gd;
                 gs.done = x.use_done ? &x.sc->done : nullptr;
+                if (x.pl->desc_kind == DMCR_DESC_S2_TILDE) {
+                    TildeSeg t{};
+                    t.src = gs.src;
+                    t.sub = gs.sub;
+                    t.tsum = reinterpret_cast<float*>(x.ws + x.pl->o_tsum) + l;
+                    t.K = g.Khalf;
+                    t.done = gs.done;
+                    tsv.push_back(t);
+                    gs.tsum = t.tsum;
+                    gs.q = x.pl->q_tilde;
+                }
                 gs.blockStart = gb;
                 gb += ceil_div((int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T, GCOEF_TH);
                 gv.push_back(gs);
@@ -756,6 +792,7 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
             av.push_back(it.a);
         }
         P.gco = {push(P.tb, gv), (int)gv.size(), gb};
+        P.tsum = {push(P.tb, tsv), (int)tsv.size(), (int64_t)tsv.size()};
         P.adj = {push(P.tb, av), (int)av.size(), ab};
         P.fin = {push(P.tb, fv), (int)fv.size(), fb};
     }
@@ -865,6 +902,10 @@ void run(const Prepared& P, cudaStream_t s) {
             ProfScope ps("s3_gram", -1, s);
             for (const S3Job& j : P.s3f) launch_s3_forward(j, P.tc, j.err, s);
         }
+        if (P.tmap.nseg > 0) {
+            ProfScope ps("tilde_map", -1, s);
+            launch_tilde_map(P.at<TildeSeg>(P.tmap.off), P.tmap.nseg, P.tmap.blocks, s);
+        }
     }
     if (P.flags & F_LOSS) {
         {
@@ -875,6 +916,10 @@ void run(const Prepared& P, cudaStream_t s) {
         launch_loss(P.at<LossSeg>(P.loss.off), P.loss.nseg, s);
     }
     if (P.flags & F_BACK) {
+        if (P.tsum.nseg > 0) {
+            ProfScope ps("tilde_sum", -1, s);
+            launch_tilde_sum(P.at<TildeSeg>(P.tsum.off), P.tsum.nseg, s);
+        }
         {
             ProfScope ps("gcoef", -1, s);
             launch_gcoef(P.at<GSeg>(P.gco.off), P.gco.nseg, P.gco.blocks, P.tc, s);

@@ -142,6 +142,40 @@ void launch_penalty(const PenSeg* segs, int nseg, cudaStream_t s) {
     stats_kernel<<<dim3(NPEN_BLOCKS, nseg), 256, 0, s>>>(segs);
 }
 
+// Corrected two-point descriptor, forward: map every block in place (entry 0 is read, never
+// written, so the map needs no second buffer).
+__global__ void tilde_map_kernel(const TildeSeg* __restrict__ segs, int nseg) {
+    const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
+    const TildeSeg& sg = segs[si];
+    if (sg.done != nullptr && *sg.done) return;
+    const int64_t k = ((int64_t)blockIdx.x - sg.blockStart) * ELEM_TH + threadIdx.x;
+    if (k < 1 || k >= sg.K) return;
+    sg.desc[k] = (sg.desc[k] - sg.q * sg.desc[0]) / (1.f - sg.q);
+}
+
+void launch_tilde_map(const TildeSeg* segs, int nseg, int64_t blocks, cudaStream_t s) {
+    if (blocks <= 0) return;
+    tilde_map_kernel<<<(unsigned)blocks, ELEM_TH, 0, s>>>(segs, nseg);
+}
+
+// Corrected two-point descriptor, backward: one block per segment, sum_{k >= 1} (src - sub)
+// in FP64 in a fixed order.
+__global__ void tilde_sum_kernel(const TildeSeg* __restrict__ segs) {
+    const TildeSeg& sg = segs[blockIdx.x];
+    if (sg.done != nullptr && *sg.done) return;
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int64_t k = 1 + threadIdx.x; k < sg.K; k += blockDim.x)
+        acc += (double)sg.src[k] - (sg.sub != nullptr ? (double)sg.sub[k] : 0.0);
+    acc = block_sum_d(acc, sh);
+    if (threadIdx.x == 0) *sg.tsum = (float)acc;
+}
+
+void launch_tilde_sum(const TildeSeg* segs, int nseg, cudaStream_t s) {
+    if (nseg <= 0) return;
+    tilde_sum_kernel<<<nseg, 256, 0, s>>>(segs);
+}
+
 // One block per instance: sums the stats partials in a fixed tree, then E, E^2, E_bc,
 // lambda, L, rel_err and the gradient scalars; in a reconstruction also the stopping test
 // and the Adam step bookkeeping.

@@ -133,6 +133,21 @@ struct GSeg {
     float scale;
     float* Gd;
     const int* done;
+    const float* tsum;      // corrected descriptor: sum_{k >= 1} (src - sub) of the block, else null
+    float q;                // corrected descriptor: 2 f(1/2)^2
+    int64_t blockStart;
+};
+// Corrected two-point descriptor (App. A, Eq. s2rfroms2rbar), one (instance, level) block:
+// forward, the block is mapped in place, S_tilde(k) = (S_bar(k) - q S_bar(0)) / (1 - q) for
+// k >= 1; backward, tsum = sum_{k >= 1} (src - sub) feeds the transposed map in gcoef.
+struct TildeSeg {
+    float* desc;
+    const float* src;
+    const float* sub;
+    float* tsum;
+    int64_t K;
+    float q;
+    const int* done;
     int64_t blockStart;
 };
 struct RestrictSeg {
@@ -220,6 +235,8 @@ void launch_fwd_reduce(const RedSeg* segs, int nseg, int64_t blocks, cudaStream_
 void launch_penalty(const PenSeg* segs, int nseg, cudaStream_t s);
 void launch_loss(const LossSeg* segs, int nseg, cudaStream_t s);
 void launch_gcoef(const GSeg* segs, int nseg, int64_t blocks, const ThreshConst& tc, cudaStream_t s);
+void launch_tilde_map(const TildeSeg* segs, int nseg, int64_t blocks, cudaStream_t s);
+void launch_tilde_sum(const TildeSeg* segs, int nseg, cudaStream_t s);
 void launch_corr_adj(const AdjSeg* segs, int nseg, int64_t blocks, size_t smem, const ThreshConst& tc,
                      cudaStream_t s);
 void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, cudaStream_t s);

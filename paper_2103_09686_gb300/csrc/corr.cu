@@ -693,7 +693,9 @@ __global__ void gcoef_kernel(const GSeg* __restrict__ segs, int nseg, ThreshCons
     if (rx <= g.P[2]) {
         int64_t k = canon_index(g, rz, ry, rx);
         if (k < 0) k = canon_index(g, -rz, -ry, -rx);
-        const float d = sg.src[k] - (sg.sub != nullptr ? sg.sub[k] : 0.f);
+        float d = sg.src[k] - (sg.sub != nullptr ? sg.sub[k] : 0.f);
+        // corrected descriptor: dL/dS_bar = A^T dL/dS_tilde (App. A map, transposed)
+        if (sg.tsum != nullptr) d = k == 0 ? d - sg.q / (1.f - sg.q) * *sg.tsum : d / (1.f - sg.q);
         float sc = sg.scale * (sg.sc != nullptr ? sg.sc->gscale : 1.f);
         if (rz == 0 && ry == 0 && rx == 0) sc *= 2.f;
         v = sc * d;
