@@ -232,6 +232,17 @@ def main_checkerboard(args):
     dm.load()
     n, P, a = 64, 31, 8
     runs = []
+    # one-time start-up (module loading, tensor-map encoding, graph capture, the norm and
+    # rounding ops) outside every timed run: 100 untimed iterations of each descriptor
+    for kind in (dm.DMCR_DESC_S3, dm.DMCR_DESC_S2):
+        p = dm.Params(shape=(n, n), window=(P, P), descriptor=kind)
+        ws = dm.workspace(p)
+        D = dm.descriptor(torch.tensor(synthetic.checkerboard(n, a), dtype=torch.float32, device="cuda"), p, ws)
+        f = torch.empty(n, n, device="cuda")
+        dm.dmcr_reconstruct(p, dm.ReconOpts(max_iters=100, lr=1e-2, seed=1, init=dm.DMCR_INIT_UNIFORM_SEEDED),
+                            D, f, torch.zeros_like(f), torch.zeros_like(f), ws=ws)
+        float(torch.linalg.norm(dm.descriptor((f >= 0.5).float(), p, ws) - D) / torch.linalg.norm(D))
+    torch.cuda.synchronize()
     specs = [("S3", dm.DMCR_SOFT, 1e-3, 6000), ("S3", dm.DMCR_SOFT, 1e-2, 6000),
              ("S3", dm.DMCR_IDENTITY, 1e-3, 6000), ("S3", dm.DMCR_IDENTITY, 1e-2, 6000),
              ("S2", dm.DMCR_SOFT, 1e-3, 6000), ("S2", dm.DMCR_SOFT, 1e-2, 6000)]

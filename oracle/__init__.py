@@ -38,6 +38,11 @@ What each function follows (sections and equations of the paper):
 * ``s2_count`` / ``s3_count`` / ``s3_from_s3bar`` -- exact two- and three-point
   probabilities of a binary field by counting (Sec. 3.2.1) and App. A's mapping from
   S_bar3 back to S3 (Eq. s3rfroms3rbar).
+* ``cross_sbar`` / ``multiphase_descriptor`` / ``multiphase_loss_grad`` -- the two-point
+  chain of Sec. 3.2.2-3.2.4 with the pair's tail and tip in two different phase fields:
+  the cross-correlations S2^{a->b} of the multi-phase outlook (Sec. 5), every ordered
+  phase pair on the half window of every level, and the exact gradient with respect to
+  every phase field.  ``cross_count`` counts S2^{a->b} of binary indicators (Sec. 3.2.1).
 """
 from __future__ import annotations
 
@@ -561,3 +566,116 @@ def tilde_loss_grad(M, D_des, p: Params, mode: str = "norm", lambda0: float | No
     dex = np.where(M - 1.0 > 0, 1.0, 0.0) - np.where(-M > 0, 1.0, 0.0)
     g = g + lam0 * phi * 2.0 * (ex / N) * dex / N
     return out, g
+
+
+# ----------------------------------------------------------------------------- multi-phase
+
+def cross_sbar(Ma, Mb, shifts, kind: str = "soft", alpha: float = 10.0) -> np.ndarray:
+    """Two-point reduction with the pair's tail in one phase field and its tip in another:
+    S_bar^{a->b}(r) = (1/N) sum_x f((Ma_x + Mb_{x+r}) / 2)^2, the convolve -> threshold ->
+    reduce chain of Sec. 3.2.2-3.2.4 applied to the cross-correlation S2^{a->b} that the
+    outlook (Sec. 5) names for microstructures of more than two phases.  Ma = Mb gives
+    S_bar2."""
+    Ma = np.asarray(Ma, dtype=np.float64)
+    Mb = np.asarray(Mb, dtype=np.float64)
+    axes = tuple(range(Ma.ndim))
+    out = np.empty(len(shifts))
+    for k, r in enumerate(shifts):
+        tip = np.roll(Mb, shift=tuple(-int(c) for c in r), axis=axes)   # tip[x] = Mb[x + r]
+        e = threshold(0.5 * (Ma + tip), kind, alpha)[0]
+        out[k] = float(np.mean(e * e))
+    return out
+
+
+def multiphase_descriptor(F, p: Params, levels_out: bool = False):
+    """Eq. mg for a stack F of phase fields (n_phase, *shape): per level l (pyramid of every
+    field) and per ordered phase pair (a, b) in row-major order, w_l S_bar_l^{a->b}(r) on the
+    half window.  The pairs (a, b) and (b, a) together give S^{a->b} on the full window
+    (S^{a->b}(-r) = S^{b->a}(r)); both hold the r = 0 value."""
+    F = np.asarray(F, dtype=np.float64)
+    nph = F.shape[0]
+    H = half_window(p.ndim, p.window)
+    pyrs = [pyramid(F[a], p.levels) for a in range(nph)]
+    w = p.weights()
+    blocks = [w[l] * cross_sbar(pyrs[a][l], pyrs[b][l], H, p.threshold, p.alpha)
+              for l in range(p.levels) for a in range(nph) for b in range(nph)]
+    D = np.concatenate(blocks)
+    return (D, blocks) if levels_out else D
+
+
+def multiphase_level_vjp(Ml, p: Params, G) -> np.ndarray:
+    """Chain rule of one level, term by term: G[a, b, k] weighs S_bar^{a->b}(r_k), whose
+    summand f(u)^2, u = (Ma_x + Mb_{x+r}) / 2, has the derivative f(u) f'(u) / N with
+    respect to Ma_x and to Mb_{x+r}.  Ml: the level's fields (n_phase, *shape)."""
+    Ml = np.asarray(Ml, dtype=np.float64)
+    nph = Ml.shape[0]
+    H = half_window(p.ndim, p.window)
+    axes = tuple(range(Ml.ndim - 1))
+    N = Ml[0].size
+    g = np.zeros_like(Ml)
+    for a in range(nph):
+        for b in range(nph):
+            for k, r in enumerate(H):
+                tip = np.roll(Ml[b], shift=tuple(-int(c) for c in r), axis=axes)
+                f, df = threshold(0.5 * (Ml[a] + tip), p.threshold, p.alpha)
+                t = G[a, b, k] * (f * df).reshape(Ml[a].shape) / N
+                g[a] += t                                                      # d/dMa_x
+                g[b] += np.roll(t, shift=tuple(int(c) for c in r), axis=axes)  # d/dMb_{x+r}
+    return g
+
+
+def multiphase_descriptor_vjp(F, p: Params, grad_D) -> np.ndarray:
+    """Gradient of <grad_D, D(F)> with respect to every finest phase field: per-level VJP,
+    then the transpose of each field's pooling chain (Sec. 3.3)."""
+    F = np.asarray(F, dtype=np.float64)
+    nph = F.shape[0]
+    K = half_window(p.ndim, p.window).shape[0]
+    pyrs = [pyramid(F[a], p.levels) for a in range(nph)]
+    w = p.weights()
+    g = None
+    for l in reversed(range(p.levels)):
+        blk = np.asarray(grad_D[l * nph * nph * K:(l + 1) * nph * nph * K], dtype=np.float64)
+        Ml = np.stack([pyrs[a][l] for a in range(nph)])
+        gl = multiphase_level_vjp(Ml, p, w[l] * blk.reshape(nph, nph, K))
+        g = gl if g is None else gl + np.stack([prolongate_adjoint(g[a]) for a in range(nph)])
+    return g
+
+
+def multiphase_loss_grad(F, D_des, p: Params, mode: str = "norm", lambda0: float | None = None,
+                         bc: bool = True):
+    """Eq. L_func_dMCR on the multi-phase descriptor and its gradient.  E_bc sums the box
+    excess of every phase field, each normalised by the finest pixel count N of one field;
+    lambda0 defaults to N."""
+    F = np.asarray(F, dtype=np.float64)
+    N = F[0].size
+    if lambda0 is None:
+        lambda0 = float(N)
+    if not bc:
+        lambda0 = 0.0
+    D = multiphase_descriptor(F, p)
+    rho = D - np.asarray(D_des, dtype=np.float64)
+    E2 = float(np.sum(rho * rho))
+    E = float(np.sqrt(E2))
+    Ebc = float(np.sum((box_excess(F) / N) ** 2))
+    phi = E if mode == "norm" else E2
+    lam = lambda0 * phi
+    ref = float(np.sqrt(np.sum(np.asarray(D_des, dtype=np.float64) ** 2)))
+    out = {"E": E, "E2": E2, "Ebc": Ebc, "lambda": lam, "L": phi + lam * Ebc,
+           "rel_err": E / ref if ref > 0 else float("inf"), "rho": rho, "lambda0": lambda0}
+    dphi_dD = (rho / E if E > 0 else np.zeros_like(rho)) if mode == "norm" else 2.0 * rho
+    g = multiphase_descriptor_vjp(F, p, dphi_dD * (1.0 + lambda0 * Ebc))
+    dex = np.where(F - 1.0 > 0, 1.0, 0.0) - np.where(-F > 0, 1.0, 0.0)
+    g = g + lambda0 * phi * 2.0 * (box_excess(F) / N) * dex / N
+    return out, g
+
+
+def cross_count(A, B, r) -> float:
+    """Binary phase indicators: the probability that x lies in phase a and x + r in phase b,
+    counted position by position."""
+    A = np.asarray(A)
+    B = np.asarray(B)
+    hits = 0
+    for x in np.ndindex(A.shape):
+        y = tuple((x[i] + int(r[i])) % A.shape[i] for i in range(A.ndim))
+        hits += int(A[x] == 1 and B[y] == 1)
+    return hits / A.size

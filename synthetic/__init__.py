@@ -138,3 +138,21 @@ def batch_instances(count: int = 256, seed: int = 4000, sizes=(64, 128, 256, 512
         tgt = target_2d_grf(n, max(n / 32.0, 2.0), vf, seed + 1 + i)
         out.append((tgt, P, seed + 1 + i))
     return out
+
+
+def multiphase_grf(shape, corr_len, fractions, seed: int) -> np.ndarray:
+    """Phase indicator stack (n_phase, *shape) of a periodic GRF cut at exact quantiles:
+    the highest fractions[0] of the values are phase 0, the next fractions[1] phase 1, ...,
+    the rest the last phase (n_phase = len(fractions) + 1).  Every position lies in exactly
+    one phase."""
+    g = gaussian_random_field(shape, corr_len, seed).ravel()
+    order = np.argsort(-g, kind="stable")
+    labels = np.full(g.size, len(fractions), dtype=np.int64)
+    start = 0
+    for a, fr in enumerate(fractions):
+        k = int(round(fr * g.size))
+        labels[order[start:start + k]] = a
+        start += k
+    out = np.zeros((len(fractions) + 1, g.size))
+    out[labels, np.arange(g.size)] = 1.0
+    return out.reshape((len(fractions) + 1,) + tuple(int(s) for s in shape))
