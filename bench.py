@@ -56,6 +56,9 @@ WORKLOADS = {
                       desc="3D 128^3 GRF(l=6/6/12, vf=0.25), window +-24, 2 levels (128,64), one Adam iteration"),
     "grf64": dict(shape=(64, 64), window=(16, 16), levels=1,
                   desc="2D 64x64 GRF(l=4, vf=0.30), window +-16, 1 level, one Adam iteration"),
+    "mp3_512": dict(shape=(512, 512), window=(64, 64), levels=3, phases=3,
+                    desc="2D three-phase 512x512 GRF(l=12, phase fractions 0.3/0.3/0.4), window +-64, 3 levels "
+                         "(512,256,128), cross-correlations of all 9 ordered phase pairs; one Adam iteration per step"),
     "batch256": dict(shape=None, window=None, levels=1, count=256,
                      desc="256 independent 2D instances, sizes uniform over {64,128,256,512}^2, GRF vf U[0.1,0.5], "
                           "windows U{16..64} capped at n/2, 1 level; one fused batched Adam iteration per step"),
@@ -362,6 +365,8 @@ def make_instances(name: str, rank: int):
 
 
 def make_target(name: str, seed_base: int) -> np.ndarray:
+    if name == "mp3_512":
+        return synthetic.multiphase_grf((512, 512), 12.0, (0.3, 0.3), 2000 + seed_base)
     if name == "grf512":
         return synthetic.target_large_2d(2000 + seed_base)
     if name == "grf128_3d":
@@ -468,6 +473,40 @@ def oracle_sample(shape, window, levels, target, field, budget_s: float, seed: i
         "full step extrapolated over %d levels" % (s, K, "x".join(map(str, shape)), q, N1, levels)
 
 
+def oracle_sample_mp(shape, window, levels, nph, field, budget_s: float, seed: int = 0):
+    """Multi-phase form of ``oracle_sample``: forward on s half-window shifts of one phase
+    pair of the finest level, the gradient of every phase at q finest positions (level 0),
+    extrapolated to all nph^2 pairs and all levels."""
+    import oracle
+    op1 = oracle.Params(ndim=len(shape), window=tuple(window), levels=1)
+    H = oracle.half_window(len(shape), window)
+    K = H.shape[0]
+    rng = np.random.default_rng(seed)
+    F = np.asarray(field, dtype=np.float32).astype(np.float64)
+    G = rng.standard_normal(nph * nph * K)
+    N1 = F[0].size
+
+    def run(s, q):
+        idx = rng.choice(K, size=min(s, K), replace=False)
+        t0 = time.perf_counter()
+        oracle.cross_sbar(F[0], F[1], H[idx])
+        t1 = time.perf_counter()
+        oracle.multiphase_vjp_at(F, op1, G, rng.choice(N1, size=q, replace=False))
+        t2 = time.perf_counter()
+        return (t1 - t0) / len(idx), (t2 - t1) / q
+
+    tf, ta = run(4, 2)           # calibrate
+    s = max(4, int(0.5 * budget_s / max(tf, 1e-9)))
+    q = max(2, min(N1, int(0.5 * budget_s / max(ta, 1e-9))))
+    tf, ta = run(s, q)
+    sizes = level_sizes(shape, levels)
+    t_full = sum(nph * nph * K * tf * (n / N1) + n * ta for n in sizes)
+    units = nph * nph * units_per_step(shape, window, levels)
+    return units / t_full, "%d forward shifts (of %d) of one phase pair on the %s level and the gradient of all %d " \
+        "phases at %d positions (of %d); full step extrapolated over %d phase pairs and %d levels" % (
+            s, K, "x".join(map(str, shape)), nph, q, N1, nph * nph, levels)
+
+
 def cores_used() -> int:
     try:
         return int(os.environ.get("OMP_NUM_THREADS", "")) or os.cpu_count()
@@ -520,20 +559,24 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     wl = WORKLOADS[args.workload]
+    nph = wl.get("phases", 1)
     insts = make_instances(args.workload, rank)
-    units = sum(units_per_step(sh, w, lev) for sh, w, lev, _ in insts)
+    units = nph * nph * sum(units_per_step(sh, w, lev) for sh, w, lev, _ in insts)
     big = max(insts, key=lambda x: int(np.prod(x[0])) * int(np.prod([2 * q + 1 for q in x[1]])))
 
     if args.impl == "reference":
         if rank != 0:
             return 0
         shape, window, levels, target = big
-        field = synthetic.uniform_field(shape, seed=1)
+        field = synthetic.uniform_field(shape if nph == 1 else (nph,) + tuple(shape), seed=1)
         per_step = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
         vals = []
         sample = ""
         for i in range(args.warmup + args.steps):
-            v, sample = oracle_sample(shape, window, levels, target, field, per_step, seed=i)
+            if nph > 1:
+                v, sample = oracle_sample_mp(shape, window, levels, nph, field, per_step, seed=i)
+            else:
+                v, sample = oracle_sample(shape, window, levels, target, field, per_step, seed=i)
             if i >= args.warmup:
                 vals.append(v)
         value = float(np.mean(vals))
@@ -558,7 +601,7 @@ def main():
     dev = torch.device("cuda", local)
 
     # inputs: this rank's own instances (weak scaling, no data-path collective)
-    params = [dm.Params(shape=sh, window=w, levels=lev) for sh, w, lev, _ in insts]
+    params = [dm.Params(shape=sh, window=w, levels=lev, phases=nph) for sh, w, lev, _ in insts]
     if args.tune:
         from paper_2103_09686_gb300 import tune
         params = [tune.tuned(p) for p in params]
@@ -572,7 +615,8 @@ def main():
         dm.dmcr_descriptor_batched(params, targets, d_des, ws)
     else:
         dm.dmcr_descriptor(params[0], targets[0], d_des[0], ws)
-    fields0 = [torch.tensor(synthetic.uniform_field(sh, seed=7 + rank + 7919 * i), dtype=torch.float32, device=dev)
+    fields0 = [torch.tensor(synthetic.uniform_field(sh if nph == 1 else (nph,) + tuple(sh), seed=7 + rank + 7919 * i),
+                            dtype=torch.float32, device=dev)
                for i, (sh, _, _, _) in enumerate(insts)]
     fields = [f.clone() for f in fields0]
     ms = [torch.zeros_like(f) for f in fields]
@@ -661,7 +705,7 @@ def main():
     pairs_adj = pairs_fwd = 0
     for sh, w, lev, _ in insts:
         kfull = int(np.prod([2 * q + 1 for q in w]))
-        nsum = sum(level_sizes(sh, lev))
+        nsum = nph * nph * sum(level_sizes(sh, lev))
         pairs_adj += nsum * kfull
         pairs_fwd += nsum * ((kfull + 1) // 2)
     pairs = pairs_adj if name.startswith("corr_adj") else (pairs_fwd if name.startswith("corr_fwd") else None)
@@ -691,8 +735,12 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         shape, window, levels, target = big
-        v_cpu, sample = oracle_sample(shape, window, levels, target, synthetic.uniform_field(shape, seed=7),
-                                      args.cpu_budget)
+        if nph > 1:
+            v_cpu, sample = oracle_sample_mp(shape, window, levels, nph,
+                                             synthetic.uniform_field((nph,) + tuple(shape), seed=7), args.cpu_budget)
+        else:
+            v_cpu, sample = oracle_sample(shape, window, levels, target, synthetic.uniform_field(shape, seed=7),
+                                          args.cpu_budget)
         cpu = {"value": v_cpu, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": sample}
 
     if rank == 0:

@@ -93,7 +93,21 @@ typedef struct {
                                 limit (1..64), adjoint rx blocks of 8 shifts per chunk at most
                                 (1..32).  Results agree to rounding across shapes. */
     int descriptor;          /* DMCR_DESC_S2 (default), DMCR_DESC_S3 or DMCR_DESC_S2_TILDE */
+    int phases;              /* phase fields (1..8; 0 means 1).  See "Several phases" below. */
 } dmcr_params;
+
+/* Several phases (the multi-phase outlook of Sec. 5; the paper defines the descriptor for
+ * one field).  With phases = P > 1 every field argument is a stack of P phase fields, each
+ * of the size n above, phase-major and contiguous (P x N floats; gradients, Adam moments
+ * and the uniform start field likewise), and the descriptor holds, per level and per
+ * ordered phase pair (a, b) in row-major order, the cross-correlation
+ *     S_bar^{a->b}(r) = (1/N) sum_x f((M^a_x + M^b_{x+r}) / 2)^2
+ * on the half window (K_half floats): P^2 K_half floats per level.  The block (b, a) holds
+ * S_bar^{a->b}(-r), so both blocks together give the full window; (a, a) is S_bar2 of
+ * phase a.  The box penalty E_bc sums the excess of every phase field, each divided by
+ * the finest position count N of one field, and lambda0 < 0 selects that N.  Requires
+ * descriptor = DMCR_DESC_S2 and the direct path (AUTO never picks the FFT; FFT gives
+ * DMCR_ENOTSUP).  Cost: P^2 times one field's. */
 
 /* Loss options (Sec. 3.1).  lambda = lambda0 * E (NORM) or lambda0 * E^2 (SQUARED). */
 typedef struct {
@@ -137,7 +151,8 @@ int dmcr_version(void);
 /* Reason for the last failing call on this host thread ("" if none). */
 const char* dmcr_last_error(void);
 
-/* Descriptor length sum_l K_half (all levels).  Returns DMCR_EINVAL on bad params. */
+/* Descriptor length: sum_l K_half (S2, S2_TILDE), sum_l K_half^2 (S3), times phases^2.
+ * Returns DMCR_EINVAL on bad params. */
 dmcr_status dmcr_descriptor_length(const dmcr_params* p, int64_t* length);
 
 /* Bytes of scratch memory (`ws`) the calls below need for these params. */

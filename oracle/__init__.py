@@ -679,3 +679,39 @@ def cross_count(A, B, r) -> float:
         y = tuple((x[i] + int(r[i])) % A.shape[i] for i in range(A.ndim))
         hits += int(A[x] == 1 and B[y] == 1)
     return hits / A.size
+
+
+def multiphase_vjp_at(F, p: Params, grad_D, positions) -> np.ndarray:
+    """``multiphase_descriptor_vjp`` at sampled finest positions (flat indices), written in
+    gather form: at level l the position's ancestor y (coordinates >> l) collects, for every
+    phase b and shift r_k, G[a, b, k] h((Ma_y + Mb_{y+r}) / 2) + G[b, a, k] h((Mb_{y-r} + Ma_y) / 2)
+    over N_l, h = f f'; the pooling transpose scales level l by 2^{-d l}.  Returns
+    (n_phase, len(positions))."""
+    F = np.asarray(F, dtype=np.float64)
+    nph = F.shape[0]
+    shape = F.shape[1:]
+    d = len(shape)
+    H = half_window(p.ndim, p.window)
+    K = H.shape[0]
+    pyrs = [pyramid(F[a], p.levels) for a in range(nph)]
+    w = p.weights()
+    coords = np.stack(np.unravel_index(np.asarray(positions, dtype=np.int64), shape), axis=1)
+    out = np.zeros((nph, coords.shape[0]))
+    for l in range(p.levels):
+        G = w[l] * np.asarray(grad_D[l * nph * nph * K:(l + 1) * nph * nph * K], dtype=np.float64)
+        G = G.reshape(nph, nph, K)
+        n = np.array(pyrs[0][l].shape)
+        Nl = int(np.prod(n))
+        for i, c in enumerate(coords):
+            y = c >> l
+            fwd = tuple(((y + H) % n).T)          # y + r_k
+            bwd = tuple(((y - H) % n).T)          # y - r_k
+            for a in range(nph):
+                ma = pyrs[a][l][tuple(y)]
+                acc = 0.0
+                for b in range(nph):
+                    f1, d1 = threshold(0.5 * (ma + pyrs[b][l][fwd]), p.threshold, p.alpha)
+                    f2, d2 = threshold(0.5 * (pyrs[b][l][bwd] + ma), p.threshold, p.alpha)
+                    acc += float(np.dot(G[a, b], f1 * d1) + np.dot(G[b, a], f2 * d2))
+                out[a, i] += acc / Nl / float(2 ** (d * l))
+    return out

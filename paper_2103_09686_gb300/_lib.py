@@ -33,7 +33,7 @@ OUT_NAMES = ("E", "E2", "Ebc", "lambda", "L", "rel_err")
 class dmcr_params(ctypes.Structure):
     _fields_ = [("ndim", c_int), ("n", c_int64 * 3), ("window", c_int * 3), ("levels", c_int),
                 ("threshold", c_int), ("alpha", c_float), ("level_weight_exp", c_float), ("path", c_int),
-                ("tune", c_int * 4), ("descriptor", c_int)]
+                ("tune", c_int * 4), ("descriptor", c_int), ("phases", c_int)]
 
 
 class dmcr_loss_opts(ctypes.Structure):
@@ -154,6 +154,7 @@ class Params:
     path: int = DMCR_PATH_AUTO
     tune: tuple = (0, 0, 0, 0)     # launch shape; 0 = built-in choice (see tune.py)
     descriptor: int = DMCR_DESC_S2  # DMCR_DESC_S3: K x K three-point matrix; S2_TILDE: App. A corrected S2
+    phases: int = 1                 # > 1: fields are (phases, *shape) stacks; cross-correlations of every pair
 
     @property
     def ndim(self) -> int:
@@ -174,6 +175,7 @@ class Params:
         for i, t in enumerate(tuple(self.tune)[:4]):
             p.tune[i] = int(t)
         p.descriptor = int(self.descriptor)
+        p.phases = int(self.phases)
         return p
 
 

@@ -124,11 +124,12 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 struct Plan {
     int ndim = 2;
     int levels = 1;
+    int phases = 1;            // phase fields, stacked phase-major (every level of the pyramid too)
     LevelGeom g[MAX_LEVELS];
     float w[MAX_LEVELS];
     int64_t off[MAX_LEVELS];   // descriptor offset of each level block
     int64_t Ktot = 0;
-    int64_t N1 = 0;
+    int64_t N1 = 0;            // finest position count of one phase field
     ThreshConst tc;
     // workspace offsets (bytes)
     size_t o_tab = 0, tab_bytes = 0, o_scal = 0, o_pen = 0, o_desc = 0, o_pyr[MAX_LEVELS] = {},
@@ -167,15 +168,19 @@ bool fft_cheaper(const LevelGeom& g) {
 }
 
 // Upper bound of the segment-table bytes of one instance (every phase, 16-B aligned arrays).
-size_t table_bound(int levels) {
+size_t table_bound(int levels, int phases) {
+    const size_t pp = (size_t)phases * phases;
     return (size_t)levels *
-               (sizeof(FwdSeg) + sizeof(RedSeg) + sizeof(GSeg) + sizeof(AdjSeg) + sizeof(RestrictSeg) +
-                2 * sizeof(TildeSeg)) +
-           sizeof(PenSeg) + sizeof(LossSeg) + sizeof(FinalSeg) + sizeof(InitSeg);
+               (pp * (sizeof(FwdSeg) + sizeof(RedSeg) + sizeof(GSeg) + sizeof(AdjSeg)) +
+                phases * sizeof(RestrictSeg) + 2 * sizeof(TildeSeg)) +
+           sizeof(PenSeg) + sizeof(LossSeg) + phases * sizeof(FinalSeg) + sizeof(InitSeg);
 }
 size_t table_slack() { return (size_t)(16 + MAX_LEVELS) * 16 + 256; }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// coefficient grid of one level and phase pair (gcoef's output)
+int64_t gd_floats(const LevelGeom& g) { return (int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * GBLOCK; }
 
 // Forward tile rows for the whole problem (all levels share one fused launch): the tallest
 // tile (fewest halo rows per output row) that still gives ~8 blocks per SM summed over levels.
@@ -270,6 +275,13 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         return fail(DMCR_EINVAL, "unknown descriptor %d", p->descriptor);
     if (p->descriptor == DMCR_DESC_S3 && p->path == DMCR_PATH_FFT)
         return fail(DMCR_ENOTSUP, "the three-point descriptor has no FFT path");
+    const int phases = p->phases == 0 ? 1 : p->phases;
+    if (phases < 1 || phases > MAX_PHASES) return fail(DMCR_EINVAL, "phases must be in [1, %d]", MAX_PHASES);
+    if (phases > 1 && p->descriptor != DMCR_DESC_S2)
+        return fail(DMCR_ENOTSUP, "several phase fields: the two-point descriptor only");
+    if (phases > 1 && p->path == DMCR_PATH_FFT)
+        return fail(DMCR_ENOTSUP, "several phase fields: the direct path only");
+    pl.phases = phases;
 
     pl.desc_kind = p->descriptor;
     pl.ndim = p->ndim;
@@ -289,7 +301,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         if (n[a] % (1LL << (p->levels - 1)) != 0)
             return fail(DMCR_EINVAL, "size %lld not divisible by 2^(levels-1)", (long long)n[a]);
     }
-    if (n[0] * n[1] * n[2] > (1LL << 34)) return fail(DMCR_EINVAL, "field too large");
+    if (n[0] * n[1] * n[2] * (p->phases > 1 ? p->phases : 1) > (1LL << 34)) return fail(DMCR_EINVAL, "field too large");
     const double we = p->level_weight_exp < 0.f ? p->ndim / 2.0 : (double)p->level_weight_exp;
     int tune[4] = {p->tune[0], p->tune[1], p->tune[2], p->tune[3]};
     if (tune[0] == 0) tune[0] = forward_rows(n, P, p->levels, p->ndim);
@@ -311,7 +323,8 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             if (!fft_sizes)
                 return fail(DMCR_ENOTSUP, "FFT path: level %d sizes must factor into 2, 3, 5 and be <= 4096", l + 1);
             g.fft = 1;
-        } else if (p->path == DMCR_PATH_AUTO && p->threshold == DMCR_IDENTITY && fft_sizes && fft_cheaper(g)) {
+        } else if (p->path == DMCR_PATH_AUTO && p->threshold == DMCR_IDENTITY && phases == 1 && fft_sizes &&
+                   fft_cheaper(g)) {
             g.fft = 1;
         }
         if (pl.desc_kind == DMCR_DESC_S3) {
@@ -329,7 +342,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             return fail(DMCR_ENOTSUP, "window too large for the shared-memory tiles of this build");
         pl.w[l] = (float)pow(2.0, we * l);
         pl.off[l] = off;
-        off += pl.desc_kind == DMCR_DESC_S3 ? g.Khalf * g.Khalf : g.Khalf;
+        off += pl.desc_kind == DMCR_DESC_S3 ? g.Khalf * g.Khalf : (int64_t)phases * phases * g.Khalf;
     }
     pl.Ktot = off;
     pl.N1 = pl.g[0].N;
@@ -365,7 +378,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
     pl.q_tilde = (float)(tc.identity ? 0.5 : 2.0 * pl.fh2);
     // workspace layout
     size_t o = 0;
-    pl.tab_bytes = align_up(table_bound(pl.levels) + table_slack());
+    pl.tab_bytes = align_up(table_bound(pl.levels, pl.phases) + table_slack());
     pl.o_tab = o; o += pl.tab_bytes;
     pl.o_scal = o; o = align_up(o + sizeof(Scalars));
     pl.o_pen = o; o = align_up(o + 3 * NPEN_BLOCKS * sizeof(double));
@@ -373,7 +386,8 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
     pl.o_tsum = o; o = align_up(o + (size_t)MAX_LEVELS * sizeof(float));
     for (int l = 0; l < pl.levels; ++l) {
         const LevelGeom& g = pl.g[l];
-        if (l > 0) { pl.o_pyr[l] = o; o = align_up(o + (size_t)g.N * sizeof(float)); }
+        const size_t ph = (size_t)pl.phases;
+        if (l > 0) { pl.o_pyr[l] = o; o = align_up(o + ph * g.N * sizeof(float)); }
         if (g.fft) {
             pl.o_fx[l] = o; o = align_up(o + (size_t)g.N * 16);
             pl.o_fh[l] = o; o = align_up(o + (size_t)g.N * 16);
@@ -389,11 +403,11 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             pl.o_gh[l] = o; o = align_up(o + Kp * Kp * sizeof(float));
             pl.o_gl[l] = o; o = align_up(o + Kp * Kp * sizeof(float));
         } else {
-            pl.o_fwd[l] = o; o = align_up(o + (size_t)g.fwdTiles * g.Khalf * sizeof(float));
+            pl.o_fwd[l] = o; o = align_up(o + ph * ph * g.fwdTiles * g.Khalf * sizeof(float));
         }
         if (pl.desc_kind != DMCR_DESC_S3)
-            pl.o_gd[l] = o, o = align_up(o + (size_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * GBLOCK * sizeof(float));
-        pl.o_adj[l] = o; o = align_up(o + (size_t)g.nChunks * g.N * sizeof(float));
+            pl.o_gd[l] = o, o = align_up(o + ph * ph * gd_floats(g) * sizeof(float));
+        pl.o_adj[l] = o; o = align_up(o + ph * ph * g.nChunks * g.N * sizeof(float));
     }
     pl.bytes = o;
     return DMCR_OK;
@@ -588,15 +602,17 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
             for (const Inst& x : in) {
                 if (x.pl->levels <= l) continue;
                 const LevelGeom& g = x.pl->g[l];
-                RestrictSeg r{};
-                r.ndim = x.pl->ndim;
-                for (int a = 0; a < 3; ++a) r.c[a] = g.n[a];
-                r.fine = x.lv[l - 1];
-                r.coarse = const_cast<float*>(x.lv[l]);
-                r.done = x.use_done ? &x.sc->done : nullptr;
-                r.blockStart = b;
-                b += ceil_div(g.N, ELEM_TH);
-                v.push_back(r);
+                for (int ph = 0; ph < x.pl->phases; ++ph) {
+                    RestrictSeg r{};
+                    r.ndim = x.pl->ndim;
+                    for (int a = 0; a < 3; ++a) r.c[a] = g.n[a];
+                    r.fine = x.lv[l - 1] + (int64_t)ph * x.pl->g[l - 1].N;
+                    r.coarse = const_cast<float*>(x.lv[l]) + (int64_t)ph * g.N;
+                    r.done = x.use_done ? &x.sc->done : nullptr;
+                    r.blockStart = b;
+                    b += ceil_div(g.N, ELEM_TH);
+                    v.push_back(r);
+                }
             }
             P.restricts.push_back({push(P.tb, v), (int)v.size(), b});
         }
@@ -620,24 +636,31 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
                     P.fftf.push_back(fft_job(x, l));
                     continue;
                 }
-                Item it{};
-                it.f.g = g;
-                it.f.field = x.lv[l];
-                it.f.partial = reinterpret_cast<float*>(x.ws + x.pl->o_fwd[l]);
-                it.f.done = x.use_done ? &x.sc->done : nullptr;
-                it.work = (int64_t)g.TY * g.PPB;
-                it.blocks = g.fwdTiles * g.fwdGroupBlocks;
-                items.push_back(it);
+                // block (a, b): tails in phase a, tips in phase b (one field: the single block)
+                const int nph = x.pl->phases;
+                for (int pa = 0; pa < nph; ++pa)
+                    for (int pb = 0; pb < nph; ++pb) {
+                        const int64_t blk = (int64_t)pa * nph + pb;
+                        Item it{};
+                        it.f.g = g;
+                        it.f.field = x.lv[l] + pa * g.N;
+                        it.f.tip = x.lv[l] + pb * g.N;
+                        it.f.partial = reinterpret_cast<float*>(x.ws + x.pl->o_fwd[l]) + blk * g.fwdTiles * g.Khalf;
+                        it.f.done = x.use_done ? &x.sc->done : nullptr;
+                        it.work = (int64_t)g.TY * g.PPB;
+                        it.blocks = g.fwdTiles * g.fwdGroupBlocks;
+                        items.push_back(it);
+                        RedSeg r{};
+                        r.g = g;
+                        r.partial = it.f.partial;
+                        r.desc = x.desc + x.pl->off[l] + blk * g.Khalf;
+                        r.done = it.f.done;
+                        r.weight = x.pl->w[l];
+                        r.blockStart = rb;
+                        rb += ceil_div(g.Khalf, RED_K);
+                        rv.push_back(r);
+                    }
                 P.smem_fwd = std::max(P.smem_fwd, fwd_smem_bytes(g));
-                RedSeg r{};
-                r.g = g;
-                r.partial = it.f.partial;
-                r.desc = x.desc + x.pl->off[l];
-                r.done = it.f.done;
-                r.weight = x.pl->w[l];
-                r.blockStart = rb;
-                rb += ceil_div(g.Khalf, RED_K);
-                rv.push_back(r);
             }
         // heaviest blocks first: the tail of the launch is made of the light ones
         std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.work > b.work; });
@@ -673,7 +696,7 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         std::vector<LossSeg> lvv;
         for (const Inst& x : in) {
             double* pen = reinterpret_cast<double*>(x.ws + x.pl->o_pen);
-            pv.push_back({x.lp.bc_on ? x.field : nullptr, x.pl->N1, x.desc, x.target, x.pl->Ktot, pen,
+            pv.push_back({x.lp.bc_on ? x.field : nullptr, x.pl->N1 * x.pl->phases, x.desc, x.target, x.pl->Ktot, pen,
                           x.use_done ? &x.sc->done : nullptr});
             LossSeg ls{};
             ls.lp = x.lp;
@@ -700,6 +723,7 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         int64_t gb = 0, fb = 0;
         const bool vjp = !(flags & F_LOSS);
         for (const Inst& x : in) {
+            const int nph = x.pl->phases;
             FinalSeg fs{};
             FinalArgs& fa = fs.a;
             fa.ndim = x.pl->ndim;
@@ -708,60 +732,67 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
             for (int l = 0; l < x.pl->levels; ++l) {
                 const LevelGeom& g = x.pl->g[l];
                 float* part = reinterpret_cast<float*>(x.ws + x.pl->o_adj[l]);
+                // phase a's gradient sums the partials of its nph blocks (a, b)
+                fa.parts[l] = part;
+                fa.nChunks[l] = nph * g.nChunks;
+                fa.Nl[l] = g.N;
+                for (int a = 0; a < 3; ++a) fa.nl[l][a] = g.n[a];
                 if (x.pl->desc_kind == DMCR_DESC_S3) {
                     S3Job j = s3_job(x, l, !vjp);
                     j.ens = (flags & F_FWD) ? 0 : 1;
                     P.s3b.push_back(j);
-                    fa.parts[l] = part;
-                    fa.nChunks[l] = g.nChunks;
-                    fa.Nl[l] = g.N;
-                    for (int a = 0; a < 3; ++a) fa.nl[l][a] = g.n[a];
                     continue;
                 }
-                float* Gd = reinterpret_cast<float*>(x.ws + x.pl->o_gd[l]);
-                GSeg gs{};
-                gs.g = g;
-                gs.src = vjp ? x.target + x.pl->off[l] : x.desc + x.pl->off[l];
-                gs.sub = vjp ? nullptr : x.target + x.pl->off[l];
-                gs.sc = vjp ? nullptr : x.sc;
-                gs.scale = gcoef_scale(g, x.pl->tc, x.pl->w[l]);
-                gs.Gd = Gd;
-                gs.done = x.use_done ? &x.sc->done : nullptr;
-                if (x.pl->desc_kind == DMCR_DESC_S2_TILDE) {
-                    TildeSeg t{};
-                    t.src = gs.src;
-                    t.sub = gs.sub;
-                    t.tsum = reinterpret_cast<float*>(x.ws + x.pl->o_tsum) + l;
-                    t.K = g.Khalf;
-                    t.done = gs.done;
-                    tsv.push_back(t);
-                    gs.tsum = t.tsum;
-                    gs.q = x.pl->q_tilde;
-                }
-                gs.blockStart = gb;
-                gb += ceil_div((int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T, GCOEF_TH);
-                gv.push_back(gs);
-                fa.parts[l] = part;
-                fa.nChunks[l] = g.nChunks;
-                fa.Nl[l] = g.N;
-                for (int a = 0; a < 3; ++a) fa.nl[l][a] = g.n[a];
-                if (g.fft) {
-                    Prepared::FftJob j = fft_job(x, l);
-                    j.Gd = Gd;
-                    j.part = part;
-                    P.fftb.push_back(j);
-                    continue;
-                }
-                Item it{};
-                it.a.g = g;
-                it.a.field = x.lv[l];
-                it.a.Gd = Gd;
-                it.a.part = part;
-                it.a.done = gs.done;
-                it.work = (int64_t)g.RZ * g.RY * g.NBc;
-                it.blocks = g.adjTiles * g.nChunks;
-                items.push_back(it);
-                P.smem_adj = std::max(P.smem_adj, adj_smem_bytes(g));
+                const float* src = vjp ? x.target + x.pl->off[l] : x.desc + x.pl->off[l];
+                const float* sub = vjp ? nullptr : x.target + x.pl->off[l];
+                for (int pa = 0; pa < nph; ++pa)
+                    for (int pb = 0; pb < nph; ++pb) {
+                        const int64_t blk = (int64_t)pa * nph + pb, mir = (int64_t)pb * nph + pa;
+                        float* Gd = reinterpret_cast<float*>(x.ws + x.pl->o_gd[l]) + blk * gd_floats(g);
+                        GSeg gs{};
+                        gs.g = g;
+                        gs.src = src + blk * g.Khalf;
+                        gs.sub = sub ? sub + blk * g.Khalf : nullptr;
+                        gs.src2 = src + mir * g.Khalf;
+                        gs.sub2 = sub ? sub + mir * g.Khalf : nullptr;
+                        gs.sc = vjp ? nullptr : x.sc;
+                        gs.scale = gcoef_scale(g, x.pl->tc, x.pl->w[l]);
+                        gs.Gd = Gd;
+                        gs.done = x.use_done ? &x.sc->done : nullptr;
+                        if (x.pl->desc_kind == DMCR_DESC_S2_TILDE) {
+                            TildeSeg t{};
+                            t.src = gs.src;
+                            t.sub = gs.sub;
+                            t.tsum = reinterpret_cast<float*>(x.ws + x.pl->o_tsum) + l;
+                            t.K = g.Khalf;
+                            t.done = gs.done;
+                            tsv.push_back(t);
+                            gs.tsum = t.tsum;
+                            gs.q = x.pl->q_tilde;
+                        }
+                        gs.blockStart = gb;
+                        gb += ceil_div((int64_t)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * g.NB * T, GCOEF_TH);
+                        gv.push_back(gs);
+                        float* pblk = part + blk * g.nChunks * g.N;
+                        if (g.fft) {
+                            Prepared::FftJob j = fft_job(x, l);
+                            j.Gd = Gd;
+                            j.part = pblk;
+                            P.fftb.push_back(j);
+                            continue;
+                        }
+                        Item it{};
+                        it.a.g = g;
+                        it.a.field = x.lv[l] + pa * g.N;
+                        it.a.tip = x.lv[l] + pb * g.N;
+                        it.a.Gd = Gd;
+                        it.a.part = pblk;
+                        it.a.done = gs.done;
+                        it.work = (int64_t)g.RZ * g.RY * g.NBc;
+                        it.blocks = g.adjTiles * g.nChunks;
+                        items.push_back(it);
+                    }
+                if (!g.fft) P.smem_adj = std::max(P.smem_adj, adj_smem_bytes(g));
             }
             const bool pen = !vjp && x.lp.bc_on;
             fa.field = pen ? x.field : nullptr;
@@ -779,9 +810,23 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
                 fa.grad_out = x.grad;
             }
             fs.done = x.use_done ? &x.sc->done : nullptr;
-            fs.blockStart = fb;
-            fb += ceil_div(x.pl->N1, ELEM_TH);
-            fv.push_back(fs);
+            // one assembly segment per phase field: its own partial blocks and field slices
+            const int64_t N1 = x.pl->N1;
+            for (int pa = 0; pa < nph; ++pa) {
+                FinalSeg f = fs;
+                for (int l = 0; l < x.pl->levels; ++l)
+                    if (x.pl->desc_kind != DMCR_DESC_S3)
+                        f.a.parts[l] = fs.a.parts[l] + (int64_t)pa * nph * x.pl->g[l].nChunks * x.pl->g[l].N;
+                auto slice = [&](auto* ptr) { return ptr != nullptr ? ptr + pa * N1 : ptr; };
+                f.a.field = slice(fs.a.field);
+                f.a.grad_out = slice(fs.a.grad_out);
+                f.a.M = slice(fs.a.M);
+                f.a.m = slice(fs.a.m);
+                f.a.v = slice(fs.a.v);
+                f.blockStart = fb;
+                fb += ceil_div(N1, ELEM_TH);
+                fv.push_back(f);
+            }
         }
         std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.work > b.work; });
         std::vector<AdjSeg> av;
@@ -995,7 +1040,7 @@ dmcr_status batch_layout(int count, const dmcr_params* params, BatchLayout& B) {
     size_t tb = table_slack();
     for (int i = 0; i < count; ++i) {
         DMCR_TRY(validate_and_plan(&params[i], B.plans[i]));
-        tb += table_bound(B.plans[i].levels) + 32;
+        tb += table_bound(B.plans[i].levels, B.plans[i].phases) + 32;
     }
     size_t o = 0;
     B.o_tab = o;
@@ -1291,7 +1336,7 @@ dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* o, con
     DMCR_TRY(prepare_device());
     memset(report, 0, sizeof(*report));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (o->init == DMCR_INIT_UNIFORM_SEEDED) launch_init_uniform(field, pl.N1, o->seed, s);
+    if (o->init == DMCR_INIT_UNIFORM_SEEDED) launch_init_uniform(field, pl.N1 * pl.phases, o->seed, s);
     std::vector<Inst> in{single(pl, ws)};
     recon_inst(in[0], o, target_desc, field, state, history);
     const dmcr_status st = reconstruct_insts(in, table_region(pl, ws), pl.tab_bytes, in[0].sc, {o->max_iters},
@@ -1417,7 +1462,8 @@ dmcr_status dmcr_reconstruct_batched(int count, const dmcr_params* params, const
         poll = std::min(poll, opts[i].check_every);
     }
     for (int i = 0; i < count; ++i)
-        if (opts[i].init == DMCR_INIT_UNIFORM_SEEDED) launch_init_uniform(fields[i], B.plans[i].N1, opts[i].seed, s);
+        if (opts[i].init == DMCR_INIT_UNIFORM_SEEDED)
+            launch_init_uniform(fields[i], B.plans[i].N1 * B.plans[i].phases, opts[i].seed, s);
     return reconstruct_insts(in, static_cast<char*>(ws) + B.o_tab, B.tab_bytes,
                              reinterpret_cast<Scalars*>(static_cast<char*>(ws) + B.o_scal), iters, poll, reports,
                              states, s, true);
@@ -1497,8 +1543,8 @@ extern "C" dmcr_status dmcr_descriptor_noalloc(const dmcr_params* p, const float
     Plan pl;
     DMCR_TRY(validate_and_plan(p, pl));
     if (field == nullptr || desc == nullptr) return fail(DMCR_EINVAL, "field/desc is NULL");
-    if (pl.desc_kind != DMCR_DESC_S2 || pl.any_fft)
-        return fail(DMCR_ENOTSUP, "dmcr_descriptor_noalloc computes the direct two-point descriptor only");
+    if (pl.desc_kind != DMCR_DESC_S2 || pl.any_fft || pl.phases != 1)
+        return fail(DMCR_ENOTSUP, "dmcr_descriptor_noalloc computes the direct two-point descriptor of one field only");
     // compact layout: segment tables, pyramid levels 2.. and the forward partials of every level
     Plan cp = pl;
     size_t o = 0;

@@ -17,6 +17,7 @@ constexpr int S3_SHIFTS = 64;      // three-point gradient gather: shifts per pa
 __host__ __device__ inline int gblock_c(int m) { return 4 * T + 2 * m; }
 constexpr int NPEN_BLOCKS = 256;   // fixed grid of the penalty reduction (deterministic)
 constexpr int MAX_DYN_SMEM = 200 * 1024;   // dynamic shared memory limit of the correlation kernels
+constexpr int MAX_PHASES = 8;      // phase fields of one problem (their ordered pairs each get a block)
 
 // One multigrid level, every field handled as 3-D (2-D fields have n[0] = 1, P[0] = 0).
 struct LevelGeom {
@@ -104,7 +105,8 @@ struct FinalArgs {
 // their segment by binary search.  Tables live in device memory (written by blob_kernel).
 struct FwdSeg {
     LevelGeom g;
-    const float* field;
+    const float* field;     // tails of the pairs (x)
+    const float* tip;       // tips of the pairs (x + r): the same field, or another phase's
     float* partial;
     const int* done;
     int64_t blockStart;
@@ -119,7 +121,8 @@ struct RedSeg {
 };
 struct AdjSeg {
     LevelGeom g;
-    const float* field;
+    const float* field;     // own positions y (the gradient's field)
+    const float* tip;       // partners y + r: the same field, or another phase's
     const float* Gd;
     float* part;
     const int* done;
@@ -127,8 +130,10 @@ struct AdjSeg {
 };
 struct GSeg {
     LevelGeom g;
-    const float* src;
+    const float* src;       // dL/dS (or S - S_des) of the block (a, b), shifts r of the half window
     const float* sub;
+    const float* src2;      // the block (b, a), which holds -r; src2 = src, sub2 = sub for a = b
+    const float* sub2;
     const Scalars* sc;
     float scale;
     float* Gd;

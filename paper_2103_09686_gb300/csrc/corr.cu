@@ -323,6 +323,7 @@ corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     if (sg.done != nullptr && *sg.done) return;
     const LevelGeom g = sg.g;
     const float* __restrict__ field = sg.field;
+    const float* __restrict__ tipf = sg.tip;
     float* __restrict__ partial = sg.partial;
     const int64_t local = (int64_t)blockIdx.x - sg.blockStart;
     extern __shared__ __align__(16) float smem[];
@@ -393,8 +394,8 @@ corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
         for (int pr = warp; pr < prAll; pr += NW) {
             const int p = pr / pairRowsH, r = pr - p * pairRowsH;
             const int64_t zz = wrap1(z + bx.rzA + p, n0);
-            const float* srcA = field + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r, n1)) * n2;
-            const float* srcB = field + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r + 1, n1)) * n2;
+            const float* srcA = tipf + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r, n1)) * n2;
+            const float* srcB = tipf + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r + 1, n1)) * n2;
             float* dst = ys + (int64_t)pr * sh.strideP;
             int64_t gx = wrap1(hx0 + lane, n2);
             for (int c = lane; c < sh.colsH; c += 32) {
@@ -449,8 +450,8 @@ corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
             for (int pr = warp; pr < prAll; pr += NW) {
                 const int p = pr / pairRowsH, r = pr - p * pairRowsH;
                 const int64_t zz = wrap1(z + bx.rzA + p, n0);
-                const float* srcA = field + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r, n1)) * n2;
-                const float* srcB = field + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r + 1, n1)) * n2;
+                const float* srcA = tipf + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r, n1)) * n2;
+                const float* srcB = tipf + (zz * n1 + wrap1(y0 + bx.rylo + 2 * r + 1, n1)) * n2;
                 float* dst = ys + (int64_t)pr * sh.strideP;
                 int64_t gx = wrap1(hx0 + lane, n2);
                 for (int c = lane; c < sh.colsH; c += 32) {
@@ -534,6 +535,7 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     if (sg.done != nullptr && *sg.done) return;
     const LevelGeom g = sg.g;
     const float* __restrict__ field = sg.field;
+    const float* __restrict__ tipf = sg.tip;
     const float* __restrict__ Gd = sg.Gd;
     float* __restrict__ part = sg.part;
     const int64_t local = (int64_t)blockIdx.x - sg.blockStart;
@@ -587,8 +589,8 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
         const int64_t gz = wrap1(z + rz, n0);
         // raw halo (pair rows i, i + 32) and the chunk's coefficient rows, copied asynchronously
         for (int i = warp; i < pairRows; i += NW) {
-            const float* srcA = field + (gz * n1 + wrap1(y0 + ryA + i, n1)) * n2;
-            const float* srcB = field + (gz * n1 + wrap1(y0 + ryA + i + 32, n1)) * n2;
+            const float* srcA = tipf + (gz * n1 + wrap1(y0 + ryA + i, n1)) * n2;
+            const float* srcB = tipf + (gz * n1 + wrap1(y0 + ryA + i + 32, n1)) * n2;
             float* dst = ys + i * strideP;
             int64_t gx = wrap1(hx0 + lane, n2);
             for (int c = lane; c < colsH; c += 32) {
@@ -620,8 +622,8 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
         const int slow = __syncthreads_or(rc);
         if (!IDENT && slow) {
             for (int i = warp; i < pairRows; i += NW) {
-                const float* srcA = field + (gz * n1 + wrap1(y0 + ryA + i, n1)) * n2;
-                const float* srcB = field + (gz * n1 + wrap1(y0 + ryA + i + 32, n1)) * n2;
+                const float* srcA = tipf + (gz * n1 + wrap1(y0 + ryA + i, n1)) * n2;
+                const float* srcB = tipf + (gz * n1 + wrap1(y0 + ryA + i + 32, n1)) * n2;
                 float* dst = ys + i * strideP;
                 int64_t gx = wrap1(hx0 + lane, n2);
                 for (int c = lane; c < colsH; c += 32) {
@@ -668,8 +670,10 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     }
 }
 
-// Dense full-window coefficient grid of one level, in adjoint order:
-//   G(r) = scale * (src[k] - sub[k]) * (2 if r = 0),  k = canonical index of +-r,
+// Dense full-window coefficient grid of one level (one phase pair (a, b)), in adjoint order:
+//   G(r) = scale * (src[k] - sub[k]) for r in the half window (k its canonical index),
+//   G(r) = scale * (src2[k] - sub2[k]) for -r in it (k the index of -r),
+//   G(0) = scale * ((src - sub) + (src2 - sub2))[0]   (2 (src - sub)[0] for one field),
 //   scale = weight * (gscale from the loss, or 1) * (c1 alpha / N_l, or 1 / N_l for f(x)=x),
 //   (A, B, C) = (-c1 G, (c1 - c3) G, c3 G)   (f(x) = x: (G, 0, 0)),
 // zero where rx > P2 (padding of the last rx block).  Row (rz, ry) holds NB blocks of 8
@@ -691,14 +695,21 @@ __global__ void gcoef_kernel(const GSeg* __restrict__ segs, int nseg, ThreshCons
     const int rz = rzi - g.P[0], ry = ryi - g.P[1], rx = col - g.P[2];
     float v = 0.f;
     if (rx <= g.P[2]) {
-        int64_t k = canon_index(g, rz, ry, rx);
-        if (k < 0) k = canon_index(g, -rz, -ry, -rx);
-        float d = sg.src[k] - (sg.sub != nullptr ? sg.sub[k] : 0.f);
-        // corrected descriptor: dL/dS_bar = A^T dL/dS_tilde (App. A map, transposed)
-        if (sg.tsum != nullptr) d = k == 0 ? d - sg.q / (1.f - sg.q) * *sg.tsum : d / (1.f - sg.q);
-        float sc = sg.scale * (sg.sc != nullptr ? sg.sc->gscale : 1.f);
-        if (rz == 0 && ry == 0 && rx == 0) sc *= 2.f;
-        v = sc * d;
+        // dL/dS of one block entry; corrected descriptor: dL/dS_bar = A^T dL/dS_tilde (App. A
+        // map, transposed)
+        auto delta = [&](const float* src, const float* sub, int64_t k) {
+            float d = src[k] - (sub != nullptr ? sub[k] : 0.f);
+            if (sg.tsum != nullptr) d = k == 0 ? d - sg.q / (1.f - sg.q) * *sg.tsum : d / (1.f - sg.q);
+            return d;
+        };
+        // r of the half window: block (a, b); -r of it: block (b, a) at r; r = 0 pairs the
+        // position with itself in both blocks (2 dL/dS(0) for a = b)
+        const int64_t k = canon_index(g, rz, ry, rx);
+        float d;
+        if (k == 0) d = delta(sg.src, sg.sub, 0) + delta(sg.src2, sg.sub2, 0);
+        else if (k > 0) d = delta(sg.src, sg.sub, k);
+        else d = delta(sg.src2, sg.sub2, canon_index(g, -rz, -ry, -rx));
+        v = sg.scale * (sg.sc != nullptr ? sg.sc->gscale : 1.f) * d;
     }
     const int b = col / T, m = col % T;
     float A, B, C;

@@ -53,15 +53,21 @@ class Job:
     def bytes_estimate(self) -> int:
         """Device bytes held while resident: field, moments, target, descriptors and the
         job's share of the batch workspace."""
-        n = int(np.prod(self.params.shape))
+        n = int(np.prod(field_shape(self.params)))
         k = _lib.dmcr_descriptor_length(self.params)
         return 4 * (4 * n + 2 * k) + _lib.dmcr_workspace_size(self.params)
 
 
+def field_shape(params: _lib.Params) -> tuple:
+    """Shape of a job's field: the phase stack (phases, *shape) when there are several."""
+    return tuple(params.shape) if params.phases == 1 else (params.phases,) + tuple(params.shape)
+
+
 def iteration_units(params: _lib.Params) -> int:
-    """Voxel-shift pairs of one iteration: sum_l N_l prod_a (2 P_a + 1)."""
+    """Voxel-shift pairs of one iteration: phases^2 sum_l N_l prod_a (2 P_a + 1)."""
     kfull = int(np.prod([2 * w + 1 for w in params.window]))
-    return sum(int(np.prod([s >> l for s in params.shape])) * kfull for l in range(params.levels))
+    return params.phases ** 2 * sum(int(np.prod([s >> l for s in params.shape])) * kfull
+                                    for l in range(params.levels))
 
 
 class _Class:
@@ -137,7 +143,7 @@ class Server:
             p = job.params
             job._tgt = torch.tensor(np.asarray(job.target, dtype=np.float32), device=self.dev)
             job.desc = torch.empty(_lib.dmcr_descriptor_length(p), dtype=torch.float32, device=self.dev)
-            job.field = torch.empty(p.shape, dtype=torch.float32, device=self.dev)
+            job.field = torch.empty(field_shape(p), dtype=torch.float32, device=self.dev)
             _lib.dmcr_init_uniform(job.field, job.opts.seed)
             job.m = torch.zeros_like(job.field)
             job.v = torch.zeros_like(job.field)
@@ -254,7 +260,7 @@ def reconstruct_alone(job: Job, device="cuda") -> Job:
     p = job.params
     tgt = torch.tensor(np.asarray(job.target, dtype=np.float32), device=dev)
     desc = _lib.descriptor(tgt, p)
-    field = torch.empty(p.shape, dtype=torch.float32, device=dev)
+    field = torch.empty(field_shape(p), dtype=torch.float32, device=dev)
     _lib.dmcr_init_uniform(field, job.opts.seed)
     m = torch.zeros_like(field)
     v = torch.zeros_like(field)

@@ -93,3 +93,30 @@ def test_threaded_classes_results_equal_alone(cuda_lib):
         alone = serve.reconstruct_alone(_jobs(dm, serve)[j.job_id])
         assert j.iters_done == alone.iters_done
         np.testing.assert_array_equal(j.result, alone.result)
+
+
+def test_serve_multiphase_job_equals_alone(cuda_lib):
+    # a three-phase job (field stack 3 x 48 x 48) batched with a one-field job
+    dm = cuda_lib
+    from paper_2103_09686_gb300 import serve
+
+    def jobs():
+        mp = serve.Job(job_id=0, params=dm.Params(shape=(48, 48), window=(6, 6), levels=2, phases=3),
+                       target=synthetic.multiphase_grf((48, 48), 3.0, (0.3, 0.3), 77),
+                       opts=dm.ReconOpts(max_iters=80, lr=1e-2, check_every=10, seed=5))
+        one = serve.Job(job_id=1, params=dm.Params(shape=(64, 64), window=(8, 8), levels=2),
+                        target=synthetic.target_2d_grf(64, 3.0, 0.3, 78),
+                        opts=dm.ReconOpts(max_iters=60, lr=1e-2, check_every=10, seed=6))
+        return [mp, one]
+
+    srv = serve.Server(max_slots=4, tick_iters=20)
+    js = jobs()
+    for j in js:
+        srv.submit(j)
+    while not srv.idle():
+        srv.tick()
+    assert js[0].result.shape == (3, 48, 48)
+    for j, a in zip(js, jobs()):
+        alone = serve.reconstruct_alone(a)
+        assert j.iters_done == alone.iters_done
+        np.testing.assert_array_equal(j.result, alone.result)

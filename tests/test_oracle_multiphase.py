@@ -120,3 +120,17 @@ def test_partition_generator():
     assert F.shape == (3, 16, 20)
     assert np.array_equal(F.sum(axis=0), np.ones((16, 20)))
     assert [int(F[a].sum()) for a in range(3)] == [64, 160, 96]
+
+
+def test_sampled_gradient_equals_the_full_gradient():
+    # gather form at sampled positions against the scatter form of the full VJP
+    rng = np.random.default_rng(10)
+    shape = (16, 12)
+    p = oracle.Params(ndim=2, window=(3, 2), levels=2)
+    K = oracle.half_window(2, p.window).shape[0]
+    F = rng.uniform(-0.2, 1.2, (3,) + shape)
+    G = rng.standard_normal(2 * 9 * K)
+    full = oracle.multiphase_descriptor_vjp(F, p, G).reshape(3, -1)
+    pos = rng.choice(F[0].size, 12, replace=False)
+    got = oracle.multiphase_vjp_at(F, p, G, pos)
+    assert _rel(got, full[:, pos]) < 1e-12
