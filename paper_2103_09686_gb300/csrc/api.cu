@@ -144,7 +144,7 @@ struct Plan {
     size_t o_tsum = 0;         // corrected descriptor: per-level residual sums (floats)
     int64_t s3Kpad = 0, s3Npad[MAX_LEVELS] = {};
     size_t o_eh[MAX_LEVELS] = {}, o_el[MAX_LEVELS] = {}, o_eth[MAX_LEVELS] = {}, o_etl[MAX_LEVELS] = {},
-           o_w[MAX_LEVELS] = {}, o_gh[MAX_LEVELS] = {}, o_gl[MAX_LEVELS] = {};
+           o_w[MAX_LEVELS] = {}, o_gh[MAX_LEVELS] = {}, o_gl[MAX_LEVELS] = {}, o_amax[MAX_LEVELS] = {};
     size_t bytes = 0;
 };
 
@@ -395,13 +395,15 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             pl.o_dc[l] = o; o = align_up(o + 16);
         } else if (pl.desc_kind == DMCR_DESC_S3) {
             const size_t Kp = (size_t)pl.s3Kpad, Np = (size_t)pl.s3Npad[l];
-            pl.o_eh[l] = o; o = align_up(o + Np * Kp * sizeof(float));
-            pl.o_el[l] = o; o = align_up(o + Np * Kp * sizeof(float));
-            pl.o_eth[l] = o; o = align_up(o + Np * Kp * sizeof(float));
-            pl.o_etl[l] = o; o = align_up(o + Np * Kp * sizeof(float));
+            // FP16 operand pairs, FP32 W^T, two scale sources
+            pl.o_eh[l] = o; o = align_up(o + Np * Kp * sizeof(uint16_t));
+            pl.o_el[l] = o; o = align_up(o + Np * Kp * sizeof(uint16_t));
+            pl.o_eth[l] = o; o = align_up(o + Np * Kp * sizeof(uint16_t));
+            pl.o_etl[l] = o; o = align_up(o + Np * Kp * sizeof(uint16_t));
             pl.o_w[l] = o; o = align_up(o + Np * Kp * sizeof(float));
-            pl.o_gh[l] = o; o = align_up(o + Kp * Kp * sizeof(float));
-            pl.o_gl[l] = o; o = align_up(o + Kp * Kp * sizeof(float));
+            pl.o_gh[l] = o; o = align_up(o + Kp * Kp * sizeof(uint16_t));
+            pl.o_gl[l] = o; o = align_up(o + Kp * Kp * sizeof(uint16_t));
+            pl.o_amax[l] = o; o = align_up(o + 2 * sizeof(float));
         } else {
             pl.o_fwd[l] = o; o = align_up(o + ph * ph * g.fwdTiles * g.Khalf * sizeof(float));
         }
@@ -550,13 +552,14 @@ S3Job s3_job(const Inst& x, int l, bool loss) {
     j.K = pl.g[l].Khalf;
     j.Kpad = pl.s3Kpad;
     j.Npad = pl.s3Npad[l];
-    j.Eh = reinterpret_cast<float*>(x.ws + pl.o_eh[l]);
-    j.El = reinterpret_cast<float*>(x.ws + pl.o_el[l]);
-    j.Eth = reinterpret_cast<float*>(x.ws + pl.o_eth[l]);
-    j.Etl = reinterpret_cast<float*>(x.ws + pl.o_etl[l]);
+    j.Eh = reinterpret_cast<uint16_t*>(x.ws + pl.o_eh[l]);
+    j.El = reinterpret_cast<uint16_t*>(x.ws + pl.o_el[l]);
+    j.Eth = reinterpret_cast<uint16_t*>(x.ws + pl.o_eth[l]);
+    j.Etl = reinterpret_cast<uint16_t*>(x.ws + pl.o_etl[l]);
     j.W = reinterpret_cast<float*>(x.ws + pl.o_w[l]);
-    j.Gh = reinterpret_cast<float*>(x.ws + pl.o_gh[l]);
-    j.Gl = reinterpret_cast<float*>(x.ws + pl.o_gl[l]);
+    j.Gh = reinterpret_cast<uint16_t*>(x.ws + pl.o_gh[l]);
+    j.Gl = reinterpret_cast<uint16_t*>(x.ws + pl.o_gl[l]);
+    j.amax = reinterpret_cast<float*>(x.ws + pl.o_amax[l]);
     j.desc = x.desc + pl.off[l];
     j.src = loss ? x.desc + pl.off[l] : x.target + pl.off[l];
     j.sub = loss ? x.target + pl.off[l] : nullptr;

@@ -198,10 +198,13 @@ struct S3Job {
     LevelGeom g;
     const float* field;     // this level's field
     int64_t K, Kpad, Npad;
-    float *Eh, *El;         // E (Npad x Kpad), TF32-exact high part and remainder
-    float *Eth, *Etl;       // E^T (Kpad x Npad)
+    // GEMM operands as FP16 bit patterns: x s = hi + lo (hi = fp16(x s), lo = fp16(x s - hi)),
+    // s a power of two that brings max |x| into [1/2, 1) (E: f(x) = x only; G: always)
+    uint16_t *Eh, *El;      // E (Npad x Kpad)
+    uint16_t *Eth, *Etl;    // E^T (Kpad x Npad)
     float* W;               // W^T (Kpad x Npad)
-    float *Gh, *Gl;         // G (Kpad x Kpad)
+    uint16_t *Gh, *Gl;      // G (Kpad x Kpad)
+    float* amax;            // [0] max |G|, [1] max |field| (f(x) = x): the scales' sources
     float* desc;            // this level's K x K block of the descriptor (w * S_bar3)
     const float* src;       // G = weight * (sc ? gscale : 1) * (src - sub): src = desc (loss) or
     const float* sub;       //   the upstream gradient (VJP, sub = null, sc = null)

@@ -191,13 +191,16 @@ __device__ __forceinline__ void fwd_chunk(const float2 (&x2)[T], const float2 (&
 // y2[j] partners at column j; pair (k, m) uses y2[k + m].  acc[k] += G(r_m) h(s) per row with
 // h(s) written s (C + s (B + A s)), A = -c1 G, B = (c1 - c3) G, C = c3 G (identity: G a).
 // The soft modes leave the rows swapped in acc (row lane in .y).  Coefficients per block:
-// (A, A, B, B) for m = 0..7, then (C_m, C_m, C_m+1, C_m+1) for even m.
-template <int MODE>
+// (A, A, B, B) for m = 0..7, then (C_m, C_m, C_m+1, C_m+1) for even m.  PARTIAL: only the
+// first mv shifts lie in the window (the last block of a row; the others have zero
+// coefficients, so skipping them leaves acc bitwise unchanged).
+template <int MODE, bool PARTIAL = false>
 __device__ __forceinline__ void adj_block(const float2 (&x2)[T], const float2 (&y2)[2 * T],
-                                          const float4* __restrict__ cf, float2 (&acc)[T]) {
+                                          const float4* __restrict__ cf, float2 (&acc)[T], int mv = T) {
     const float2 one2 = make_float2(1.0f, 1.0f);
 #pragma unroll
     for (int m = 0; m < T; ++m) {
+        if (PARTIAL && m >= mv) break;
         const float4 ab = cf[m];
         const float4 cc = cf[T + m / 2];
         const float2 A2 = make_float2(ab.x, ab.y);
@@ -512,17 +515,25 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedSeg* __restric
 
 // ------------------------------------------------------------------------- adjoint
 
+// lastValid: shifts of the chunk's last rx block inside the window (T unless the chunk ends
+// the row and 2 P2 + 1 is not a multiple of T); block-uniform
 template <int MODE>
 __device__ __forceinline__ void adj_rows(const float* ys, const float* Gs, int strideP, int NB, int ryN, int lane,
-                                         int strip, const float2 (&x2)[T], float2 (&acc)[T]) {
+                                         int strip, const float2 (&x2)[T], float2 (&acc)[T], int lastValid) {
+    const int nFull = lastValid < T ? NB - 1 : NB;
     for (int r = 0; r < ryN; ++r) {
         const float* yrow = ys + (lane + r) * strideP + 2 * T * strip;
         const float4* grow = reinterpret_cast<const float4*>(Gs + r * (NB * GBLOCK));
 #pragma unroll 1
-        for (int bb = 0; bb < NB; ++bb) {
+        for (int bb = 0; bb < nFull; ++bb) {
             float2 y2[2 * T];
             load_pairs16(yrow + 2 * T * bb, y2);
             adj_block<MODE>(x2, y2, grow + (GBLOCK / 4) * bb, acc);
+        }
+        if (nFull < NB) {
+            float2 y2[2 * T];
+            load_pairs16(yrow + 2 * T * nFull, y2);
+            adj_block<MODE, true>(x2, y2, grow + (GBLOCK / 4) * nFull, acc, lastValid);
         }
     }
 }
@@ -557,6 +568,7 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     const int ryN = ryB - ryA;
     const int bbA = xc * g.NBc;
     const int nbb = min(g.NBc, g.NB - bbA);
+    const int lastValid = bbA + nbb == g.NB ? 2 * g.P[2] + 1 - T * (g.NB - 1) : T;
     const int colsH = T * nbb + 4 * T;      // read extent: 8 strip + 8 bb + 16 columns
     const int strideP = stride_4mod32(2 * colsH);
     const int pairRows = 32 + ryN - 1;      // pair row i holds halo rows i and i + 32
@@ -651,9 +663,9 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
             }
         }
         __syncthreads();
-        if (IDENT) adj_rows<MODE_IDENT>(ys, Gs, strideP, nbb, ryN, lane, strip, x2, acc);
-        else if (slow) adj_rows<MODE_SLOW>(ys, Gs, strideP, nbb, ryN, lane, strip, x2, acc);
-        else adj_rows<MODE_FAST>(ys, Gs, strideP, nbb, ryN, lane, strip, x2, acc);
+        if (IDENT) adj_rows<MODE_IDENT>(ys, Gs, strideP, nbb, ryN, lane, strip, x2, acc, lastValid);
+        else if (slow) adj_rows<MODE_SLOW>(ys, Gs, strideP, nbb, ryN, lane, strip, x2, acc, lastValid);
+        else adj_rows<MODE_FAST>(ys, Gs, strideP, nbb, ryN, lane, strip, x2, acc, lastValid);
     }
 
 #pragma unroll

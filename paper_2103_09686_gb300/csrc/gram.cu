@@ -4,24 +4,28 @@
 // footnote of Sec. 3.4), and the gradient of a loss on it.
 //
 //   ens_kernel      e and f' never leave the chip except as the GEMM operands: E (N x K)
-//                   and E^T (K x N), each split into a TF32-exact high part and the FP32
-//                   remainder (e = hi + lo exactly);
-//   tc_gemm_kernel  C = A B^T on the 5th-generation tensor cores: tcgen05.mma kind::tf32
-//                   from shared memory, FP32 accumulators in TMEM drained every 256
+//                   and E^T (K x N), each split into two FP16 parts, e s = hi + lo with
+//                   hi = fp16(e s), lo = fp16(e s - hi) (22 significant bits; s = 1 for the
+//                   soft threshold, whose f is bounded, and a power of two bringing max |M|
+//                   into [1/2, 1) for f(x) = x);
+//   tc_gemm_kernel  C = A B^T on the 5th-generation tensor cores: tcgen05.mma kind::f16
+//                   from shared memory, FP32 accumulators in TMEM drained every 512
 //                   reduction steps into FP32 registers, three products
-//                   hi*hi + hi*lo + lo*hi per k-step (error ~2^-21 relative per product),
-//                   operands staged by cp.async in three stages (128-byte swizzled
-//                   K-major layout), one thread issues the MMAs
-//                   and commits them to an mbarrier per stage;
+//                   hi*hi + hi*lo + lo*hi per k-step (the dropped lo*lo is below 2^-22 of the
+//                   product), operands staged by TMA in three stages (128-byte swizzled
+//                   K-major layout), one thread issues the MMAs and commits them to an
+//                   mbarrier per stage; the epilogue undoes the operands' scales exactly;
 //                   Gram:  S_bar3 = Et Et^T w/N (upper-triangle tiles, mirrored);
 //                   W:     W^T = (2/N) G E^T  as  E G^T with a transposed epilogue;
 //   g3_split_kernel G = w * gscale * (D3 - D3_des) symmetrised (or the upstream gradient),
-//                   split like E;
+//                   scaled by the power of two that brings max |G| (g3_absmax_kernel) into
+//                   [1/2, 1), split like E;
 //   s3_gather_kernel g_y = sum_r 1/2 [W(r, y) f'(a_y(r)) + W(r, y - r) f'(a_{y-r}(r))]
 //                   (weight 1 at r = 0), the two ends of every shift vector.
 // Every wait on an mbarrier is bounded; a timeout sets an error flag that the host reads.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -36,6 +40,8 @@ struct GemmArgs {
     CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
     int M, N, K;
     float scale;
+    const float* amaxA;     // operand scale sources (null: unscaled); C *= 2^(eA + eB)
+    const float* amaxB;
     float* C;
     int64_t ldc;
     int mode;               // 0 C[m][n], 1 symmetric Gram (upper tiles, mirrored), 2 C[n][m]
@@ -46,10 +52,12 @@ struct GemmArgs {
 
 // the same with plain device pointers (host side)
 struct GemmOperands {
-    const float *Ah, *Al, *Bh, *Bl;
+    const uint16_t *Ah, *Al, *Bh, *Bl;   // FP16 bit patterns
     int64_t lda, ldb;
     int M, N, K;
     float scale;
+    const float* amaxA;
+    const float* amaxB;
     float* C;
     int64_t ldc;
     int mode;
@@ -60,24 +68,24 @@ struct GemmOperands {
 
 namespace {
 
-constexpr int GM = 128, GN = 128, GK = 32;            // tile: 128 x 128 outputs, 32 reduction steps
-constexpr int TILE_BYTES = GM * GK * 4;                // one operand tile, 16 KB
+constexpr int GM = 128, GN = 128, GK = 64;            // tile: 128 x 128 outputs, 64 reduction steps
+constexpr int TILE_BYTES = GM * GK * 2;                // one FP16 operand tile (128-byte rows), 16 KB
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;            // A hi, A lo, B hi, B lo
 constexpr int GSTAGES = 3;
 constexpr int GEMM_THREADS = 192;                     // warps 0-3 epilogue, 4 TMA, 5 MMA
 constexpr uint32_t TMEM_COLS = 512;                    // 2 buffers x (main + cross) FP32, 128 lanes x 128 columns each
 // The tensor core adds into its FP32 accumulator without round-to-nearest: over a long
 // reduction the error is biased toward zero (~4e-8 relative per accumulation measured on
-// GB300).  So TMEM accumulates at most FLUSH k-blocks (FLUSH * 32 reduction steps) before the
-// partial sums are added, rounded to nearest, into FP32 registers; the small cross terms
-// hi*lo + lo*hi accumulate separately from hi*hi.
+// GB300).  So TMEM accumulates at most FLUSH k-blocks (FLUSH * 64 reduction steps, 32 MMAs
+// per accumulator) before the partial sums are added, rounded to nearest, into FP32
+// registers; the small cross terms hi*lo + lo*hi accumulate separately from hi*hi.
 constexpr int FLUSH = 8;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
-// instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2),
+// instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B F16 (bits 7-9, 10-12 = 0),
 // both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
-constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(GN >> 3) << 17) |
-                                ((uint32_t)(GM >> 4) << 24);
+constexpr uint32_t IDESC_F16 = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(GN >> 3) << 17) |
+                               ((uint32_t)(GM >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -132,20 +140,20 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 }
 
 // shared-memory matrix descriptor, K-major with the 128-byte swizzle: each operand row is
-// one 128-byte line (32 TF32) whose 16-byte chunks are stored at chunk ^ (row % 8); atoms of
+// one 128-byte line (64 FP16) whose 16-byte chunks are stored at chunk ^ (row % 8); atoms of
 // 8 rows (1024 bytes, 1024-byte aligned) follow each other at SBO = 1024; LBO is unused by
 // this layout (encoded 1); descriptor version 1, layout type 2 (SWIZZLE_128B).  A k-step of
-// 8 TF32 starts 32 bytes further into the line.
+// 16 FP16 starts 32 bytes further into the line.
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
            (2ull << 61);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(IDESC_TF32), "r"(acc)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(IDESC_F16), "r"(acc)
         : "memory");
 }
 
@@ -170,18 +178,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ void split_tf32(float e, float& hi, float& lo) {
-    hi = __uint_as_float(__float_as_uint(e) & 0xFFFFE000u);
-    lo = e - hi;
+// x = hi + lo to 22 significant bits (both FP16, round to nearest)
+__device__ __forceinline__ void split_f16(float x, uint16_t& hi, uint16_t& lo) {
+    const __half h = __float2half_rn(x);
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+}
+
+// exponent e of the scale 2^-e that maps max |x| = *amax into [1/2, 1); 0 without a source,
+// for 0 and for non-finite maxima
+__device__ __forceinline__ int scale_exp(const float* amax) {
+    if (amax == nullptr) return 0;
+    const float a = *amax;
+    if (!(a > 0.f) || !isfinite(a)) return 0;
+    int e;
+    frexpf(a, &e);
+    return e;
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------------- GEMM
 
-// C = scale * A B^T with A (M x K) and B (N x K) row-major (K contiguous), each given as
-// hi + lo through four TMA tensor maps (box 32 x 128, 128-byte swizzle).  M, N multiples of
-// 128, K a multiple of 32.  mode 0: C[m][n]; mode 1 (Gram, A = B): only tiles bn >= bm,
+// C = scale 2^(eA + eB) A B^T with A (M x K) and B (N x K) row-major (K contiguous), each given
+// as FP16 hi + lo through four TMA tensor maps (box 64 x 128, 128-byte swizzle).  M, N
+// multiples of 128, K a multiple of 64.  mode 0: C[m][n]; mode 1 (Gram, A = B): only tiles bn >= bm,
 // written to C[m][n] and C[n][m]; mode 2: C[n][m].  Entries with m >= Mvalid or
 // n >= Nvalid are not written.
 //
@@ -270,16 +291,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
                 const uint32_t st = smem_u32(gsm + s * STAGE_BYTES);
                 const uint32_t t_main = tmem + (uint32_t)buf * (2 * GN), t_cross = t_main + GN;
 #pragma unroll
-                for (int ks = 0; ks < GK / 8; ++ks) {
-                    const uint32_t off = ks * 32;   // 8 TF32 = 32 bytes per k-step
+                for (int ks = 0; ks < GK / 16; ++ks) {
+                    const uint32_t off = ks * 32;   // 16 FP16 = 32 bytes per k-step
                     const uint64_t ah = smem_desc_sw128(st + 0 * TILE_BYTES + off);
                     const uint64_t al = smem_desc_sw128(st + 1 * TILE_BYTES + off);
                     const uint64_t bh = smem_desc_sw128(st + 2 * TILE_BYTES + off);
                     const uint64_t bl = smem_desc_sw128(st + 3 * TILE_BYTES + off);
                     const uint32_t more = (kb % FLUSH != 0) || ks != 0;
-                    mma_tf32(t_main, ah, bh, more);
-                    mma_tf32(t_cross, ah, bl, more);
-                    mma_tf32(t_cross, al, bh, 1);
+                    mma_f16(t_main, ah, bh, more);
+                    mma_f16(t_cross, ah, bl, more);
+                    mma_f16(t_cross, al, bh, 1);
                 }
                 mma_commit(&empty[s]);
                 if (kb % FLUSH == FLUSH - 1 || kb == nk - 1) mma_commit(&tfull[buf]);
@@ -310,12 +331,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
             mbar_arrive(&tempty[buf]);
         }
         const int m = bm * GM + 32 * warp + lane;
+        // undo the operands' power-of-two scales together with the output scale (exact)
+        const float scale = ldexpf(g.scale, scale_exp(g.amaxA) + scale_exp(g.amaxB));
         if (ok && m < g.Mvalid) {
 #pragma unroll
             for (int c = 0; c < GN; ++c) {
                 const int n = bn * GN + c;
                 if (n >= g.Nvalid) continue;
-                const float x = g.scale * acc[c];
+                const float x = scale * acc[c];
                 if (g.mode == 2) {
                     g.C[(int64_t)n * g.ldc + m] = x;
                 } else {
@@ -396,8 +419,10 @@ __device__ __forceinline__ float sig_pair(const ThreshConst& tc, float u, float 
 // (coalesced over shifts) through a shared transpose; padding entries are 0
 __global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
     if (j.done != nullptr && *j.done) return;
-    __shared__ float th[32][33], tl[32][33];
+    __shared__ uint16_t th[32][34], tl[32][34];
     const LevelGeom& g = j.g;
+    // f(x) = x: e is bounded by max |M|, scaled into [-1, 1); the soft f is bounded by ~1.03
+    const float sE = ldexpf(1.f, -(tc.identity ? scale_exp(j.amax + 1) : 0));
     const int64_t x0 = (int64_t)(blockIdx.x % (j.Npad / 32)) * 32;
     const int64_t k0 = (int64_t)(blockIdx.x / (j.Npad / 32)) * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -414,8 +439,8 @@ __global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
             const float v = j.field[partner(g, px, rz, ry, rx)];
             e = tc.identity ? 0.5f * (u + v) : fmaf(tc.c1, sig_pair(tc, u, v), tc.c3);
         }
-        float hi, lo;
-        split_tf32(e, hi, lo);
+        uint16_t hi, lo;
+        split_f16(e * sE, hi, lo);
         j.Eth[k * j.Npad + x] = hi;
         j.Etl[k * j.Npad + x] = lo;
         th[kk][tx] = hi;
@@ -428,21 +453,54 @@ __global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
     }
 }
 
-// G = w * gscale * sym(D3 - D3_des) on the level's K x K block (zero padding to Kpad), split
+// G(a, b) = w * gscale * sym(D3 - D3_des) on the level's K x K block; d<G, E^T E>/dE =
+// E (G + G^T), so G is symmetrised (the loss gradient already is symmetric)
+__device__ __forceinline__ float g3_value(const S3Job& j, int64_t a, int64_t b) {
+    const float dab = j.src[a * j.K + b] - (j.sub != nullptr ? j.sub[a * j.K + b] : 0.f);
+    const float dba = j.src[b * j.K + a] - (j.sub != nullptr ? j.sub[b * j.K + a] : 0.f);
+    return j.weight * (j.sc != nullptr ? j.sc->gscale : 1.f) * 0.5f * (dab + dba);
+}
+
+// max |v| of a block's values into *out (non-negative floats order like their bit patterns;
+// *out starts at 0)
+__device__ __forceinline__ void block_absmax(float m, float* out) {
+    __shared__ float sh[8];
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[w]);
+        atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
+    }
+}
+
+__global__ void __launch_bounds__(256) g3_absmax_kernel(S3Job j) {
+    if (j.done != nullptr && *j.done) return;
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < j.K * j.K;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(g3_value(j, i / j.K, i % j.K)));
+    block_absmax(m, j.amax);
+}
+
+// f(x) = x: max |M| of the level's field, the bound of |e|
+__global__ void __launch_bounds__(256) field_absmax_kernel(S3Job j) {
+    if (j.done != nullptr && *j.done) return;
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < j.g.N; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(j.field[i]));
+    block_absmax(m, j.amax + 1);
+}
+
+// G scaled by 2^-eG (max |G| into [1/2, 1)) and split into FP16 hi + lo; zero padding to Kpad
 __global__ void g3_split_kernel(S3Job j) {
     if (j.done != nullptr && *j.done) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)j.Kpad * j.Kpad) return;
     const int64_t a = i / j.Kpad, b = i % j.Kpad;
-    float v = 0.f;
-    if (a < j.K && b < j.K) {
-        // d<G, E^T E>/dE = E (G + G^T): symmetrise (the loss gradient already is symmetric)
-        const float dab = j.src[a * j.K + b] - (j.sub != nullptr ? j.sub[a * j.K + b] : 0.f);
-        const float dba = j.src[b * j.K + a] - (j.sub != nullptr ? j.sub[b * j.K + a] : 0.f);
-        v = j.weight * (j.sc != nullptr ? j.sc->gscale : 1.f) * 0.5f * (dab + dba);
-    }
-    float hi, lo;
-    split_tf32(v, hi, lo);
+    const float v = (a < j.K && b < j.K) ? g3_value(j, a, b) : 0.f;
+    uint16_t hi, lo;
+    split_f16(ldexpf(v, -scale_exp(j.amax)), hi, lo);
     j.Gh[i] = hi;
     j.Gl[i] = lo;
 }
@@ -507,15 +565,15 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// rows x cols FP32 row-major (row stride ld elements), boxes of 128 rows x 32 columns
-bool make_map(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, int64_t ld) {
+// rows x cols FP16 row-major (row stride ld elements), boxes of 128 rows x 64 columns
+bool make_map(CUtensorMap* m, const uint16_t* base, int64_t rows, int64_t cols, int64_t ld) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (enc == nullptr) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(uint16_t)};
     const cuuint32_t box[2] = {(cuuint32_t)GK, (cuuint32_t)GM};
     const cuuint32_t estr[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<uint16_t*>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -536,6 +594,8 @@ void launch_tc_gemm(const GemmOperands& o, cudaStream_t s) {
     }
     a.M = o.M; a.N = o.N; a.K = o.K;
     a.scale = o.scale;
+    a.amaxA = o.amaxA;
+    a.amaxB = o.amaxB;
     a.C = o.C;
     a.ldc = o.ldc;
     a.mode = o.mode;
@@ -545,10 +605,23 @@ void launch_tc_gemm(const GemmOperands& o, cudaStream_t s) {
     tc_gemm_kernel<<<(unsigned)blocks, GEMM_THREADS, gemm_smem_bytes(), s>>>(a);
 }
 
-void launch_s3_forward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s) {
+constexpr int ABSMAX_BLOCKS = 512;
+
+// E and E^T of one level (f(x) = x: after the bound of |e|)
+void launch_ensemble(const S3Job& j, const ThreshConst& tc, cudaStream_t s) {
+    if (tc.identity) {
+        set_flag_kernel<<<1, 1, 0, s>>>(reinterpret_cast<int*>(j.amax + 1), 0);
+        const int64_t blocks = std::min<int64_t>(ABSMAX_BLOCKS, (j.g.N + 255) / 256);
+        field_absmax_kernel<<<(unsigned)blocks, 256, 0, s>>>(j);
+    }
     ens_kernel<<<(unsigned)((j.Npad / 32) * (j.Kpad / 32)), 256, 0, s>>>(j, tc);
+}
+
+void launch_s3_forward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s) {
+    launch_ensemble(j, tc, s);
     GemmOperands a{};
     a.Ah = j.Eth; a.Al = j.Etl; a.Bh = j.Eth; a.Bl = j.Etl;
+    a.amaxA = a.amaxB = tc.identity ? j.amax + 1 : nullptr;
     a.lda = a.ldb = j.Npad;
     a.M = a.N = (int)j.Kpad;
     a.K = (int)j.Npad;
@@ -563,11 +636,15 @@ void launch_s3_forward(const S3Job& j, const ThreshConst& tc, int* err, cudaStre
 }
 
 void launch_s3_backward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s) {
-    if (j.ens) ens_kernel<<<(unsigned)((j.Npad / 32) * (j.Kpad / 32)), 256, 0, s>>>(j, tc);
+    if (j.ens) launch_ensemble(j, tc, s);
+    set_flag_kernel<<<1, 1, 0, s>>>(reinterpret_cast<int*>(j.amax), 0);
+    g3_absmax_kernel<<<(unsigned)std::min<int64_t>(ABSMAX_BLOCKS, (j.K * j.K + 255) / 256), 256, 0, s>>>(j);
     const int64_t nG = j.Kpad * j.Kpad;
     g3_split_kernel<<<(unsigned)((nG + 255) / 256), 256, 0, s>>>(j);
     GemmOperands a{};
     a.Ah = j.Eh; a.Al = j.El; a.Bh = j.Gh; a.Bl = j.Gl;
+    a.amaxA = tc.identity ? j.amax + 1 : nullptr;
+    a.amaxB = j.amax;
     a.lda = j.Kpad;
     a.ldb = j.Kpad;
     a.M = (int)j.Npad;

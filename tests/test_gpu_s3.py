@@ -114,3 +114,29 @@ def test_s3_adam_steps_reduce_the_loss(cuda_lib):
     assert rep["rel_err"] < 0.5
     first, _ = dm.loss_grad(_dev(synthetic.uniform_field((n, n), 9)), D, p)
     assert rep["L"] < 0.5 * float(first[4])
+
+
+def test_s3_identity_values_beyond_the_fp16_range(cuda_lib):
+    # f(x) = x: e = (M_x + M_{x+r}) / 2 reaches 2e5, beyond FP16; the ensemble is scaled by a
+    # power of two before the split and the Gram is scaled back
+    dm = cuda_lib
+    shape, window = (24, 20), (3, 4)
+    p = dm.Params(shape=shape, window=window, descriptor=dm.DMCR_DESC_S3, threshold=dm.DMCR_IDENTITY)
+    M = np.random.default_rng(13).uniform(-1e5, 2e5, shape)
+    got = dm.descriptor(_dev(M), p).cpu().numpy().astype(np.float64)
+    want = oracle.s3_descriptor(M, _op(p))
+    np.testing.assert_allclose(got, want, rtol=1e-5, atol=1e-6 * np.max(np.abs(want)))
+
+
+@pytest.mark.parametrize("gscale", [1e-12, 1e6])
+def test_s3_vjp_of_tiny_and_large_upstream_gradients(cuda_lib, gscale):
+    # G far below or above the FP16 range: scaled into [1/2, 1) before the split
+    dm = cuda_lib
+    shape, window = (24, 24), (5, 4)
+    p = dm.Params(shape=shape, window=window, descriptor=dm.DMCR_DESC_S3)
+    M = _field(shape, 15, "relaxed")
+    K = oracle.half_window(2, window).shape[0]
+    G = gscale * np.random.default_rng(16).standard_normal(K * K)
+    g = dm.descriptor_vjp(_dev(M), _dev(G), p).cpu().numpy().astype(np.float64)
+    g_ref = oracle.s3_level_vjp(M, _op(p), G.reshape(K, K))
+    assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) < 1e-5
