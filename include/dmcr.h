@@ -70,8 +70,9 @@ enum { DMCR_PROLONG_ADJOINT_ACCUMULATE = 0, DMCR_PROLONG_INJECT = 1 };
  * (Sec. 3.2.4).  S3: the full quadratic reduction of the ensemble, Eq. s3,
  * S_bar3(r_a, r_b) = (1/N) sum_x e_x(r_a) e_x(r_b) for every pair of half-window shifts: a
  * K_half x K_half matrix per level, row-major, whose diagonal is S_bar2 (the Gram matrix of
- * the ensemble, Sec. 3.4 footnote).  S3 is computed on the tensor cores (TF32 operands
- * split in three products, FP32 accumulation) and needs the DIRECT or AUTO path. */
+ * the ensemble, Sec. 3.4 footnote).  S3 is computed on the tensor cores (operands split
+ * into two FP16 parts after a power-of-two scaling, three products, FP32 accumulation;
+ * FP32-level accuracy) and needs the DIRECT or AUTO path. */
 /* S2_TILDE: the corrected two-point descriptor of App. A (Eq. s2rfroms2rbar), per level
  * S_tilde(0) = S_bar(0) and S_tilde(r) = (S_bar(r) - 2 f(1/2)^2 S_bar(0)) / (1 - 2 f(1/2)^2),
  * K_half floats per level (equal to the exact S2 of binary fields); any path. */

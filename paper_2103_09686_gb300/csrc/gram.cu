@@ -234,8 +234,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
         }
         bn = bm + (int)t;
     } else {
-        bm = (int)(blockIdx.x % tilesM);
-        bn = (int)(blockIdx.x / tilesM);
+        // B tiles fastest: the CTAs in flight share a few A row blocks and sweep the whole of
+        // B (the W GEMM's G, Kpad x Kpad, stays in L2), so A streams from DRAM once
+        const int tilesN = g.N / GN;
+        bn = (int)(blockIdx.x % tilesN);
+        bm = (int)(blockIdx.x / tilesN);
     }
     if (tid == 0) {
         for (int s = 0; s < GSTAGES; ++s) {
