@@ -46,9 +46,9 @@ RCP_PER_PAIR = {"corr_fwd": 0.5, "corr_adj": 5.0 / 8.0 * 0.5 + 3.0 / 8.0}
 # DRAM bytes (read + write) per launch of the current kernels on the 512^2, +-64, 3-level
 # workload, from the ncu full-set capture summarised in profiles/corr_kernels_grf512_w64_L3.md
 # (None whenever the kernels changed since the last capture).
-NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2694912 + 36096, ("grf512", "corr_fwd"): 1450752 + 256,
+NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2706944 + 21760, ("grf512", "corr_fwd"): 1452288 + 2560,
                      # profiles/launches_mp3_512_w64_L3.md
-                     ("mp3_512", "corr_adj"): 15959296 + 259887872, ("mp3_512", "corr_fwd"): 4220928 + 44103168}
+                     ("mp3_512", "corr_adj"): 16637440 + 259935488, ("mp3_512", "corr_fwd"): 4471808 + 44815616}
 
 WORKLOADS = {
     "grf512": dict(shape=(512, 512), window=(64, 64), levels=3,

@@ -423,12 +423,19 @@ __device__ __forceinline__ float sig_pair(const ThreshConst& tc, float u, float 
 __global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
     if (j.done != nullptr && *j.done) return;
     __shared__ uint16_t th[32][34], tl[32][34];
+    __shared__ int3 shifts[32];
     const LevelGeom& g = j.g;
     // f(x) = x: e is bounded by max |M|, scaled into [-1, 1); the soft f is bounded by ~1.03
     const float sE = ldexpf(1.f, -(tc.identity ? scale_exp(j.amax + 1) : 0));
     const int64_t x0 = (int64_t)(blockIdx.x % (j.Npad / 32)) * 32;
     const int64_t k0 = (int64_t)(blockIdx.x / (j.Npad / 32)) * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    if (threadIdx.x < 32 && k0 + threadIdx.x < j.K) {
+        int rz, ry, rx;
+        decode_shift(g, (int)(k0 + threadIdx.x), rz, ry, rx);
+        shifts[threadIdx.x] = make_int3(rz, ry, rx);
+    }
+    __syncthreads();
     const int64_t x = x0 + tx;
     const bool xin = x < g.N;
     const Pos3 px = pos_of(g, xin ? x : 0);
@@ -437,9 +444,8 @@ __global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
         const int64_t k = k0 + kk;
         float e = 0.f;
         if (xin && k < j.K) {
-            int rz, ry, rx;
-            decode_shift(g, (int)k, rz, ry, rx);
-            const float v = j.field[partner(g, px, rz, ry, rx)];
+            const int3 r = shifts[kk];
+            const float v = j.field[partner(g, px, r.x, r.y, r.z)];
             e = tc.identity ? 0.5f * (u + v) : fmaf(tc.c1, sig_pair(tc, u, v), tc.c3);
         }
         uint16_t hi, lo;
@@ -457,11 +463,27 @@ __global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
 }
 
 // G(a, b) = w * gscale * sym(D3 - D3_des) on the level's K x K block; d<G, E^T E>/dE =
-// E (G + G^T), so G is symmetrised (the loss gradient already is symmetric)
-__device__ __forceinline__ float g3_value(const S3Job& j, int64_t a, int64_t b) {
-    const float dab = j.src[a * j.K + b] - (j.sub != nullptr ? j.sub[a * j.K + b] : 0.f);
-    const float dba = j.src[b * j.K + a] - (j.sub != nullptr ? j.sub[b * j.K + a] : 0.f);
-    return j.weight * (j.sc != nullptr ? j.sc->gscale : 1.f) * 0.5f * (dab + dba);
+// E (G + G^T), so G is symmetrised (the loss gradient already is symmetric).  A block holds
+// a 32 x 32 tile; the transposed entries come through shared memory, so both reads are
+// coalesced.  Returns v(a0 + i, b0 + tx) for i = ty, ty + 8, ... in v[4] (0 outside K x K).
+__device__ __forceinline__ float g3_delta(const S3Job& j, int64_t a, int64_t b) {
+    return j.src[a * j.K + b] - (j.sub != nullptr ? j.sub[a * j.K + b] : 0.f);
+}
+
+__device__ __forceinline__ void g3_tile(const S3Job& j, int64_t a0, int64_t b0, float (&v)[4]) {
+    __shared__ float tt[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < 32; i += 8) {
+        const int64_t b = b0 + i, a = a0 + tx;
+        tt[tx][i] = (a < j.K && b < j.K) ? g3_delta(j, b, a) : 0.f;   // tt[a - a0][b - b0] = d(b, a)
+    }
+    __syncthreads();
+    const float sc = j.weight * (j.sc != nullptr ? j.sc->gscale : 1.f);
+    for (int q = 0; q < 4; ++q) {
+        const int i = ty + 8 * q;
+        const int64_t a = a0 + i, b = b0 + tx;
+        v[q] = (a < j.K && b < j.K) ? sc * 0.5f * (g3_delta(j, a, b) + tt[i][tx]) : 0.f;
+    }
 }
 
 // max |v| of a block's values into *out (non-negative floats order like their bit patterns;
@@ -477,12 +499,14 @@ __device__ __forceinline__ void block_absmax(float m, float* out) {
     }
 }
 
+// one 32 x 32 tile of G per block
 __global__ void __launch_bounds__(256) g3_absmax_kernel(S3Job j) {
     if (j.done != nullptr && *j.done) return;
+    const int64_t tiles = (j.K + 31) / 32;
+    float v[4];
+    g3_tile(j, (blockIdx.x / tiles) * 32, (blockIdx.x % tiles) * 32, v);
     float m = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < j.K * j.K;
-         i += (int64_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(g3_value(j, i / j.K, i % j.K)));
+    for (int q = 0; q < 4; ++q) m = fmaxf(m, fabsf(v[q]));
     block_absmax(m, j.amax);
 }
 
@@ -495,17 +519,23 @@ __global__ void __launch_bounds__(256) field_absmax_kernel(S3Job j) {
     block_absmax(m, j.amax + 1);
 }
 
-// G scaled by 2^-eG (max |G| into [1/2, 1)) and split into FP16 hi + lo; zero padding to Kpad
-__global__ void g3_split_kernel(S3Job j) {
+// G scaled by 2^-eG (max |G| into [1/2, 1)) and split into FP16 hi + lo, one 32 x 32 tile of
+// Kpad x Kpad per block (zero padding)
+__global__ void __launch_bounds__(256) g3_split_kernel(S3Job j) {
     if (j.done != nullptr && *j.done) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)j.Kpad * j.Kpad) return;
-    const int64_t a = i / j.Kpad, b = i % j.Kpad;
-    const float v = (a < j.K && b < j.K) ? g3_value(j, a, b) : 0.f;
-    uint16_t hi, lo;
-    split_f16(ldexpf(v, -scale_exp(j.amax)), hi, lo);
-    j.Gh[i] = hi;
-    j.Gl[i] = lo;
+    const int64_t tiles = j.Kpad / 32;
+    const int64_t a0 = (blockIdx.x / tiles) * 32, b0 = (blockIdx.x % tiles) * 32;
+    float v[4];
+    g3_tile(j, a0, b0, v);
+    const int eG = scale_exp(j.amax);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = (a0 + ty + 8 * q) * j.Kpad + b0 + tx;
+        uint16_t hi, lo;
+        split_f16(ldexpf(v[q], -eG), hi, lo);
+        j.Gh[i] = hi;
+        j.Gl[i] = lo;
+    }
 }
 
 // g_y = sum_k c_k [W(k, y) f'(a_y(r_k)) + W(k, y - r_k) f'(a_{y - r_k}(r_k))], c_0 = 1/2 (the two
@@ -523,9 +553,10 @@ __global__ void __launch_bounds__(256) s3_gather_kernel(S3Job j, ThreshConst tc)
     const float my = j.field[y];
     const Pos3 py = pos_of(g, y);
     float acc = 0.f;
+    // the chunk's shifts in canonical order: rx fastest, then ry, then rz (decoded once)
+    int rz, ry, rx;
+    decode_shift(g, (int)kA, rz, ry, rx);
     for (int64_t k = kA; k < kB; ++k) {
-        int rz, ry, rx;
-        decode_shift(g, (int)k, rz, ry, rx);
         const int64_t yp = partner(g, py, rz, ry, rx);      // y + r
         const int64_t ym = partner(g, py, -rz, -ry, -rx);   // y - r
         float d1 = 1.f, d2 = 1.f;
@@ -537,6 +568,13 @@ __global__ void __launch_bounds__(256) s3_gather_kernel(S3Job j, ThreshConst tc)
         }
         acc = fmaf(0.5f * j.W[k * j.Npad + y], d1, acc);
         acc = fmaf(0.5f * j.W[k * j.Npad + ym], d2, acc);
+        if (++rx > g.P[2]) {
+            rx = -g.P[2];
+            if (++ry > g.P[1]) {
+                ry = -g.P[1];
+                ++rz;
+            }
+        }
     }
     j.part[(int64_t)blockIdx.y * g.N + y] = acc;
 }
@@ -641,9 +679,9 @@ void launch_s3_forward(const S3Job& j, const ThreshConst& tc, int* err, cudaStre
 void launch_s3_backward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s) {
     if (j.ens) launch_ensemble(j, tc, s);
     set_flag_kernel<<<1, 1, 0, s>>>(reinterpret_cast<int*>(j.amax), 0);
-    g3_absmax_kernel<<<(unsigned)std::min<int64_t>(ABSMAX_BLOCKS, (j.K * j.K + 255) / 256), 256, 0, s>>>(j);
-    const int64_t nG = j.Kpad * j.Kpad;
-    g3_split_kernel<<<(unsigned)((nG + 255) / 256), 256, 0, s>>>(j);
+    const int64_t tk = (j.K + 31) / 32;
+    g3_absmax_kernel<<<(unsigned)(tk * tk), 256, 0, s>>>(j);
+    g3_split_kernel<<<(unsigned)((j.Kpad / 32) * (j.Kpad / 32)), 256, 0, s>>>(j);
     GemmOperands a{};
     a.Ah = j.Eh; a.Al = j.El; a.Bh = j.Gh; a.Bl = j.Gl;
     a.amaxA = tc.identity ? j.amax + 1 : nullptr;
