@@ -348,7 +348,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
     pl.N1 = pl.g[0].N;
     if (pl.desc_kind == DMCR_DESC_S3) {
         if (pl.g[0].Khalf > 16384) return fail(DMCR_ENOTSUP, "three-point descriptor: at most 16384 shifts");
-        pl.s3Kpad = (pl.g[0].Khalf + 127) / 128 * 128;
+        pl.s3Kpad = (pl.g[0].Khalf + 255) / 256 * 256;   // whole 256-wide tiles of the W GEMM
         for (int l = 0; l < pl.levels; ++l) pl.s3Npad[l] = (pl.g[l].N + 127) / 128 * 128;
     }
     // threshold constants (FP64 on the host, rounded once)

@@ -192,8 +192,8 @@ struct InitSeg {
     double b1t, b2t;
 };
 
-// Three-point descriptor, one (instance, level) (gram.cu).  K = half-window shifts,
-// Kpad and Npad = K and the level's position count rounded up to 128.
+// Three-point descriptor, one (instance, level) (gram.cu).  K = half-window shifts, Kpad =
+// K rounded up to 256, Npad = the level's position count rounded up to 128.
 struct S3Job {
     LevelGeom g;
     const float* field;     // this level's field

@@ -9,14 +9,16 @@
 //                   soft threshold, whose f is bounded, and a power of two bringing max |M|
 //                   into [1/2, 1) for f(x) = x);
 //   tc_gemm_kernel  C = A B^T on the 5th-generation tensor cores: tcgen05.mma kind::f16
-//                   from shared memory, FP32 accumulators in TMEM drained every 512
+//                   from shared memory, FP32 accumulators in TMEM drained every 256-512
 //                   reduction steps into FP32 registers, three products
 //                   hi*hi + hi*lo + lo*hi per k-step (the dropped lo*lo is below 2^-22 of the
-//                   product), operands staged by TMA in three stages (128-byte swizzled
-//                   K-major layout), one thread issues the MMAs and commits them to an
-//                   mbarrier per stage; the epilogue undoes the operands' scales exactly;
-//                   Gram:  S_bar3 = Et Et^T w/N (upper-triangle tiles, mirrored);
-//                   W:     W^T = (2/N) G E^T  as  E G^T with a transposed epilogue;
+//                   product), operands staged by TMA (128-byte swizzled K-major layout), one
+//                   thread issues the MMAs and commits them to an mbarrier per stage; the
+//                   epilogue undoes the operands' scales exactly;
+//                   Gram:  S_bar3 = Et Et^T w/N (upper-triangle 128 x 128 tiles, mirrored,
+//                          three 64 KB stages);
+//                   W:     W^T = (2/N) G E^T  as  E G^T with a transposed epilogue (128 x 256
+//                          tiles, two 96 KB stages);
 //   g3_split_kernel G = w * gscale * (D3 - D3_des) symmetrised (or the upstream gradient),
 //                   scaled by the power of two that brings max |G| (g3_absmax_kernel) into
 //                   [1/2, 1), split like E;
@@ -44,7 +46,7 @@ struct GemmArgs {
     const float* amaxB;
     float* C;
     int64_t ldc;
-    int mode;               // 0 C[m][n], 1 symmetric Gram (upper tiles, mirrored), 2 C[n][m]
+    int mode;               // 1 symmetric Gram (upper tiles, mirrored), 2 C[n][m]
     int Mvalid, Nvalid;
     const int* done;
     int* err;
@@ -68,24 +70,35 @@ struct GemmOperands {
 
 namespace {
 
-constexpr int GM = 128, GN = 128, GK = 64;            // tile: 128 x 128 outputs, 64 reduction steps
-constexpr int TILE_BYTES = GM * GK * 2;                // one FP16 operand tile (128-byte rows), 16 KB
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;            // A hi, A lo, B hi, B lo
-constexpr int GSTAGES = 3;
-constexpr int GEMM_THREADS = 192;                     // warps 0-3 epilogue, 4 TMA, 5 MMA
-constexpr uint32_t TMEM_COLS = 512;                    // 2 buffers x (main + cross) FP32, 128 lanes x 128 columns each
+// Tiles of GM x BN outputs, BN = 128 or 256 (kernel template); GK reduction steps per stage.
+constexpr int GM = 128, GK = 64;
+constexpr int A_TILE = GM * GK * 2;                    // one FP16 A tile (128 rows of 128 bytes), 16 KB
+template <int BN>
+struct GemmShape {
+    static constexpr int B_TILE = BN * GK * 2;                   // one FP16 B tile
+    static constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;  // A hi, A lo, B hi, B lo
+    static constexpr int STAGES = BN == 128 ? 3 : 2;             // 192 KB of stages
+    static constexpr int EPI_WARPS = BN / 32;                    // 128 columns of one lane quadrant each
+    static constexpr int THREADS = 32 * (EPI_WARPS + 2);         // epilogue warps, then TMA, then MMA
+    // 128-wide tiles keep the small cross terms hi*lo + lo*hi in an accumulator of their own
+    // (FLUSH 8 k-blocks: 32 MMAs per accumulator); 256-wide tiles add all three products into
+    // one accumulator (TMEM holds two buffers of 256 columns) and drain twice as often
+    static constexpr bool SPLIT = BN == 128;
+    static constexpr int FLUSH = SPLIT ? 8 : 4;
+    static constexpr uint32_t BUF_COLS = SPLIT ? 2 * BN : BN;     // one buffer: main (+ cross)
+    static constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;          // 512 columns, 128 lanes
+    // instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B F16 (bits 7-9, 10-12 = 0),
+    // both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+    static constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(GM >> 4) << 24);
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+};
 // The tensor core adds into its FP32 accumulator without round-to-nearest: over a long
 // reduction the error is biased toward zero (~4e-8 relative per accumulation measured on
-// GB300).  So TMEM accumulates at most FLUSH k-blocks (FLUSH * 64 reduction steps, 32 MMAs
-// per accumulator) before the partial sums are added, rounded to nearest, into FP32
-// registers; the small cross terms hi*lo + lo*hi accumulate separately from hi*hi.
-constexpr int FLUSH = 8;
+// GB300).  So TMEM accumulates at most FLUSH k-blocks (GemmShape) before the partial sums are
+// added, rounded to nearest, into FP32 registers.
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
-// instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B F16 (bits 7-9, 10-12 = 0),
-// both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
-constexpr uint32_t IDESC_F16 = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(GN >> 3) << 17) |
-                               ((uint32_t)(GM >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -149,11 +162,11 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
            (2ull << 61);
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(IDESC_F16), "r"(acc)
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 
@@ -201,17 +214,28 @@ __device__ __forceinline__ int scale_exp(const float* amax) {
 // ------------------------------------------------------------------------- GEMM
 
 // C = scale 2^(eA + eB) A B^T with A (M x K) and B (N x K) row-major (K contiguous), each given
-// as FP16 hi + lo through four TMA tensor maps (box 64 x 128, 128-byte swizzle).  M, N
-// multiples of 128, K a multiple of 64.  mode 0: C[m][n]; mode 1 (Gram, A = B): only tiles bn >= bm,
-// written to C[m][n] and C[n][m]; mode 2: C[n][m].  Entries with m >= Mvalid or
-// n >= Nvalid are not written.
+// as FP16 hi + lo through four TMA tensor maps (boxes 64 x 128 for A, 64 x BN for B, 128-byte
+// swizzle).  M a multiple of 128, N of BN, K of 64.  Tiles are 128 x BN.  mode 1 (Gram, A = B,
+// square tiles, BN = 128): only tiles bn >= bm, written to C[m][n] and C[n][m]; mode 2:
+// C[n][m].  Entries with m >= Mvalid or n >= Nvalid are not written.
 //
-// Warp roles: warp 4 (one lane) loads the stages with TMA; warp 5 (one lane) issues the MMAs
-// and commits them; warps 0-3 drain the TMEM accumulators every FLUSH k-blocks into FP32
-// registers (TMEM is double-buffered: two periods of main + cross accumulators, 512
-// columns) and write the tile.  Barriers: full[s] (TMA bytes landed), empty[s] (MMAs done
-// reading stage s), tfull[b] (period finished in TMEM buffer b), tempty[b] (buffer b read).
-__global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_constant__ GemmArgs g) {
+// The single issuing thread spends about 400 cycles per stage besides the MMAs (barrier
+// wait, commit, loop): 128 x 256 tiles (twice the MMA work per stage) keep the tensor pipe
+// fed where the grid is large (the W GEMM); the Gram, whose upper triangle holds few tiles,
+// keeps 128 x 128 tiles so that it fills the SMs.
+//
+// Warp roles: warp EPI (one lane) loads the stages with TMA; warp EPI + 1 (one lane) issues
+// the MMAs and commits them; warps 0 .. EPI - 1 drain the TMEM accumulators every FLUSH
+// k-blocks into FP32 registers (warp w reads TMEM lanes 32 (w % 4) .. + 31 and columns
+// 128 (w / 4) .. + 127; TMEM is double-buffered, two periods of BN columns) and write the
+// tile.  Barriers: full[s] (TMA bytes landed), empty[s] (MMAs done reading stage s),
+// tfull[b] (period finished in TMEM buffer b), tempty[b] (buffer b read).
+template <int BN>
+__global__ void __launch_bounds__(GemmShape<BN>::THREADS, 1) tc_gemm_kernel(const __grid_constant__ GemmArgs g) {
+    using S = GemmShape<BN>;
+    constexpr int GN = BN, GSTAGES = S::STAGES, STAGE_BYTES = S::STAGE_BYTES, B_TILE = S::B_TILE;
+    constexpr int EPI_WARPS = S::EPI_WARPS, FLUSH = S::FLUSH;
+    constexpr uint32_t TMEM_COLS = S::TMEM_COLS;
     if (g.done != nullptr && *g.done) return;
     extern __shared__ __align__(1024) uint8_t gsm_raw[];
     // the swizzle atoms need 1024-byte aligned tiles
@@ -222,21 +246,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
     uint64_t* tempty = tfull + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tilesM = g.M / GM;
+    const int tilesM = g.M / GM, tilesN = g.N / GN;
     int bm, bn;
     if (g.mode == 1) {
-        // upper triangle, row by row: tiles (bm, bn >= bm)
-        int64_t t = blockIdx.x;
+        // the upper triangle in square tiles (the launcher takes BN = GM), row by row: (bm, bn >= bm)
+        int t = (int)blockIdx.x;
         bm = 0;
-        while (t >= tilesM - bm) {
-            t -= tilesM - bm;
+        while (t >= tilesN - bm) {
+            t -= tilesN - bm;
             ++bm;
         }
-        bn = bm + (int)t;
+        bn = bm + t;
     } else {
         // B tiles fastest: the CTAs in flight share a few A row blocks and sweep the whole of
         // B (the W GEMM's G, Kpad x Kpad, stays in L2), so A streams from DRAM once
-        const int tilesN = g.N / GN;
         bn = (int)(blockIdx.x % tilesN);
         bm = (int)(blockIdx.x / tilesN);
     }
@@ -247,11 +270,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4 * 32);
+            mbar_init(&tempty[b], EPI_WARPS * 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) tmem_alloc(tslot, TMEM_COLS);
+    if (warp == EPI_WARPS + 1) tmem_alloc(tslot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -260,7 +283,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
     const int nper = (nk + FLUSH - 1) / FLUSH;
     bool ok = true;
 
-    if (warp == 4) {
+    if (warp == EPI_WARPS) {
         // ---- TMA producer
         if (lane == 0) {
             for (int kb = 0; kb < nk; ++kb) {
@@ -270,17 +293,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
                 uint8_t* st = gsm + s * STAGE_BYTES;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
                 const int k0 = kb * GK;
-                tma_load_2d(st + 0 * TILE_BYTES, &g.ta_hi, k0, bm * GM, &full[s]);
-                tma_load_2d(st + 1 * TILE_BYTES, &g.ta_lo, k0, bm * GM, &full[s]);
-                tma_load_2d(st + 2 * TILE_BYTES, &g.tb_hi, k0, bn * GN, &full[s]);
-                tma_load_2d(st + 3 * TILE_BYTES, &g.tb_lo, k0, bn * GN, &full[s]);
+                tma_load_2d(st, &g.ta_hi, k0, bm * GM, &full[s]);
+                tma_load_2d(st + A_TILE, &g.ta_lo, k0, bm * GM, &full[s]);
+                tma_load_2d(st + 2 * A_TILE, &g.tb_hi, k0, bn * GN, &full[s]);
+                tma_load_2d(st + 2 * A_TILE + B_TILE, &g.tb_lo, k0, bn * GN, &full[s]);
             }
             // no copy may still be in flight at exit: the last stages' bytes have landed
             for (int kb = nk > GSTAGES ? nk - GSTAGES : 0; kb < nk; ++kb)
                 mbar_wait(&full[kb % GSTAGES], (kb / GSTAGES) & 1);
         }
         __syncwarp();
-    } else if (warp == 5) {
+    } else if (warp == EPI_WARPS + 1) {
         // ---- MMA issuer
         if (lane == 0) {
             for (int kb = 0; kb < nk; ++kb) {
@@ -292,18 +315,19 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t st = smem_u32(gsm + s * STAGE_BYTES);
-                const uint32_t t_main = tmem + (uint32_t)buf * (2 * GN), t_cross = t_main + GN;
+                const uint32_t t_acc = tmem + (uint32_t)buf * S::BUF_COLS;
+                const uint32_t t_cross = S::SPLIT ? t_acc + GN : t_acc;
 #pragma unroll
                 for (int ks = 0; ks < GK / 16; ++ks) {
                     const uint32_t off = ks * 32;   // 16 FP16 = 32 bytes per k-step
-                    const uint64_t ah = smem_desc_sw128(st + 0 * TILE_BYTES + off);
-                    const uint64_t al = smem_desc_sw128(st + 1 * TILE_BYTES + off);
-                    const uint64_t bh = smem_desc_sw128(st + 2 * TILE_BYTES + off);
-                    const uint64_t bl = smem_desc_sw128(st + 3 * TILE_BYTES + off);
+                    const uint64_t ah = smem_desc_sw128(st + off);
+                    const uint64_t al = smem_desc_sw128(st + A_TILE + off);
+                    const uint64_t bh = smem_desc_sw128(st + 2 * A_TILE + off);
+                    const uint64_t bl = smem_desc_sw128(st + 2 * A_TILE + B_TILE + off);
                     const uint32_t more = (kb % FLUSH != 0) || ks != 0;
-                    mma_f16(t_main, ah, bh, more);
-                    mma_f16(t_cross, ah, bl, more);
-                    mma_f16(t_cross, al, bh, 1);
+                    mma_f16(t_acc, ah, bh, S::IDESC, more);
+                    mma_f16(t_cross, ah, bl, S::IDESC, S::SPLIT ? more : 1u);
+                    mma_f16(t_cross, al, bh, S::IDESC, 1);
                 }
                 mma_commit(&empty[s]);
                 if (kb % FLUSH == FLUSH - 1 || kb == nk - 1) mma_commit(&tfull[buf]);
@@ -311,42 +335,53 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
         }
         __syncwarp();
     } else {
-        // ---- epilogue: warps 0-3 own TMEM lanes 32 w .. 32 w + 31 = tile rows
-        float acc[GN];
+        // ---- epilogue: warp w owns TMEM lanes 32 (w % 4) .. + 31 (tile rows) and the 128
+        // columns from 128 (w / 4)
+        constexpr int EC = 128;
+        const int quad = warp & 3, half = warp >> 2;
+        float acc[EC];
 #pragma unroll
-        for (int c = 0; c < GN; ++c) acc[c] = 0.f;
+        for (int c = 0; c < EC; ++c) acc[c] = 0.f;
         for (int p = 0; p < nper; ++p) {
             const int buf = p & 1;
             // warp-uniform decision: tcgen05.ld below is .sync.aligned
             ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], (p / 2) & 1));
             if (!ok) break;
             tc_fence_after();
-            const uint32_t t_main = tmem + (uint32_t)buf * (2 * GN) + ((uint32_t)(32 * warp) << 16);
+            const uint32_t t_acc =
+                tmem + (uint32_t)buf * S::BUF_COLS + (uint32_t)(EC * half) + ((uint32_t)(32 * quad) << 16);
 #pragma unroll
-            for (int c = 0; c < GN; c += 16) {
-                float vm[16], vc[16];
-                tmem_ld16(t_main + (uint32_t)c, vm);
-                tmem_ld16(t_main + GN + (uint32_t)c, vc);
+            for (int c = 0; c < EC; c += 16) {
+                float v[16];
+                tmem_ld16(t_acc + (uint32_t)c, v);
+                if (S::SPLIT) {
+                    float w[16];
+                    tmem_ld16(t_acc + GN + (uint32_t)c, w);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc[c + j] += vm[j] + vc[j];
+                    for (int j = 0; j < 16; ++j) acc[c + j] += v[j] + w[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[c + j] += v[j];
+                }
             }
             tc_fence_before();
             mbar_arrive(&tempty[buf]);
         }
-        const int m = bm * GM + 32 * warp + lane;
+        const int m = bm * GM + 32 * quad + lane;
         // undo the operands' power-of-two scales together with the output scale (exact)
         const float scale = ldexpf(g.scale, scale_exp(g.amaxA) + scale_exp(g.amaxB));
         if (ok && m < g.Mvalid) {
 #pragma unroll
-            for (int c = 0; c < GN; ++c) {
-                const int n = bn * GN + c;
+            for (int c = 0; c < EC; ++c) {
+                const int n = bn * GN + EC * half + c;
                 if (n >= g.Nvalid) continue;
                 const float x = scale * acc[c];
                 if (g.mode == 2) {
                     g.C[(int64_t)n * g.ldc + m] = x;
                 } else {
+                    // Gram: a diagonal tile holds both halves; the others are mirrored
                     g.C[(int64_t)m * g.ldc + n] = x;
-                    if (g.mode == 1 && bm != bn) g.C[(int64_t)n * g.ldc + m] = x;
+                    if (bm != bn) g.C[(int64_t)n * g.ldc + m] = x;
                 }
             }
         }
@@ -354,7 +389,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
     if (!ok && g.err != nullptr) atomicExch(g.err, 1);
     tc_fence_before();
     __syncthreads();
-    if (warp == 5) tmem_dealloc(tmem, TMEM_COLS);
+    if (warp == EPI_WARPS + 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // ------------------------------------------------------------------------- ensemble
@@ -581,10 +616,11 @@ __global__ void __launch_bounds__(256) s3_gather_kernel(S3Job j, ThreshConst tc)
 
 // ------------------------------------------------------------------------- launchers
 
-size_t gemm_smem_bytes() { return (size_t)GSTAGES * STAGE_BYTES + 1024 + 256; }
+size_t gemm_smem_bytes() { return std::max(GemmShape<128>::SMEM, GemmShape<256>::SMEM); }
 
 void set_gram_attributes() {
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
+    cudaFuncSetAttribute(tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmShape<128>::SMEM);
+    cudaFuncSetAttribute(tc_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmShape<256>::SMEM);
 }
 
 __global__ void set_flag_kernel(int* flag, int v) {
@@ -606,13 +642,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// rows x cols FP16 row-major (row stride ld elements), boxes of 128 rows x 64 columns
-bool make_map(CUtensorMap* m, const uint16_t* base, int64_t rows, int64_t cols, int64_t ld) {
+// rows x cols FP16 row-major (row stride ld elements), boxes of box_rows rows x 64 columns
+bool make_map(CUtensorMap* m, const uint16_t* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (enc == nullptr) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(uint16_t)};
-    const cuuint32_t box[2] = {(cuuint32_t)GK, (cuuint32_t)GM};
+    const cuuint32_t box[2] = {(cuuint32_t)GK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<uint16_t*>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -621,13 +657,16 @@ bool make_map(CUtensorMap* m, const uint16_t* base, int64_t rows, int64_t cols, 
 
 bool gram_ready() { return tensor_map_encoder() != nullptr; }
 
+// BN = 128 for the Gram (mode 1), 256 otherwise
 void launch_tc_gemm(const GemmOperands& o, cudaStream_t s) {
-    const int64_t tm = o.M / GM, tn = o.N / GN;
-    const int64_t blocks = o.mode == 1 ? tm * (tm + 1) / 2 : tm * tn;
+    const int BN = o.mode == 1 ? 128 : 256;
+    const int64_t tm = o.M / GM, tn = o.N / BN;
+    int64_t blocks = tm * tn;
+    if (o.mode == 1) blocks = tm * (tm + 1) / 2;   // square tiles: BN = 128, M = N
     if (blocks <= 0) return;
     GemmArgs a{};
-    const bool ok = make_map(&a.ta_hi, o.Ah, o.M, o.K, o.lda) && make_map(&a.ta_lo, o.Al, o.M, o.K, o.lda) &&
-                    make_map(&a.tb_hi, o.Bh, o.N, o.K, o.ldb) && make_map(&a.tb_lo, o.Bl, o.N, o.K, o.ldb);
+    const bool ok = make_map(&a.ta_hi, o.Ah, o.M, o.K, o.lda, GM) && make_map(&a.ta_lo, o.Al, o.M, o.K, o.lda, GM) &&
+                    make_map(&a.tb_hi, o.Bh, o.N, o.K, o.ldb, BN) && make_map(&a.tb_lo, o.Bl, o.N, o.K, o.ldb, BN);
     if (!ok) {
         // no valid tensor map: never launch TMA on it; report through the error word
         set_flag_kernel<<<1, 1, 0, s>>>(o.err, 2);
@@ -643,7 +682,10 @@ void launch_tc_gemm(const GemmOperands& o, cudaStream_t s) {
     a.Mvalid = o.Mvalid; a.Nvalid = o.Nvalid;
     a.done = o.done;
     a.err = o.err;
-    tc_gemm_kernel<<<(unsigned)blocks, GEMM_THREADS, gemm_smem_bytes(), s>>>(a);
+    if (BN == 128)
+        tc_gemm_kernel<128><<<(unsigned)blocks, GemmShape<128>::THREADS, GemmShape<128>::SMEM, s>>>(a);
+    else
+        tc_gemm_kernel<256><<<(unsigned)blocks, GemmShape<256>::THREADS, GemmShape<256>::SMEM, s>>>(a);
 }
 
 constexpr int ABSMAX_BLOCKS = 512;
