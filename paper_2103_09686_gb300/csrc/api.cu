@@ -658,7 +658,7 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
                         r.partial = it.f.partial;
                         r.desc = x.desc + x.pl->off[l] + blk * g.Khalf;
                         r.done = it.f.done;
-                        r.weight = x.pl->w[l];
+                        r.scale = (float)((double)x.pl->w[l] / (double)g.N);
                         r.blockStart = rb;
                         rb += ceil_div(g.Khalf, RED_K);
                         rv.push_back(r);
@@ -697,21 +697,26 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
     if (flags & F_LOSS) {
         std::vector<PenSeg> pv;
         std::vector<LossSeg> lvv;
+        int maxblk = 0;
         for (const Inst& x : in) {
             double* pen = reinterpret_cast<double*>(x.ws + x.pl->o_pen);
-            pv.push_back({x.lp.bc_on ? x.field : nullptr, x.pl->N1 * x.pl->phases, x.desc, x.target, x.pl->Ktot, pen,
-                          x.use_done ? &x.sc->done : nullptr});
+            const int64_t Nall = x.pl->N1 * x.pl->phases;
+            const int nblk = stats_blocks(x.pl->Ktot, x.lp.bc_on ? Nall : 0);
+            maxblk = std::max(maxblk, nblk);
+            pv.push_back({x.lp.bc_on ? x.field : nullptr, Nall, x.desc, x.target, x.pl->Ktot, pen,
+                          x.use_done ? &x.sc->done : nullptr, nblk});
             LossSeg ls{};
             ls.lp = x.lp;
             ls.desc = x.desc;
             ls.target = x.target;
             ls.pen = pen;
+            ls.nblk = nblk;
             ls.sc = x.sc;
             ls.loss_out = x.loss_out;
             ls.history = x.history;
             lvv.push_back(ls);
         }
-        P.pen = {push(P.tb, pv), (int)pv.size(), (int64_t)pv.size()};
+        P.pen = {push(P.tb, pv), (int)pv.size(), (int64_t)maxblk};
         P.loss = {push(P.tb, lvv), (int)lvv.size(), (int64_t)lvv.size()};
     }
     if (flags & F_BACK) {
@@ -958,7 +963,7 @@ void run(const Prepared& P, cudaStream_t s) {
     if (P.flags & F_LOSS) {
         {
             ProfScope ps("loss_stats", -1, s);
-            launch_penalty(P.at<PenSeg>(P.pen.off), P.pen.nseg, s);
+            launch_penalty(P.at<PenSeg>(P.pen.off), P.pen.nseg, (int)P.pen.blocks, s);
         }
         ProfScope ps("loss", -1, s);
         launch_loss(P.at<LossSeg>(P.loss.off), P.loss.nseg, s);

@@ -98,14 +98,16 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
     return r;
 }
 
-// grid (NPEN_BLOCKS, instances): fixed-grid FP64 partial sums of one loss evaluation --
-// sum (D - D_des)^2 and sum D_des^2 over the descriptor, and sum ex^2 of the box excess over
-// the field (when the penalty is on).  partials[3 b + {0, 1, 2}] for block b.
+// grid (max nblk, instances): FP64 partial sums of one loss evaluation over the instance's
+// own nblk blocks (a fixed grid per problem size) -- sum (D - D_des)^2 and sum D_des^2 over
+// the descriptor, and sum ex^2 of the box excess over the field (when the penalty is on).
+// partials[3 b + {0, 1, 2}] for block b.
 __global__ void stats_kernel(const PenSeg* __restrict__ segs) {
     const PenSeg& sg = segs[blockIdx.y];
     if (sg.done != nullptr && *sg.done) return;
-    __shared__ double sh[256];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if ((int)blockIdx.x >= sg.nblk) return;
+    __shared__ DF sh[32];
+    const int64_t stride = (int64_t)sg.nblk * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // per-thread compensated (Kahan) FP32 sums in a fixed order -- FP64 arithmetic is slow on
     // this part and a thread sums only K / 65536 terms -- then FP64 across the block
@@ -127,19 +129,29 @@ __global__ void stats_kernel(const PenSeg* __restrict__ segs) {
             const float e = box_excess(sg.field[i]);
             kahan(e2, e2c, e * e);
         }
-    const double R2 = block_sum_d((double)r2 - (double)r2c, sh);
-    const double T2 = block_sum_d((double)t2 - (double)t2c, sh);
-    const double E2 = block_sum_d((double)e2 - (double)e2c, sh);
+    // Kahan's (sum, comp) stands for sum - comp
+    const DF R2 = block_sum_df(df_two_sum(r2, -r2c), sh);
+    const DF T2 = block_sum_df(df_two_sum(t2, -t2c), sh);
+    const DF E2 = block_sum_df(df_two_sum(e2, -e2c), sh);
     if (threadIdx.x == 0) {
-        sg.partials[3 * blockIdx.x + 0] = R2;
-        sg.partials[3 * blockIdx.x + 1] = T2;
-        sg.partials[3 * blockIdx.x + 2] = E2;
+        float2* part = reinterpret_cast<float2*>(sg.partials);
+        part[3 * blockIdx.x + 0] = make_float2(R2.hi, R2.lo);
+        part[3 * blockIdx.x + 1] = make_float2(T2.hi, T2.lo);
+        part[3 * blockIdx.x + 2] = make_float2(E2.hi, E2.lo);
     }
 }
 
-void launch_penalty(const PenSeg* segs, int nseg, cudaStream_t s) {
+void launch_penalty(const PenSeg* segs, int nseg, int maxblk, cudaStream_t s) {
     if (nseg <= 0) return;
-    stats_kernel<<<dim3(NPEN_BLOCKS, nseg), 256, 0, s>>>(segs);
+    stats_kernel<<<dim3(maxblk, nseg), 256, 0, s>>>(segs);
+}
+
+// blocks of the loss statistics: about 2048 terms per block, 256 .. NPEN_BLOCKS, a power of two
+int stats_blocks(int64_t K, int64_t N) {
+    const int64_t work = K > N ? K : N;
+    int b = 256;
+    while (b < NPEN_BLOCKS && (int64_t)b * 2048 < work) b *= 2;
+    return b;
 }
 
 // Corrected two-point descriptor, forward: map every block in place (entry 0 is read, never
@@ -187,12 +199,19 @@ __global__ void __launch_bounds__(NPEN_BLOCKS) loss_kernel(const LossSeg* __rest
     float* loss_out = sg.loss_out;
     float* history = sg.history;
     if (lp.recon && sc->done) return;
-    __shared__ double sh[NPEN_BLOCKS];
+    __shared__ DF sh[32];
+    // the instance's nblk double-float partials (the remaining threads add zeros)
     const int b = threadIdx.x;
-    const double E2 = block_sum_d(pen[3 * b + 0], sh);
-    const double T2 = block_sum_d(pen[3 * b + 1], sh);
-    const double ex2 = block_sum_d(pen[3 * b + 2], sh);
+    const float2* part = reinterpret_cast<const float2*>(pen);
+    const DF zero{0.f, 0.f};
+    auto get = [&](int q) { return b < sg.nblk ? DF{part[3 * b + q].x, part[3 * b + q].y} : zero; };
+    const DF e2s = block_sum_df(get(0), sh);
+    const DF t2s = block_sum_df(get(1), sh);
+    const DF x2s = block_sum_df(get(2), sh);
     if (threadIdx.x != 0) return;
+    const double E2 = (double)e2s.hi + (double)e2s.lo;
+    const double T2 = (double)t2s.hi + (double)t2s.lo;
+    const double ex2 = (double)x2s.hi + (double)x2s.lo;
     const double N = (double)lp.N;
     const double lam0 = lp.bc_on ? (double)lp.lambda0 : 0.0;
     const double E = sqrt(E2);

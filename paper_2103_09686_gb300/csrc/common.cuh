@@ -11,11 +11,50 @@ constexpr int FWD_THREADS = 128;
 constexpr int ADJ_THREADS = 128;   // 32 row pairs (lane, lane + 32) x 4 strips of 8 positions
 constexpr int ADJ_ROWS = 64;       // adjoint tile rows
 constexpr int GBLOCK = 48;         // coefficient floats per block of 8 shifts (packed pairs)
-constexpr int S3_SHIFTS = 64;      // three-point gradient gather: shifts per partial sum
+constexpr int S3_SHIFTS = 32;      // three-point gradient gather: shifts per partial sum
 
 // offset of C_m inside a coefficient block: (C_m, C_m, C_m+1, C_m+1) after the 8 (A, A, B, B)
 __host__ __device__ inline int gblock_c(int m) { return 4 * T + 2 * m; }
-constexpr int NPEN_BLOCKS = 256;   // fixed grid of the penalty reduction (deterministic)
+constexpr int NPEN_BLOCKS = 1024;  // most blocks of the loss statistics of one instance
+
+// Double-float sums: an FP32 pair hi + lo carries about 48 significant bits.  FP64
+// arithmetic is slow on this part, and the reductions below sit on the critical path of
+// every iteration, so they add double-floats in fixed orders instead.
+struct DF {
+    float hi, lo;
+};
+
+// a + b exactly as hi + lo (Knuth's two-sum; no ordering of |a|, |b| needed); commutative
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const DF s = df_two_sum(a.hi, b.hi);
+    const float lo = s.lo + (a.lo + b.lo);
+    const float hi = s.hi + lo;
+    return {hi, lo - (hi - s.hi)};
+}
+
+// fixed-order sum over the block (blockDim.x a multiple of 32, <= 1024): xor butterflies in
+// each warp, then over the warp results in warp 0; the result is valid in thread 0.  sh holds
+// 32 entries.
+__device__ __forceinline__ DF block_sum_df(DF v, DF* sh) {
+    for (int o = 16; o > 0; o >>= 1)
+        v = df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();   // sh may still be read by a previous call
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? sh[lane] : DF{0.f, 0.f};
+        for (int o = 16; o > 0; o >>= 1)
+            v = df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+    }
+    return v;
+}
 constexpr int MAX_DYN_SMEM = 200 * 1024;   // dynamic shared memory limit of the correlation kernels
 constexpr int MAX_PHASES = 8;      // phase fields of one problem (their ordered pairs each get a block)
 
@@ -116,7 +155,7 @@ struct RedSeg {
     const float* partial;
     float* desc;
     const int* done;
-    float weight;
+    float scale;             // w_l / N_l
     int64_t blockStart;
 };
 struct AdjSeg {
@@ -169,14 +208,16 @@ struct PenSeg {
     const float* desc;
     const float* target;
     int64_t K;
-    double* partials;        // 3 x NPEN_BLOCKS
+    double* partials;        // 3 x nblk
     const int* done;
+    int nblk;                // blocks of this instance: a function of its own sizes only
 };
 struct LossSeg {
     LossParams lp;
     const float* desc;
     const float* target;
     const double* pen;
+    int nblk;
     Scalars* sc;
     float* loss_out;
     float* history;
@@ -240,7 +281,8 @@ void launch_prolongate(int ndim, const int64_t nc[3], const float* coarse, float
 void launch_corr_fwd(const FwdSeg* segs, int nseg, int64_t blocks, size_t smem, const ThreshConst& tc,
                      cudaStream_t s);
 void launch_fwd_reduce(const RedSeg* segs, int nseg, int64_t blocks, cudaStream_t s);
-void launch_penalty(const PenSeg* segs, int nseg, cudaStream_t s);
+void launch_penalty(const PenSeg* segs, int nseg, int maxblk, cudaStream_t s);
+int stats_blocks(int64_t K, int64_t N);
 void launch_loss(const LossSeg* segs, int nseg, cudaStream_t s);
 void launch_gcoef(const GSeg* segs, int nseg, int64_t blocks, const ThreshConst& tc, cudaStream_t s);
 void launch_tilde_map(const TildeSeg* segs, int nseg, int64_t blocks, cudaStream_t s);

@@ -484,15 +484,15 @@ corr_fwd_kernel(const FwdSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     }
 }
 
-// Fixed-order FP64 sum over tiles, scaled by w_l / N_l.  A block owns 32 consecutive
-// shifts (one per lane, coalesced rows); warp w sums the tiles t = w (mod 8) in order and
-// the 8 warp sums are combined in a fixed order.
+// Fixed-order sum over tiles, scaled by w_l / N_l.  A block owns 32 consecutive shifts (one
+// per lane, coalesced rows); warp w sums the tiles t = w (mod 8) in order (Kahan, FP32) and
+// the 8 warp sums are combined in a fixed order as double-floats.
 __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedSeg* __restrict__ segs, int nseg) {
     const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
     const RedSeg& sg = segs[si];
     if (sg.done != nullptr && *sg.done) return;
     const int64_t Khalf = sg.g.Khalf, tiles = sg.g.fwdTiles;
-    __shared__ double sh[8][RED_K];
+    __shared__ DF sh[8][RED_K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k = ((int64_t)blockIdx.x - sg.blockStart) * RED_K + lane;
     // compensated (Kahan) FP32 sum over this warp's tiles, then an FP64 sum of the 8 warps
@@ -504,12 +504,12 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedSeg* __restric
             comp = (u - sum) - y;
             sum = u;
         }
-    sh[warp][lane] = (double)sum - (double)comp;
+    sh[warp][lane] = df_two_sum(sum, -comp);
     __syncthreads();
     if (warp == 0 && k < Khalf) {
-        double tot = 0.0;
-        for (int w = 0; w < 8; ++w) tot += sh[w][lane];
-        sg.desc[k] = (float)((double)sg.weight * tot / (double)sg.g.N);
+        DF tot = sh[0][lane];
+        for (int w = 1; w < 8; ++w) tot = df_add(tot, sh[w][lane]);
+        sg.desc[k] = (tot.hi + tot.lo) * sg.scale;
     }
 }
 

@@ -453,17 +453,20 @@ __device__ __forceinline__ float sig_pair(const ThreshConst& tc, float u, float 
     return s;
 }
 
-// one block: 32 positions x 32 shifts, written to E^T (coalesced over positions) and E
-// (coalesced over shifts) through a shared transpose; padding entries are 0
+// one block: 64 positions x 32 shifts.  Thread (tx, ty) owns positions x0 + 2 tx and
+// x0 + 2 tx + 1 and shifts k0 + ty + 8 i (i = 0..3).  E^T rows (shift-major) are written as
+// pairs of positions, one 32-bit word per thread (128-byte lines per warp); E rows
+// (position-major) go through a shared transpose and are written as pairs of shifts.
+// Padding entries are 0.
 __global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
     if (j.done != nullptr && *j.done) return;
-    __shared__ uint16_t th[32][34], tl[32][34];
+    __shared__ uint16_t th[64][34], tl[64][34];
     __shared__ int3 shifts[32];
     const LevelGeom& g = j.g;
     // f(x) = x: e is bounded by max |M|, scaled into [-1, 1); the soft f is bounded by ~1.03
     const float sE = ldexpf(1.f, -(tc.identity ? scale_exp(j.amax + 1) : 0));
-    const int64_t x0 = (int64_t)(blockIdx.x % (j.Npad / 32)) * 32;
-    const int64_t k0 = (int64_t)(blockIdx.x / (j.Npad / 32)) * 32;
+    const int64_t x0 = (int64_t)(blockIdx.x % (j.Npad / 64)) * 64;
+    const int64_t k0 = (int64_t)(blockIdx.x / (j.Npad / 64)) * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     if (threadIdx.x < 32 && k0 + threadIdx.x < j.K) {
         int rz, ry, rx;
@@ -471,29 +474,46 @@ __global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
         shifts[threadIdx.x] = make_int3(rz, ry, rx);
     }
     __syncthreads();
-    const int64_t x = x0 + tx;
-    const bool xin = x < g.N;
-    const Pos3 px = pos_of(g, xin ? x : 0);
-    const float u = xin ? j.field[x] : 0.f;
+    const int64_t xa = x0 + 2 * tx;
+    const bool ina = xa < g.N, inb = xa + 1 < g.N;
+    const Pos3 pa = pos_of(g, ina ? xa : 0), pb = pos_of(g, inb ? xa + 1 : 0);
+    const float ua = ina ? j.field[xa] : 0.f, ub = inb ? j.field[xa + 1] : 0.f;
+    uint32_t* Eth = reinterpret_cast<uint32_t*>(j.Eth);
+    uint32_t* Etl = reinterpret_cast<uint32_t*>(j.Etl);
     for (int kk = ty; kk < 32; kk += 8) {
         const int64_t k = k0 + kk;
-        float e = 0.f;
-        if (xin && k < j.K) {
+        float ea = 0.f, eb = 0.f;
+        if (k < j.K) {
             const int3 r = shifts[kk];
-            const float v = j.field[partner(g, px, r.x, r.y, r.z)];
-            e = tc.identity ? 0.5f * (u + v) : fmaf(tc.c1, sig_pair(tc, u, v), tc.c3);
+            if (ina) {
+                const float v = j.field[partner(g, pa, r.x, r.y, r.z)];
+                ea = tc.identity ? 0.5f * (ua + v) : fmaf(tc.c1, sig_pair(tc, ua, v), tc.c3);
+            }
+            if (inb) {
+                const float v = j.field[partner(g, pb, r.x, r.y, r.z)];
+                eb = tc.identity ? 0.5f * (ub + v) : fmaf(tc.c1, sig_pair(tc, ub, v), tc.c3);
+            }
         }
-        uint16_t hi, lo;
-        split_f16(e * sE, hi, lo);
-        j.Eth[k * j.Npad + x] = hi;
-        j.Etl[k * j.Npad + x] = lo;
-        th[kk][tx] = hi;
-        tl[kk][tx] = lo;
+        uint16_t ha, la, hb, lb;
+        split_f16(ea * sE, ha, la);
+        split_f16(eb * sE, hb, lb);
+        // the lower address holds the lower 16 bits (little endian)
+        Eth[(k * j.Npad + xa) / 2] = (uint32_t)ha | ((uint32_t)hb << 16);
+        Etl[(k * j.Npad + xa) / 2] = (uint32_t)la | ((uint32_t)lb << 16);
+        th[2 * tx][kk] = ha;
+        th[2 * tx + 1][kk] = hb;
+        tl[2 * tx][kk] = la;
+        tl[2 * tx + 1][kk] = lb;
     }
     __syncthreads();
-    for (int xx = ty; xx < 32; xx += 8) {
-        j.Eh[(x0 + xx) * j.Kpad + k0 + tx] = th[tx][xx];
-        j.El[(x0 + xx) * j.Kpad + k0 + tx] = tl[tx][xx];
+    // E rows: 64 positions x 16 words of shift pairs
+    uint32_t* Eh = reinterpret_cast<uint32_t*>(j.Eh);
+    uint32_t* El = reinterpret_cast<uint32_t*>(j.El);
+    const int w = threadIdx.x & 15;
+    for (int pp = threadIdx.x >> 4; pp < 64; pp += 16) {
+        const int64_t o = ((x0 + pp) * j.Kpad + k0) / 2 + w;
+        Eh[o] = (uint32_t)th[pp][2 * w] | ((uint32_t)th[pp][2 * w + 1] << 16);
+        El[o] = (uint32_t)tl[pp][2 * w] | ((uint32_t)tl[pp][2 * w + 1] << 16);
     }
 }
 
@@ -697,7 +717,7 @@ void launch_ensemble(const S3Job& j, const ThreshConst& tc, cudaStream_t s) {
         const int64_t blocks = std::min<int64_t>(ABSMAX_BLOCKS, (j.g.N + 255) / 256);
         field_absmax_kernel<<<(unsigned)blocks, 256, 0, s>>>(j);
     }
-    ens_kernel<<<(unsigned)((j.Npad / 32) * (j.Kpad / 32)), 256, 0, s>>>(j, tc);
+    ens_kernel<<<(unsigned)((j.Npad / 64) * (j.Kpad / 32)), 256, 0, s>>>(j, tc);
 }
 
 void launch_s3_forward(const S3Job& j, const ThreshConst& tc, int* err, cudaStream_t s) {
