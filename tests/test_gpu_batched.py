@@ -128,3 +128,32 @@ def test_nan_poisoned_instance_is_isolated(cuda_lib):
     with pytest.raises(dm.DmcrError) as e:
         dm.dmcr_reconstruct(params[1], opts, d_des[1], f, torch.zeros_like(f), torch.zeros_like(f))
     assert e.value.status == 4
+
+
+def test_batched_mix_of_descriptor_kinds_and_phases_equals_single_calls(cuda_lib):
+    # one batch holding two-point, three-point, corrected and three-phase instances
+    dm = cuda_lib
+    specs = [dict(shape=(48, 40), window=(5, 4), levels=2),
+             dict(shape=(32, 32), window=(6, 6), descriptor=dm.DMCR_DESC_S3),
+             dict(shape=(40, 48), window=(4, 7), levels=2, descriptor=dm.DMCR_DESC_S2_TILDE),
+             dict(shape=(64, 48), window=(7, 5), levels=2, phases=3),
+             dict(shape=(16, 16, 16), window=(2, 2, 2), phases=2)]
+    params = [dm.Params(**s) for s in specs]
+    fields, targets = [], []
+    for i, p in enumerate(params):
+        shape = tuple(p.shape) if p.phases == 1 else (p.phases,) + tuple(p.shape)
+        fields.append(_dev(np.random.default_rng(70 + i).uniform(-0.2, 1.2, shape)))
+        targets.append(_dev((np.random.default_rng(80 + i).random(shape) < 0.35).astype(np.float32)))
+    descs = [torch.empty(dm.dmcr_descriptor_length(p), device="cuda") for p in params]
+    dm.dmcr_descriptor_batched(params, fields, descs)
+    for p, f, d in zip(params, fields, descs):
+        assert torch.equal(d, dm.descriptor(f, p))
+    d_des = [dm.descriptor(t, p) for p, t in zip(params, targets)]
+    n = len(params)
+    loss = torch.empty(n * 6, device="cuda")
+    grads = [torch.empty_like(f) for f in fields]
+    dm.dmcr_loss_grad_batched(params, dm.LossOpts(), fields, d_des, loss, grads)
+    for i in range(n):
+        l1, g1 = dm.loss_grad(fields[i], d_des[i], params[i])
+        assert torch.equal(loss[6 * i:6 * i + 6], l1), i
+        assert torch.equal(grads[i], g1), i
