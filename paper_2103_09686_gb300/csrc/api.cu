@@ -156,14 +156,14 @@ bool fft_size_ok(int64_t n) {
 }
 
 // Identity threshold, AUTO path: the FFT when its estimated cost is lower.  Both costs are
-// fitted to GB300 measurements of descriptor + gradient on 64^3 and 128^3 (P = 1..24):
-// the FFT path is ~1.15 ns per grid point + 0.17 ms; the direct kernels ~0.163 ps per
-// voxel-shift + 0.14 ns per point + 0.13 ms.  Measured crossovers: P = 10 (64^3), P = 8
-// (128^3, where the two paths tie).
+// fitted (relative error) to GB300 measurements of descriptor + gradient on 64^3 and 128^3
+// (P = 1..24): the FFT path is ~1.15 ns per grid point + 0.18 ms; the direct kernels
+// ~0.149 ps per voxel-shift + 0.14 ns per point + 0.13 ms.  Measured crossovers: P = 10 on
+// both grids (at P = 8 the direct path is ahead by 13% on 64^3 and 9% on 128^3).
 bool fft_cheaper(const LevelGeom& g) {
     const double kfull = (double)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * (2 * g.P[2] + 1);
-    const double t_direct = (double)g.N * kfull * 1.63e-13 + (double)g.N * 1.4e-10 + 1.27e-4;
-    const double t_fft = (double)g.N * 1.15e-9 + 1.72e-4;
+    const double t_direct = (double)g.N * kfull * 1.49e-13 + (double)g.N * 1.35e-10 + 1.31e-4;
+    const double t_fft = (double)g.N * 1.148e-9 + 1.77e-4;
     return t_fft < t_direct;
 }
 
