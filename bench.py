@@ -39,16 +39,14 @@ MUFU_RCP_PER_CLK_PER_SM = 16      # MUFU.RCP throughput per SM per clock (measur
 # soft-threshold formulation:
 #   forward: d = 1 + E'E (1), product d_a d_b of two pairs sharing a reciprocal (1/2),
 #            u = s + c3/c1 (1), acc += u^2 (1); one reciprocal per two pairs;
-#   adjoint: d (1), Horner G h(s) (3); 5 of every 8 positions share a reciprocal between two
-#            pairs (product 1/2, s 1), 3 of 8 take one reciprocal per pair.
-LANE_OPS_PER_PAIR = {"corr_fwd": 3.5, "corr_adj": 4.0 + 5.0 / 8.0 * 1.5}
-RCP_PER_PAIR = {"corr_fwd": 0.5, "corr_adj": 5.0 / 8.0 * 0.5 + 3.0 / 8.0}
+#   adjoint: d (1), Horner G h(s) (3); 4 of every 8 positions share a reciprocal between two
+#            pairs (product 1/2, s 1), 4 of 8 take one reciprocal per pair.
+LANE_OPS_PER_PAIR = {"corr_fwd": 3.5, "corr_adj": 4.0 + 4.0 / 8.0 * 1.5}
+RCP_PER_PAIR = {"corr_fwd": 0.5, "corr_adj": 4.0 / 8.0 * 0.5 + 4.0 / 8.0}
 # DRAM bytes (read + write) per launch of the current kernels on the 512^2, +-64, 3-level
 # workload, from the ncu full-set capture summarised in profiles/corr_kernels_grf512_w64_L3.md
 # (None whenever the kernels changed since the last capture).
-NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2706944 + 21760, ("grf512", "corr_fwd"): 1452288 + 2560,
-                     # profiles/launches_mp3_512_w64_L3.md
-                     ("mp3_512", "corr_adj"): 16637440 + 259935488, ("mp3_512", "corr_fwd"): 4471808 + 44815616}
+NCU_TRAFFIC_BYTES = {}
 
 WORKLOADS = {
     "grf512": dict(shape=(512, 512), window=(64, 64), levels=3,
