@@ -46,7 +46,9 @@ RCP_PER_PAIR = {"corr_fwd": 0.5, "corr_adj": 4.0 / 8.0 * 0.5 + 4.0 / 8.0}
 # DRAM bytes (read + write) per launch of the current kernels on the 512^2, +-64, 3-level
 # workload, from the ncu full-set capture summarised in profiles/corr_kernels_grf512_w64_L3.md
 # (None whenever the kernels changed since the last capture).
-NCU_TRAFFIC_BYTES = {}
+NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2707968 + 28416, ("grf512", "corr_fwd"): 1452032 + 768,
+                     # profiles/launches_mp3_512_w64_L3.md
+                     ("mp3_512", "corr_adj"): 16447744 + 259444224, ("mp3_512", "corr_fwd"): 4369152 + 42389504}
 
 WORKLOADS = {
     "grf512": dict(shape=(512, 512), window=(64, 64), levels=3,
