@@ -480,7 +480,9 @@ __global__ void __launch_bounds__(256) ens_kernel(S3Job j, ThreshConst tc) {
     const float ua = ina ? j.field[xa] : 0.f, ub = inb ? j.field[xa + 1] : 0.f;
     uint32_t* Eth = reinterpret_cast<uint32_t*>(j.Eth);
     uint32_t* Etl = reinterpret_cast<uint32_t*>(j.Etl);
-    for (int kk = ty; kk < 32; kk += 8) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int kk = ty + 8 * i;
         const int64_t k = k0 + kk;
         float ea = 0.f, eb = 0.f;
         if (k < j.K) {
@@ -608,27 +610,62 @@ __global__ void __launch_bounds__(256) s3_gather_kernel(S3Job j, ThreshConst tc)
     const float my = j.field[y];
     const Pos3 py = pos_of(g, y);
     float acc = 0.f;
-    // the chunk's shifts in canonical order: rx fastest, then ry, then rz (decoded once)
+    // the chunk's shifts in canonical order: rx fastest, then ry, then rz (decoded once); the
+    // partner indices y + r and y - r are stepped along rx and rebuilt when (rz, ry) changes;
+    // four shifts per step, their loads issued together
     int rz, ry, rx;
     decode_shift(g, (int)kA, rz, ry, rx);
-    for (int64_t k = kA; k < kB; ++k) {
-        const int64_t yp = partner(g, py, rz, ry, rx);      // y + r
-        const int64_t ym = partner(g, py, -rz, -ry, -rx);   // y - r
-        float d1 = 1.f, d2 = 1.f;
-        if (!tc.identity) {
-            const float s1 = sig_pair(tc, my, j.field[yp]);
-            const float s2 = sig_pair(tc, j.field[ym], my);
-            d1 = c1a * s1 * (1.f - s1);
-            d2 = c1a * s2 * (1.f - s2);
-        }
-        acc = fmaf(0.5f * j.W[k * j.Npad + y], d1, acc);
-        acc = fmaf(0.5f * j.W[k * j.Npad + ym], d2, acc);
-        if (++rx > g.P[2]) {
-            rx = -g.P[2];
-            if (++ry > g.P[1]) {
-                ry = -g.P[1];
-                ++rz;
+    const float* __restrict__ field = j.field;
+    const float* __restrict__ W = j.W;
+    const int n0 = (int)g.n[0], n1 = (int)g.n[1], n2 = (int)g.n[2];
+    int64_t rowp = 0, rowm = 0;
+    int cp = 0, cm = 0;
+    auto rows = [&]() {
+        rowp = ((int64_t)wrap_add(py.z, rz, n0) * n1 + wrap_add(py.y, ry, n1)) * n2;
+        rowm = ((int64_t)wrap_add(py.z, -rz, n0) * n1 + wrap_add(py.y, -ry, n1)) * n2;
+    };
+    rows();
+    cp = wrap_add(py.c, rx, n2);
+    cm = wrap_add(py.c, -rx, n2);
+    constexpr int U = 4;
+    for (int64_t k0 = kA; k0 < kB; k0 += U) {
+        int64_t ym[U];
+        float vp[U], vm[U], w1[U], w2[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool in = k0 + u < kB;
+            const int64_t k = in ? k0 + u : kA;
+            const int64_t yp = rowp + cp;                       // y + r
+            ym[u] = rowm + cm;                                  // y - r
+            vp[u] = field[yp];
+            vm[u] = field[ym[u]];
+            w1[u] = in ? W[k * j.Npad + y] : 0.f;
+            w2[u] = in ? W[k * j.Npad + ym[u]] : 0.f;
+            if (++rx > g.P[2]) {
+                rx = -g.P[2];
+                if (++ry > g.P[1]) {
+                    ry = -g.P[1];
+                    ++rz;
+                }
+                rows();
+                cp = wrap_add(py.c, rx, n2);
+                cm = wrap_add(py.c, -rx, n2);
+            } else {
+                cp = cp + 1 == n2 ? 0 : cp + 1;
+                cm = cm == 0 ? n2 - 1 : cm - 1;
             }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float d1 = 1.f, d2 = 1.f;
+            if (!tc.identity) {
+                const float s1 = sig_pair(tc, my, vp[u]);
+                const float s2 = sig_pair(tc, vm[u], my);
+                d1 = c1a * s1 * (1.f - s1);
+                d2 = c1a * s2 * (1.f - s2);
+            }
+            acc = fmaf(0.5f * w1[u], d1, acc);
+            acc = fmaf(0.5f * w2[u], d2, acc);
         }
     }
     j.part[(int64_t)blockIdx.y * g.N + y] = acc;
