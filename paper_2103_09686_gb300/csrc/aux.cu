@@ -278,7 +278,18 @@ __global__ void final_kernel(const FinalSeg* __restrict__ segs, int nseg) {
         const int64_t li = (lz * a.nl[l][1] + (y >> l)) * a.nl[l][2] + (x >> l);
         float s = 0.f;
         const float* p = a.parts[l] + li;
-        for (int c = 0; c < a.nChunks[l]; ++c) s += p[(int64_t)c * a.Nl[l]];
+        // the chunks in order, their loads issued eight at a time
+        const int nc = a.nChunks[l];
+        const int64_t stride = a.Nl[l];
+        int c = 0;
+        for (; c + 8 <= nc; c += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = p[(int64_t)(c + u) * stride];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+        for (; c < nc; ++c) s += p[(int64_t)c * stride];
         g = fmaf(scale, s, g);
         scale *= step;
     }

@@ -534,13 +534,24 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedSeg* __restric
     const int64_t k = ((int64_t)blockIdx.x - sg.blockStart) * RED_K + lane;
     // compensated (Kahan) FP32 sum over this warp's tiles, then an FP64 sum of the 8 warps
     float sum = 0.f, comp = 0.f;
-    if (k < Khalf)
-        for (int64_t t = warp; t < tiles; t += 8) {
-            const float y = sg.partial[t * Khalf + k] - comp;
-            const float u = sum + y;
-            comp = (u - sum) - y;
-            sum = u;
+    auto kahan = [&](float v) {
+        const float y = v - comp;
+        const float u = sum + y;
+        comp = (u - sum) - y;
+        sum = u;
+    };
+    if (k < Khalf) {
+        // this warp's tiles in order, their loads issued four at a time
+        int64_t t = warp;
+        for (; t + 24 < tiles; t += 32) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = sg.partial[(t + 8 * u) * Khalf + k];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) kahan(v[u]);
         }
+        for (; t < tiles; t += 8) kahan(sg.partial[t * Khalf + k]);
+    }
     sh[warp][lane] = df_two_sum(sum, -comp);
     __syncthreads();
     if (warp == 0 && k < Khalf) {
