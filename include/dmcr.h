@@ -163,7 +163,11 @@ dmcr_status dmcr_workspace_size(const dmcr_params* p, size_t* bytes);
  * dmcr_descriptor -- the multigrid descriptor D of `field` (Sec. 3.2, Sec. 3.3 Eq. mg).
  *   field: N floats (device, read only).  desc: dmcr_descriptor_length floats (device,
  *   written).  Also used to characterise a target: D_des = dmcr_descriptor(target).
- *   Errors: DMCR_EINVAL (params), DMCR_ENOMEM (ws_bytes too small), DMCR_ECUDA.
+ *   Errors: DMCR_EINVAL (params), DMCR_ENOMEM (ws_bytes too small), DMCR_ENOTSUP (a
+ *   combination of descriptor, path and phases that is not provided, see above),
+ *   DMCR_ECUDA.  The call is asynchronous: a bounded tensor-core wait of the three-point
+ *   descriptor that gives up only marks the workspace, and the synchronous
+ *   dmcr_reconstruct reports it as DMCR_ETIMEOUT.
  */
 dmcr_status dmcr_descriptor(const dmcr_params* p, const float* field, float* desc,
                             void* ws, size_t ws_bytes, void* stream);
