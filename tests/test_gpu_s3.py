@@ -140,3 +140,20 @@ def test_s3_vjp_of_tiny_and_large_upstream_gradients(cuda_lib, gscale):
     g = dm.descriptor_vjp(_dev(M), _dev(G), p).cpu().numpy().astype(np.float64)
     g_ref = oracle.s3_level_vjp(M, _op(p), G.reshape(K, K))
     assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) < 1e-5
+
+
+def test_s3_full_size_paper_configuration_64_p31(cuda_lib):
+    # the configuration the three-point bench times: 64^2, P = 31 (K = 1985, padded to 2048),
+    # checked entry by entry against the oracle, with the gradient of a random upstream
+    dm = cuda_lib
+    n, P = 64, 31
+    p = dm.Params(shape=(n, n), window=(P, P), descriptor=dm.DMCR_DESC_S3)
+    M = _field((n, n), 17, "relaxed")
+    got = dm.descriptor(_dev(M), p).cpu().numpy().astype(np.float64)
+    want = oracle.s3_descriptor(M, _op(p))
+    np.testing.assert_allclose(got, want, rtol=1e-5, atol=1e-6 * np.max(np.abs(want)))
+    K = oracle.half_window(2, (P, P)).shape[0]
+    G = np.random.default_rng(18).standard_normal(K * K)
+    g = dm.descriptor_vjp(_dev(M), _dev(G), p).cpu().numpy().astype(np.float64)
+    g_ref = oracle.s3_level_vjp(M, _op(p), G.reshape(K, K))
+    assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) < 1e-5
