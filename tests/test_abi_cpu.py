@@ -72,3 +72,32 @@ def test_null_workspace_is_rejected_before_any_launch(lib):
     assert st == _lib.DMCR_EINVAL
     st = lib.dmcr_descriptor(ctypes.byref(p), 1 << 20, 1 << 21, 1 << 22, 16, None)
     assert st == _lib.DMCR_ENOMEM
+
+
+def test_lengths_of_the_other_descriptors(lib):
+    import paper_2103_09686_gb300 as dm
+    # three-point: K_half^2 per level; corrected two-point: K_half; P phases: P^2 K_half
+    assert dm.dmcr_descriptor_length(dm.Params((64, 64), (31, 31), descriptor=dm.DMCR_DESC_S3)) == 1985 ** 2
+    assert dm.dmcr_descriptor_length(dm.Params((64, 64), (4, 4), levels=2, descriptor=dm.DMCR_DESC_S3)) == 2 * 41 ** 2
+    assert dm.dmcr_descriptor_length(dm.Params((64, 64), (16, 16), descriptor=dm.DMCR_DESC_S2_TILDE)) == 545
+    assert dm.dmcr_descriptor_length(dm.Params((512, 512), (64, 64), levels=3, phases=3)) == 3 * 9 * 8321
+    assert dm.dmcr_descriptor_length(dm.Params((64, 64), (16, 16), phases=1)) == 545
+    one = dm.dmcr_workspace_size(dm.Params((256, 256), (16, 16), levels=2))
+    three = dm.dmcr_workspace_size(dm.Params((256, 256), (16, 16), levels=2, phases=3))
+    assert three > 3 * one
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(shape=(64, 64), window=(4, 4), descriptor=7), 1),                       # unknown descriptor
+    (dict(shape=(64, 64), window=(4, 4), descriptor=1, path=2), 6),               # S3 has no FFT path
+    (dict(shape=(64, 64), window=(4, 4), phases=9), 1),                           # at most 8 phases
+    (dict(shape=(64, 64), window=(4, 4), phases=-1), 1),
+    (dict(shape=(64, 64), window=(4, 4), phases=2, descriptor=1), 6),             # phases: S2 only
+    (dict(shape=(64, 64), window=(4, 4), phases=2, descriptor=2), 6),
+    (dict(shape=(64, 64), window=(4, 4), phases=2, path=2, threshold=1), 6),      # phases: direct only
+])
+def test_validation_of_descriptor_kinds_and_phases(lib, kw, status):
+    import paper_2103_09686_gb300 as dm
+    with pytest.raises(dm.DmcrError) as e:
+        dm.dmcr_descriptor_length(dm.Params(**kw))
+    assert e.value.status == status
