@@ -35,9 +35,14 @@ def _cache_path(path: str | None) -> str:
     return os.environ.get("DMCR_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "dmcr_tune.json"))
 
 
-def _key(p: _lib.Params) -> str:
-    name = torch.cuda.get_device_name()
-    return "|".join(map(str, (name, tuple(p.shape), tuple(p.window), p.levels, p.threshold, p.alpha, p.path)))
+def _key(p: _lib.Params, device_name: str | None = None) -> str:
+    name = device_name if device_name is not None else torch.cuda.get_device_name()
+    return "|".join(map(str, (name, tuple(p.shape), tuple(p.window), p.levels, p.threshold, p.alpha, p.path,
+                              p.descriptor, p.phases)))
+
+
+def _field_shape(p: _lib.Params) -> tuple:
+    return tuple(p.shape) if p.phases == 1 else (p.phases,) + tuple(p.shape)
 
 
 def _time(p: _lib.Params, field, target, reps: int = 3) -> float:
@@ -60,15 +65,18 @@ def _time(p: _lib.Params, field, target, reps: int = 3) -> float:
     return float(np.median(times))
 
 
-def search(p: _lib.Params, seed: int = 0) -> tuple[tuple, float, list]:
-    """Coordinate descent over the launch shapes; returns (best tune, its ms, trials)."""
+def search(p: _lib.Params, seed: int = 0, device="cuda", timer=None) -> tuple[tuple, float, list]:
+    """Coordinate descent over the launch shapes; returns (best tune, its ms, trials).
+    ``timer(params, field, target)`` measures one shape (default: CUDA events)."""
     rng = np.random.default_rng(seed)
-    field = torch.tensor(rng.uniform(0.0, 1.0, p.shape), dtype=torch.float32, device="cuda")
-    target = torch.tensor((rng.random(p.shape) < 0.35).astype(np.float32), device="cuda")
+    shape = _field_shape(p)
+    field = torch.tensor(rng.uniform(0.0, 1.0, shape), dtype=torch.float32, device=device)
+    target = torch.tensor((rng.random(shape) < 0.35).astype(np.float32), device=device)
     trials = []
+    timer = timer or _time
 
     def run(t):
-        ms = _time(dataclasses.replace(p, tune=t), field, target)
+        ms = timer(dataclasses.replace(p, tune=t), field, target)
         trials.append((t, ms))
         return ms
 
@@ -88,7 +96,10 @@ def search(p: _lib.Params, seed: int = 0) -> tuple[tuple, float, list]:
 
 
 def tuned(p: _lib.Params, cache: str | None = None) -> _lib.Params:
-    """params with the cached (or freshly measured) fastest launch shape."""
+    """params with the cached (or freshly measured) fastest launch shape.  The three-point
+    descriptor does not run the tuned kernels: its params come back unchanged."""
+    if p.descriptor == _lib.DMCR_DESC_S3:
+        return p
     path = _cache_path(cache)
     key = _key(p)
     with _lock:
