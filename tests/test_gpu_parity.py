@@ -257,6 +257,32 @@ def test_reconstruction_trajectory_matches_oracle(cuda_lib):
     np.testing.assert_allclose(h[:, 1], want, rtol=1e-4)
 
 
+def test_reconstruction_64_window16_matches_oracle_over_200_iterations(cuda_lib):
+    """The 64^2, +-16, one-level reconstruction (GRF target thresholded to 0.30, uniform
+    start): the loss follows the oracle's for the first 50 iterations within 1e-4, and the
+    relative descriptor error after 200 iterations agrees within 5%."""
+    dm = cuda_lib
+    n, P, iters = 64, 16, 200
+    T = synthetic.target_small_2d(1000)
+    M0 = synthetic.uniform_field((n, n), seed=1001)
+    p = dm.Params(shape=(n, n), window=(P, P))
+    op = _oparams(p)
+    D_des = oracle.descriptor(T, op)
+    _, hist = oracle.reconstruct(M0, D_des, op, iters=iters, lr=1e-2)
+    f = _dev(M0)
+    m = torch.zeros_like(f)
+    v = torch.zeros_like(f)
+    h = torch.zeros(iters * 3, device="cuda")
+    rep, step = dm.dmcr_reconstruct(p, dm.ReconOpts(max_iters=iters, lr=1e-2), _dev(D_des), f, m, v, history=h)
+    assert rep["iterations"] == iters and step == iters
+    h = h.cpu().numpy().reshape(iters, 3)
+    want_L = np.array([x["L"] for x in hist])
+    np.testing.assert_allclose(h[:50, 1], want_L[:50], rtol=1e-4)
+    want_rel = hist[-1]["rel_err"]
+    assert want_rel < 0.1 * hist[0]["rel_err"]              # the run did converge a long way
+    assert abs(h[-1, 2] - want_rel) <= 0.05 * want_rel
+
+
 def test_reconstruction_converges_and_resume_is_exact(cuda_lib):
     dm = cuda_lib
     n, P = 64, 16
