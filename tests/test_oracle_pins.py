@@ -344,6 +344,25 @@ def test_adam_constant_gradient_steps_by_lr():
         M = M_new
 
 
+def test_adam_two_steps_where_eps_matters():
+    """Two steps by hand on one parameter with gradients 1e-6 then -2e-6, beta = (0.9, 0.999),
+    eps = 1e-7, in the efficient form of Kingma & Ba (Sec. 2: step size
+    lr * sqrt(1 - beta2^t) / (1 - beta1^t), eps added to the uncorrected sqrt(v)):
+      t = 1: m = 1e-7, v = 1e-15, sqrt(v) = 3.16227766e-8,
+             move = lr * 0.316227766 * 1e-7 / 1.316227766e-7   = 0.240253073 lr;
+      t = 2: m = -1.1e-7, v = 4.999e-15, sqrt(v) = 7.0703607e-8,
+             move = lr * 0.235317 * -1.1e-7 / 1.70703607e-7  = -0.151636162 lr.
+    At |g| ~ eps these differ from the bias-corrected-eps placement (0.909 lr at t = 1)."""
+    lr = 0.01
+    M = np.zeros(1)
+    m = np.zeros(1)
+    v = np.zeros(1)
+    M1, m, v = oracle.adam_step(M, np.array([1e-6]), m, v, 1, lr, 0.9, 0.999, 1e-7)
+    np.testing.assert_allclose(M1, -0.240253073352042 * lr, rtol=1e-12)
+    M2, m, v = oracle.adam_step(M1, np.array([-2e-6]), m, v, 2, lr, 0.9, 0.999, 1e-7)
+    np.testing.assert_allclose(M2 - M1, 0.151636162157530 * lr, rtol=1e-12)
+
+
 def test_oracle_reconstruction_lowers_loss_on_small_checkerboard():
     """Flow chart of Sec. 3 on a 16x16 checkerboard: the loss falls."""
     T = synthetic.checkerboard(16, 4)
