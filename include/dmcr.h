@@ -87,7 +87,7 @@ typedef struct {
     int levels;              /* >= 1; level l has size n / 2^(l-1), mean of 2^d children */
     int threshold;           /* DMCR_SOFT (default) or DMCR_IDENTITY */
     float alpha;             /* soft-threshold slope; the paper uses 10 */
-    float level_weight_exp;  /* w_l = 2^(level_weight_exp (l-1)); <0 selects ndim/2 (2^(l-1) in 2-D) */
+    float level_weight_exp;  /* w_l = 2^(level_weight_exp (l-1)); <0 selects ndim/2 (2^(l-1) in 2-D); must be finite */
     int path;                /* DMCR_PATH_AUTO, DMCR_PATH_DIRECT or DMCR_PATH_FFT */
     int tune[4];             /* launch shape (0 = built-in choice): forward tile rows {8,16,32},
                                 adjoint ry rows per shift chunk (1..16), adjoint chunk target

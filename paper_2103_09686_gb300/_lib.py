@@ -161,6 +161,9 @@ class Params:
         return len(self.shape)
 
     def c(self) -> dmcr_params:
+        if len(self.shape) not in (2, 3) or len(self.window) != len(self.shape) or len(self.tune) > 4:
+            raise DmcrError(DMCR_EINVAL, "shape and window must both have 2 or 3 entries (got %d and %d),"
+                            " tune at most 4" % (len(self.shape), len(self.window)))
         p = dmcr_params()
         p.ndim = len(self.shape)
         for a, s in enumerate(self.shape):
@@ -172,7 +175,7 @@ class Params:
         p.alpha = float(self.alpha)
         p.level_weight_exp = float(self.level_weight_exp)
         p.path = int(self.path)
-        for i, t in enumerate(tuple(self.tune)[:4]):
+        for i, t in enumerate(self.tune):
             p.tune[i] = int(t)
         p.descriptor = int(self.descriptor)
         p.phases = int(self.phases)

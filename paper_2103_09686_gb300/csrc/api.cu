@@ -302,6 +302,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             return fail(DMCR_EINVAL, "size %lld not divisible by 2^(levels-1)", (long long)n[a]);
     }
     if (n[0] * n[1] * n[2] * (p->phases > 1 ? p->phases : 1) > (1LL << 34)) return fail(DMCR_EINVAL, "field too large");
+    if (!isfinite(p->level_weight_exp)) return fail(DMCR_EINVAL, "level_weight_exp must be finite");
     const double we = p->level_weight_exp < 0.f ? p->ndim / 2.0 : (double)p->level_weight_exp;
     int tune[4] = {p->tune[0], p->tune[1], p->tune[2], p->tune[3]};
     if (tune[0] == 0) tune[0] = forward_rows(n, P, p->levels, p->ndim);

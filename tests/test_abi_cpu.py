@@ -55,6 +55,16 @@ def test_version_and_lengths(lib):
     (dict(shape=(14, 14), window=(3, 3), path=2), 6),      # FFT path: sizes must factor into 2, 3, 5
     (dict(shape=(64, 60), window=(4, 4), threshold=1), 6),  # identity needs n % 8 == 0
     (dict(shape=(64, 64), window=(4, 4), tune=(12, 0, 0, 0)), 1),   # forward tile rows must be 8/16/32
+    (dict(shape=(0, 64), window=(0, 0)), 1),               # empty field
+    (dict(shape=(64, 64), window=(-1, 4)), 1),
+    (dict(shape=(64,), window=(4,)), 1),                   # 1-D
+    (dict(shape=(8, 8, 8, 8), window=(1, 1, 1, 1)), 1),    # 4-D
+    (dict(shape=(64, 64), window=(4, 4, 4)), 1),           # window rank differs from the field's
+    (dict(shape=(64, 64), window=(4, 4), levels=0), 1),
+    (dict(shape=(64, 64), window=(4, 4), levels=9), 1),
+    (dict(shape=(64, 64), window=(4, 4), alpha=float("nan")), 1),
+    (dict(shape=(64, 64), window=(4, 4), level_weight_exp=float("inf")), 1),
+    (dict(shape=(1 << 18, 1 << 17), window=(1, 1)), 1),   # more than 2^34 elements
 ])
 def test_argument_validation(lib, kw, status):
     import paper_2103_09686_gb300 as dm
@@ -62,6 +72,15 @@ def test_argument_validation(lib, kw, status):
         dm.dmcr_descriptor_length(dm.Params(**kw))
     assert e.value.status == status
     assert len(lib.dmcr_last_error()) > 0
+
+
+def test_degenerate_windows_are_valid():
+    import paper_2103_09686_gb300 as dm
+    # window 0: only S(0) per level; a 1 x 1 field; a window of exactly half the size
+    assert dm.dmcr_descriptor_length(dm.Params((64, 64), (0, 0), levels=2)) == 2
+    assert dm.dmcr_descriptor_length(dm.Params((1, 1), (0, 0))) == 1
+    assert dm.dmcr_descriptor_length(dm.Params((8, 8), (4, 4))) == (9 * 9 + 1) // 2
+    assert dm.dmcr_descriptor_length(dm.Params((8, 8, 8), (0, 0, 4))) == 5
 
 
 def test_null_workspace_is_rejected_before_any_launch(lib):
