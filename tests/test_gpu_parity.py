@@ -48,6 +48,11 @@ CASES = [
     ((64, 64), (16, 16), 1, "mid"),           # |M| up to 3: the two-pair product form
     ((96, 64), (12, 9), 2, "mixed"),          # a few out-of-range pixels: per-block mode mix
     ((80, 96), (10, 44), 1, "uniform"),       # 12 rx blocks: adjoint chunks split the rx range
+    ((32, 32), (0, 0), 2, "uniform"),         # window 0: S(0) alone per level
+    ((24, 40), (0, 5), 1, "uniform"),         # shifts along one axis only
+    ((40, 24), (6, 0), 1, "binary"),
+    ((8, 8, 16), (0, 2, 0), 1, "relaxed"),    # 3-D, one axis of shifts
+    ((1, 1), (0, 0), 1, "relaxed"),           # a single pixel
 ]
 
 
@@ -281,6 +286,39 @@ def test_reconstruction_64_window16_matches_oracle_over_200_iterations(cuda_lib)
     want_rel = hist[-1]["rel_err"]
     assert want_rel < 0.1 * hist[0]["rel_err"]              # the run did converge a long way
     assert abs(h[-1, 2] - want_rel) <= 0.05 * want_rel
+
+
+def test_adam_step_matches_oracle(cuda_lib):
+    """Two single iterations through dmcr_adam_step: the loss, the moments and the field
+    update follow the oracle's gradient and Adam step (Keras form)."""
+    dm = cuda_lib
+    shape, window, levels = (48, 40), (5, 7), 2
+    rng = np.random.default_rng(23)
+    T = (rng.random(shape) < 0.35).astype(np.float64)
+    M = rng.uniform(-0.2, 1.2, shape)
+    p = dm.Params(shape=shape, window=window, levels=levels)
+    op = _oparams(p)
+    D_des = oracle.descriptor(T, op)
+    opts = dm.ReconOpts(lr=1e-2)
+    f = _dev(M)
+    m = torch.zeros_like(f)
+    v = torch.zeros_like(f)
+    loss = torch.zeros(len(dm.OUT_NAMES), device="cuda")
+    Mr, mr, vr = _f64(M), np.zeros(shape), np.zeros(shape)
+    step = 0
+    for t in (1, 2):
+        f_before = f.cpu().numpy().astype(np.float64)
+        step = dm.dmcr_adam_step(p, opts, _dev(D_des), f, m, v, step, loss_out=loss)
+        out, g = oracle.loss_grad(Mr, _f64(D_des), op)
+        Mn, mr, vr = oracle.adam_step(Mr, g, mr, vr, t, lr=1e-2)
+        assert step == t
+        np.testing.assert_allclose(float(loss[list(dm.OUT_NAMES).index("L")]), out["L"], rtol=1e-4)
+        for got, want, tol in ((m, mr, 2e-5), (v, vr, 4e-5)):
+            got = got.cpu().numpy().astype(np.float64)
+            assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol
+        dM = f.cpu().numpy().astype(np.float64) - f_before
+        assert np.linalg.norm(dM - (Mn - Mr)) / np.linalg.norm(Mn - Mr) < 1e-4
+        Mr = f.cpu().numpy().astype(np.float64)     # continue from the GPU's FP32 iterate
 
 
 def test_reconstruction_converges_and_resume_is_exact(cuda_lib):
