@@ -98,9 +98,10 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
     return r;
 }
 
-// grid (max nblk, instances): FP64 partial sums of one loss evaluation over the instance's
-// own nblk blocks (a fixed grid per problem size) -- sum (D - D_des)^2 and sum D_des^2 over
-// the descriptor, and sum ex^2 of the box excess over the field (when the penalty is on).
+// grid (max nblk, instances): double-float partial sums of one loss evaluation over the
+// instance's own nblk blocks (a fixed grid per problem size) -- sum (D - D_des)^2 and
+// sum D_des^2 over the descriptor, and sum ex^2 of the box excess over the field (when the
+// penalty is on).
 // partials[3 b + {0, 1, 2}] for block b.
 __global__ void stats_kernel(const PenSeg* __restrict__ segs) {
     const PenSeg& sg = segs[blockIdx.y];
@@ -110,7 +111,8 @@ __global__ void stats_kernel(const PenSeg* __restrict__ segs) {
     const int64_t stride = (int64_t)sg.nblk * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // per-thread compensated (Kahan) FP32 sums in a fixed order -- FP64 arithmetic is slow on
-    // this part and a thread sums only K / 65536 terms -- then FP64 across the block
+    // this part and a thread sums only about 8 terms (stats_blocks) -- then a double-float
+    // (two-sum) tree across the block
     float r2 = 0.f, r2c = 0.f, t2 = 0.f, t2c = 0.f, e2 = 0.f, e2c = 0.f;
     auto kahan = [](float& sum, float& comp, float v) {
         const float y = v - comp;

@@ -17,8 +17,9 @@
 // (broadcast) and 16 tip values (4 x LDS.128) and evaluates 64 pairs.  Consecutive lanes
 // own consecutive ry, i.e. consecutive shared-memory rows whose stride is 4 mod 32 words,
 // so the LDS.128 reads are bank-conflict free.  Per-thread sums are hierarchical (row,
-// plane, block) in FP32, written per tile and reduced across tiles in FP64 in fixed order:
-// the result is deterministic.
+// plane, block) in FP32, written per tile and reduced across tiles in fixed order with
+// compensated sums (Kahan per warp, then a double-float two-sum of the warps): the result
+// is deterministic.
 //
 // Adjoint (full window, gather form).  A thread owns 8 consecutive positions of one row;
 // lanes own consecutive rows.  For every shift of its block's chunk it accumulates
@@ -532,7 +533,8 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedSeg* __restric
     __shared__ DF sh[8][RED_K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k = ((int64_t)blockIdx.x - sg.blockStart) * RED_K + lane;
-    // compensated (Kahan) FP32 sum over this warp's tiles, then an FP64 sum of the 8 warps
+    // compensated (Kahan) FP32 sum over this warp's tiles, then a double-float (two-sum)
+    // combination of the 8 warps
     float sum = 0.f, comp = 0.f;
     auto kahan = [&](float v) {
         const float y = v - comp;
