@@ -144,6 +144,7 @@ typedef struct {
     int converged;           /* 1 if tol_rel was reached */
     float loss[DMCR_OUT_COUNT];   /* loss_out of the last evaluated iterate */
     int status;              /* dmcr_status of the run */
+    float rounded_rel_err;   /* rel_err of the returned field rounded to 0/1 (M >= 1/2 -> 1; Sec. 4.1) */
 } dmcr_recon_report;
 
 /* Library version as 10000*major + 100*minor + patch. */

@@ -51,7 +51,8 @@ class dmcr_adam_state(ctypes.Structure):
 
 
 class dmcr_recon_report(ctypes.Structure):
-    _fields_ = [("iterations", c_int), ("converged", c_int), ("loss", c_float * 6), ("status", c_int)]
+    _fields_ = [("iterations", c_int), ("converged", c_int), ("loss", c_float * 6), ("status", c_int),
+                ("rounded_rel_err", c_float)]
 
 
 class DmcrError(RuntimeError):
@@ -289,7 +290,8 @@ def dmcr_reconstruct(p: Params, opts: ReconOpts, target_desc, field, m, v, step:
                                      ctypes.byref(st), _ptr(history), ctypes.byref(rep), ws.data_ptr(), ws.numel(),
                                      _stream(stream))
     _check(status)
-    report = {"iterations": rep.iterations, "converged": bool(rep.converged), "status": rep.status}
+    report = {"iterations": rep.iterations, "converged": bool(rep.converged), "status": rep.status,
+              "rounded_rel_err": float(rep.rounded_rel_err)}
     report.update({k: float(rep.loss[i]) for i, k in enumerate(OUT_NAMES)})
     return report, st.step
 
@@ -389,7 +391,8 @@ def dmcr_reconstruct_batched(params, opts, targets, fields, ms, vs, steps, ws=No
     _check(status)
     out = []
     for i in range(n):
-        r = {"iterations": reps[i].iterations, "converged": bool(reps[i].converged), "status": reps[i].status}
+        r = {"iterations": reps[i].iterations, "converged": bool(reps[i].converged), "status": reps[i].status,
+             "rounded_rel_err": float(reps[i].rounded_rel_err)}
         r.update({k: float(reps[i].loss[j]) for j, k in enumerate(OUT_NAMES)})
         out.append(r)
     return out, [st[i].step for i in range(n)]

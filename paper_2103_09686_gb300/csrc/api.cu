@@ -1159,6 +1159,31 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
             else if (hs[i].done == 2 && !per_instance_status)
                 st = fail(DMCR_ENONFINITE, "loss became non-finite in instance %d", i);
         }
+        if (st) break;
+        // one more evaluation, of every returned field rounded to phases 0/1 (Sec. 4.1): the
+        // rounded field goes to the first level's adjoint partials, which no forward pass uses
+        std::vector<Inst> rin(in);
+        for (Inst& y : rin) {
+            float* rf = reinterpret_cast<float*>(y.ws + y.pl->o_adj[0]);
+            launch_round_field(y.field, rf, y.pl->N1 * y.pl->phases, s);
+            y.field = rf;
+            y.M = nullptr;
+            y.loss_out = nullptr;
+            y.grad = nullptr;
+            y.m = y.v = nullptr;
+            y.history = nullptr;
+            y.use_done = false;
+            y.lp.recon = 0;
+        }
+        Prepared PR;
+        if ((st = prepare(rin, F_FWD | F_LOSS, tab, tab_cap, PR))) break;
+        upload(PR, s);
+        run(PR, s);
+        if ((st = cuda_check(cudaMemcpyAsync(hs.data(), scal_base, count * sizeof(Scalars), cudaMemcpyDeviceToHost, s),
+                             "scalars D2H")))
+            break;
+        if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
+        for (int i = 0; i < count; ++i) reports[i].rounded_rel_err = hs[i].err ? NAN : hs[i].loss[5];
     } while (0);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);

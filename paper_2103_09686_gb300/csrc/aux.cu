@@ -384,4 +384,18 @@ void launch_init_uniform(float* field, int64_t count, uint64_t seed, cudaStream_
     init_uniform_kernel<<<(unsigned)((count + th - 1) / th), th, 0, s>>>(field, count, seed);
 }
 
+// The rounded field used to evaluate a reconstruction (Sec. 4.1): values >= 1/2 become
+// phase 1, the rest phase 0.
+__global__ void round_field_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    dst[i] = src[i] >= 0.5f ? 1.f : 0.f;
+}
+
+void launch_round_field(const float* src, float* dst, int64_t count, cudaStream_t s) {
+    if (count <= 0) return;
+    const int th = 256;
+    round_field_kernel<<<(unsigned)((count + th - 1) / th), th, 0, s>>>(src, dst, count);
+}
+
 }  // namespace dmcr

@@ -291,6 +291,7 @@ void launch_corr_adj(const AdjSeg* segs, int nseg, int64_t blocks, size_t smem, 
                      cudaStream_t s);
 void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, cudaStream_t s);
 void launch_init_uniform(float* field, int64_t count, uint64_t seed, cudaStream_t s);
+void launch_round_field(const float* src, float* dst, int64_t count, cudaStream_t s);
 void launch_scalars_init(const InitSeg* segs, int nseg, cudaStream_t s);
 void set_kernel_attributes();
 void set_gram_attributes();

@@ -100,6 +100,7 @@ def test_reconstruction_same_alone_and_in_the_mix(cuda_lib):
         assert rep["converged"] == reps[i]["converged"]
         assert torch.equal(f, fb[i]), i
         assert rep["rel_err"] == reps[i]["rel_err"]
+        assert rep["rounded_rel_err"] == reps[i]["rounded_rel_err"]
 
 
 def test_nan_poisoned_instance_is_isolated(cuda_lib):

@@ -166,6 +166,9 @@ def test_multiphase_reconstruction_reduces_the_loss(cuda_lib):
     f0 = _dev(synthetic.uniform_field((3, n, n), 3))
     first, _ = dm.loss_grad(f0, D, p)
     assert rep["L"] < 0.2 * float(first[4])
+    Dr = dm.descriptor((f >= 0.5).float(), p).double()
+    want = float(torch.linalg.norm(Dr - D.double()) / torch.linalg.norm(D.double()))
+    np.testing.assert_allclose(rep["rounded_rel_err"], want, rtol=1e-4, atol=1e-7)
 
 
 def test_multiphase_rejections(cuda_lib):

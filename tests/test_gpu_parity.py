@@ -361,6 +361,30 @@ def test_reconstruction_stops_at_tolerance(cuda_lib):
     assert rep["rel_err"] < 0.05 * 1.5
 
 
+def test_report_gives_the_rounded_field_error(cuda_lib):
+    """report.rounded_rel_err is the relative descriptor error of the returned field rounded
+    to phases 0/1 (M >= 1/2 -> 1, Sec. 4.1), against the oracle's descriptor of that field."""
+    dm = cuda_lib
+    n, P = 32, 4
+    T = synthetic.target_2d_grf(n, 3.0, 0.4, seed=19)
+    p = dm.Params(shape=(n, n), window=(P, P), levels=2)
+    op = _oparams(p)
+    D_des = oracle.descriptor(T, op)
+    f = torch.empty(n, n, device="cuda")
+    m = torch.zeros_like(f)
+    v = torch.zeros_like(f)
+    rep, _ = dm.dmcr_reconstruct(p, dm.ReconOpts(max_iters=150, lr=1e-2, init=dm.DMCR_INIT_UNIFORM_SEEDED, seed=4),
+                                 _dev(D_des), f, m, v)
+    Mr = oracle.round_field(f.cpu().numpy().astype(np.float64))
+    want = np.linalg.norm(oracle.descriptor(Mr, op) - D_des) / np.linalg.norm(D_des)
+    assert want > 1e-3                                     # not yet exact: a non-trivial value
+    np.testing.assert_allclose(rep["rounded_rel_err"], want, rtol=1e-3)
+    # the rounded error of the exact target is zero
+    f = _dev(T)
+    rep, _ = dm.dmcr_reconstruct(p, dm.ReconOpts(max_iters=0), _dev(D_des), f, m, v)
+    assert rep["rounded_rel_err"] < 1e-6
+
+
 def test_workspace_too_small_is_enomem(cuda_lib):
     dm = cuda_lib
     p = dm.Params(shape=(64, 64), window=(8, 8))

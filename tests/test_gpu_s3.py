@@ -114,6 +114,9 @@ def test_s3_adam_steps_reduce_the_loss(cuda_lib):
     assert rep["rel_err"] < 0.5
     first, _ = dm.loss_grad(_dev(synthetic.uniform_field((n, n), 9)), D, p)
     assert rep["L"] < 0.5 * float(first[4])
+    Dr = dm.descriptor((f >= 0.5).float(), p).double()
+    want = float(torch.linalg.norm(Dr - D.double()) / torch.linalg.norm(D.double()))
+    np.testing.assert_allclose(rep["rounded_rel_err"], want, rtol=1e-4, atol=1e-7)
 
 
 def test_s3_identity_values_beyond_the_fp16_range(cuda_lib):
