@@ -130,6 +130,8 @@ typedef struct {
     int init;                /* DMCR_INIT_CALLER or DMCR_INIT_UNIFORM_SEEDED */
     uint64_t seed;           /* SplitMix64 seed for DMCR_INIT_UNIFORM_SEEDED */
     int check_every;         /* stopping test every k iterations (>= 1) */
+    int report_rounded;      /* nonzero: dmcr_reconstruct(_batched) evaluates the returned field
+                                rounded to 0/1 once more for report.rounded_rel_err (NaN when 0) */
 } dmcr_recon_opts;
 
 /* Adam state of one job: caller-owned device buffers, kept between calls (resume). */
@@ -144,7 +146,8 @@ typedef struct {
     int converged;           /* 1 if tol_rel was reached */
     float loss[DMCR_OUT_COUNT];   /* loss_out of the last evaluated iterate */
     int status;              /* dmcr_status of the run */
-    float rounded_rel_err;   /* rel_err of the returned field rounded to 0/1 (M >= 1/2 -> 1; Sec. 4.1) */
+    float rounded_rel_err;   /* rel_err of the returned field rounded to 0/1 (M >= 1/2 -> 1; Sec. 4.1);
+                                NaN unless opts.report_rounded */
 } dmcr_recon_report;
 
 /* Library version as 10000*major + 100*minor + patch. */

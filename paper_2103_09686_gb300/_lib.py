@@ -43,7 +43,7 @@ class dmcr_loss_opts(ctypes.Structure):
 class dmcr_recon_opts(ctypes.Structure):
     _fields_ = [("max_iters", c_int), ("tol_rel", c_float), ("lr", c_float), ("beta1", c_float),
                 ("beta2", c_float), ("eps", c_float), ("loss", dmcr_loss_opts), ("init", c_int),
-                ("seed", c_uint64), ("check_every", c_int)]
+                ("seed", c_uint64), ("check_every", c_int), ("report_rounded", c_int)]
 
 
 class dmcr_adam_state(ctypes.Structure):
@@ -205,6 +205,7 @@ class ReconOpts:
     init: int = DMCR_INIT_CALLER
     seed: int = 0
     check_every: int = 1
+    report_rounded: bool = True   # evaluate the rounded result once more (report["rounded_rel_err"])
 
     def c(self) -> dmcr_recon_opts:
         o = dmcr_recon_opts()
@@ -215,6 +216,7 @@ class ReconOpts:
         o.init = int(self.init)
         o.seed = int(self.seed) & ((1 << 64) - 1)
         o.check_every = int(self.check_every)
+        o.report_rounded = int(bool(self.report_rounded))
         return o
 
 

@@ -472,6 +472,7 @@ struct Inst {
     LossParams lp{};
     float* history = nullptr;
     bool use_done = false;         // kernels skip the instance once its done flag is set
+    bool round_eval = false;       // reconstruction: evaluate the rounded result once more
     int64_t step = 0;              // F_INIT: Adam steps taken before this call
     const float* lv[MAX_LEVELS] = {};
 };
@@ -1160,9 +1161,19 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
                 st = fail(DMCR_ENONFINITE, "loss became non-finite in instance %d", i);
         }
         if (st) break;
-        // one more evaluation, of every returned field rounded to phases 0/1 (Sec. 4.1): the
-        // rounded field goes to the first level's adjoint partials, which no forward pass uses
-        std::vector<Inst> rin(in);
+        // one more evaluation, of the returned fields rounded to phases 0/1 (Sec. 4.1) where
+        // asked for: a rounded field goes to its first level's adjoint partials, which no
+        // forward pass uses
+        std::vector<Inst> rin;
+        std::vector<int> rid;
+        for (int i = 0; i < count; ++i) {
+            reports[i].rounded_rel_err = NAN;
+            if (in[i].round_eval) {
+                rin.push_back(in[i]);
+                rid.push_back(i);
+            }
+        }
+        if (rin.empty()) break;
         for (Inst& y : rin) {
             float* rf = reinterpret_cast<float*>(y.ws + y.pl->o_adj[0]);
             launch_round_field(y.field, rf, y.pl->N1 * y.pl->phases, s);
@@ -1183,7 +1194,7 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
                              "scalars D2H")))
             break;
         if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
-        for (int i = 0; i < count; ++i) reports[i].rounded_rel_err = hs[i].err ? NAN : hs[i].loss[5];
+        for (int i : rid) reports[i].rounded_rel_err = hs[i].err ? NAN : hs[i].loss[5];
     } while (0);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -1223,6 +1234,7 @@ void recon_inst(Inst& x, const dmcr_recon_opts* o, const float* target, float* f
     x.lp.recon = 1;
     x.history = history;
     x.use_done = true;
+    x.round_eval = o->report_rounded != 0;
     x.step = st->step;
 }
 

@@ -162,7 +162,8 @@ class Server:
         opts = []
         for j in jobs:
             left = j.opts.max_iters - j.iters_done
-            opts.append(dataclasses.replace(j.opts, max_iters=min(self.tick_iters, left), init=_lib.DMCR_INIT_CALLER))
+            opts.append(dataclasses.replace(j.opts, max_iters=min(self.tick_iters, left), init=_lib.DMCR_INIT_CALLER,
+                                            report_rounded=False))
         t_tick = time.perf_counter()
         reps, steps = _lib.dmcr_reconstruct_batched([j.params for j in jobs], opts, [j.desc for j in jobs],
                                                     [j.field for j in jobs], [j.m for j in jobs],

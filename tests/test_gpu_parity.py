@@ -383,6 +383,8 @@ def test_report_gives_the_rounded_field_error(cuda_lib):
     f = _dev(T)
     rep, _ = dm.dmcr_reconstruct(p, dm.ReconOpts(max_iters=0), _dev(D_des), f, m, v)
     assert rep["rounded_rel_err"] < 1e-6
+    rep, _ = dm.dmcr_reconstruct(p, dm.ReconOpts(max_iters=0, report_rounded=False), _dev(D_des), f, m, v)
+    assert np.isnan(rep["rounded_rel_err"])
 
 
 def test_workspace_too_small_is_enomem(cuda_lib):
