@@ -28,6 +28,7 @@ DMCR_LOSS_NORM, DMCR_LOSS_SQUARED = 0, 1
 DMCR_PROLONG_ADJOINT_ACCUMULATE, DMCR_PROLONG_INJECT = 0, 1
 DMCR_INIT_CALLER, DMCR_INIT_UNIFORM_SEEDED = 0, 1
 OUT_NAMES = ("E", "E2", "Ebc", "lambda", "L", "rel_err")
+DMCR_OUT_COUNT = len(OUT_NAMES)
 
 
 class dmcr_params(ctypes.Structure):
@@ -141,6 +142,34 @@ def _ptr(t):
     return t.data_ptr()
 
 
+# The C calls take bare device pointers and trust their sizes; the binding checks every
+# tensor against the sizes the parameters imply before anything is launched, so that a
+# wrong tensor raises here instead of reaching the device.
+
+def _sized(t, n: int, what: str, at_least: bool = False):
+    """Pointer of a float32 CUDA tensor holding exactly (or at least) n elements."""
+    ptr = _ptr(t)
+    if t is not None and (t.numel() < n if at_least else t.numel() != n):
+        raise ValueError("%s must hold %s%d float32 elements (has %d)" % (what, "at least " if at_least else "", n,
+                                                                          t.numel()))
+    return ptr
+
+
+def _ws(ws):
+    """(pointer, bytes) of a workspace tensor."""
+    if not ws.is_cuda or not ws.is_contiguous():
+        raise ValueError("workspace must be a contiguous CUDA tensor")
+    return ws.data_ptr(), ws.numel() * ws.element_size()
+
+
+def _lengths(p) -> tuple:
+    """(field elements, descriptor length) of a problem: N * phases and sum_l K."""
+    n = 1
+    for a in p.shape:
+        n *= int(a)
+    return n * max(int(p.phases), 1), dmcr_descriptor_length(p)
+
+
 # ----------------------------------------------------------------------------- params
 
 @dataclasses.dataclass(frozen=True)
@@ -244,36 +273,44 @@ def workspace(p: Params, device=None) -> torch.Tensor:
 
 
 def dmcr_descriptor(p: Params, field, desc, ws=None, stream=None):
+    N, K = _lengths(p)
+    fp, dp = _sized(field, N, "field"), _sized(desc, K, "desc")
     ws = workspace(p, field.device) if ws is None else ws
-    _check(load().dmcr_descriptor(ctypes.byref(p.c()), _ptr(field), _ptr(desc), ws.data_ptr(), ws.numel(),
-                                  _stream(stream)))
+    _check(load().dmcr_descriptor(ctypes.byref(p.c()), fp, dp, *_ws(ws), _stream(stream)))
     return desc
 
 
 def dmcr_loss_grad(p: Params, opts: LossOpts, field, target_desc, loss_out, grad=None, desc_out=None, ws=None,
                    stream=None):
+    N, K = _lengths(p)
+    ptrs = (_sized(field, N, "field"), _sized(target_desc, K, "target_desc"),
+            _sized(loss_out, DMCR_OUT_COUNT, "loss_out", at_least=True), _sized(grad, N, "grad"),
+            _sized(desc_out, K, "desc_out"))
     ws = workspace(p, field.device) if ws is None else ws
-    _check(load().dmcr_loss_grad(ctypes.byref(p.c()), ctypes.byref(opts.c()), _ptr(field), _ptr(target_desc),
-                                 _ptr(loss_out), _ptr(grad), _ptr(desc_out), ws.data_ptr(), ws.numel(),
-                                 _stream(stream)))
+    _check(load().dmcr_loss_grad(ctypes.byref(p.c()), ctypes.byref(opts.c()), *ptrs, *_ws(ws), _stream(stream)))
 
 
 def dmcr_descriptor_vjp(p: Params, field, grad_desc, grad_field, ws=None, stream=None):
+    N, K = _lengths(p)
+    ptrs = (_sized(field, N, "field"), _sized(grad_desc, K, "grad_desc"), _sized(grad_field, N, "grad_field"))
     ws = workspace(p, field.device) if ws is None else ws
-    _check(load().dmcr_descriptor_vjp(ctypes.byref(p.c()), _ptr(field), _ptr(grad_desc), _ptr(grad_field),
-                                      ws.data_ptr(), ws.numel(), _stream(stream)))
+    _check(load().dmcr_descriptor_vjp(ctypes.byref(p.c()), *ptrs, *_ws(ws), _stream(stream)))
     return grad_field
 
 
 def dmcr_restrict(fine, coarse, stream=None):
     n = (c_int64 * 3)(*list(fine.shape) + [0] * (3 - fine.dim()))
-    _check(load().dmcr_restrict(fine.dim(), n, _ptr(fine), _ptr(coarse), _stream(stream)))
+    fp = _ptr(fine)
+    cp = _sized(coarse, fine.numel() >> fine.dim(), "coarse")
+    _check(load().dmcr_restrict(fine.dim(), n, fp, cp, _stream(stream)))
     return coarse
 
 
 def dmcr_prolongate(coarse, fine, mode=DMCR_PROLONG_ADJOINT_ACCUMULATE, stream=None):
     n = (c_int64 * 3)(*list(coarse.shape) + [0] * (3 - coarse.dim()))
-    _check(load().dmcr_prolongate(coarse.dim(), n, _ptr(coarse), _ptr(fine), int(mode), _stream(stream)))
+    cp = _ptr(coarse)
+    fp = _sized(fine, coarse.numel() << coarse.dim(), "fine")
+    _check(load().dmcr_prolongate(coarse.dim(), n, cp, fp, int(mode), _stream(stream)))
     return fine
 
 
@@ -285,12 +322,14 @@ def dmcr_init_uniform(field, seed: int, stream=None):
 def dmcr_reconstruct(p: Params, opts: ReconOpts, target_desc, field, m, v, step: int = 0, history=None, ws=None,
                      stream=None):
     """Runs the reconstruction (synchronous).  Returns (report dict, new Adam step)."""
+    N, K = _lengths(p)
+    tp, fp = _sized(target_desc, K, "target_desc"), _sized(field, N, "field")
+    hp = _sized(history, 3 * max(int(opts.max_iters), 0), "history", at_least=True)
+    st = dmcr_adam_state(_sized(m, N, "m"), _sized(v, N, "v"), int(step))
     ws = workspace(p, field.device) if ws is None else ws
-    st = dmcr_adam_state(_ptr(m), _ptr(v), int(step))
     rep = dmcr_recon_report()
-    status = load().dmcr_reconstruct(ctypes.byref(p.c()), ctypes.byref(opts.c()), _ptr(target_desc), _ptr(field),
-                                     ctypes.byref(st), _ptr(history), ctypes.byref(rep), ws.data_ptr(), ws.numel(),
-                                     _stream(stream))
+    status = load().dmcr_reconstruct(ctypes.byref(p.c()), ctypes.byref(opts.c()), tp, fp, ctypes.byref(st), hp,
+                                     ctypes.byref(rep), *_ws(ws), _stream(stream))
     _check(status)
     report = {"iterations": rep.iterations, "converged": bool(rep.converged), "status": rep.status,
               "rounded_rel_err": float(rep.rounded_rel_err)}
@@ -301,16 +340,21 @@ def dmcr_reconstruct(p: Params, opts: ReconOpts, target_desc, field, m, v, step:
 def dmcr_adam_step(p: Params, opts: ReconOpts, target_desc, field, m, v, step: int, loss_out=None, ws=None,
                    stream=None) -> int:
     """One asynchronous iteration (loss, gradient, Adam step).  Returns the new step count."""
+    N, K = _lengths(p)
+    tp, fp = _sized(target_desc, K, "target_desc"), _sized(field, N, "field")
+    lp = _sized(loss_out, DMCR_OUT_COUNT, "loss_out", at_least=True)
+    st = dmcr_adam_state(_sized(m, N, "m"), _sized(v, N, "v"), int(step))
     ws = workspace(p, field.device) if ws is None else ws
-    st = dmcr_adam_state(_ptr(m), _ptr(v), int(step))
-    _check(load().dmcr_adam_step(ctypes.byref(p.c()), ctypes.byref(opts.c()), _ptr(target_desc), _ptr(field),
-                                 ctypes.byref(st), _ptr(loss_out), ws.data_ptr(), ws.numel(), _stream(stream)))
+    _check(load().dmcr_adam_step(ctypes.byref(p.c()), ctypes.byref(opts.c()), tp, fp, ctypes.byref(st), lp,
+                                 *_ws(ws), _stream(stream)))
     return st.step
 
 
 def dmcr_descriptor_noalloc(p: Params, field, desc, stream=None):
     """dmcr_descriptor without a workspace: scratch from the library's fixed device array."""
-    _check(load().dmcr_descriptor_noalloc(ctypes.byref(p.c()), _ptr(field), _ptr(desc), _stream(stream)))
+    N, K = _lengths(p)
+    _check(load().dmcr_descriptor_noalloc(ctypes.byref(p.c()), _sized(field, N, "field"), _sized(desc, K, "desc"),
+                                          _stream(stream)))
     return desc
 
 
@@ -323,10 +367,30 @@ def _params_array(params):
     return arr
 
 
-def _ptr_array(tensors, allow_none=False):
+def _ptr_array(tensors, sizes=None, what="tensor"):
+    """Host array of device pointers; tensor i must hold sizes[i] elements when given."""
     if tensors is None:
         return None
-    return (c_void_p * len(tensors))(*[(_ptr(t) if t is not None else None) for t in tensors])
+    if sizes is not None and len(tensors) != len(sizes):
+        raise ValueError("%s: %d tensors for %d instances" % (what, len(tensors), len(sizes)))
+    ptrs = [_sized(t, sizes[i], "%s[%d]" % (what, i)) if sizes is not None else _ptr(t)
+            for i, t in enumerate(tensors)]
+    return (c_void_p * len(tensors))(*ptrs)
+
+
+def _adam_states(ms, vs, steps, Ns):
+    n = len(Ns)
+    if len(ms) != n or len(vs) != n or len(steps) != n:
+        raise ValueError("ms, vs and steps need one entry per instance (%d)" % n)
+    st = (dmcr_adam_state * n)()
+    for i in range(n):
+        st[i] = dmcr_adam_state(_sized(ms[i], Ns[i], "ms[%d]" % i), _sized(vs[i], Ns[i], "vs[%d]" % i), int(steps[i]))
+    return st
+
+
+def _batch_lengths(params):
+    ln = [_lengths(p) for p in params]
+    return [a for a, _ in ln], [b for _, b in ln]
 
 
 def dmcr_batch_workspace_size(params) -> int:
@@ -340,37 +404,43 @@ def batch_workspace(params, device=None) -> torch.Tensor:
 
 
 def dmcr_descriptor_batched(params, fields, descs, ws=None, stream=None):
+    Ns, Ks = _batch_lengths(params)
+    fa, da = _ptr_array(fields, Ns, "fields"), _ptr_array(descs, Ks, "descs")
     ws = batch_workspace(params, fields[0].device) if ws is None else ws
-    _check(load().dmcr_descriptor_batched(len(params), _params_array(params), _ptr_array(fields), _ptr_array(descs),
-                                          ws.data_ptr(), ws.numel(), _stream(stream)))
+    _check(load().dmcr_descriptor_batched(len(params), _params_array(params), fa, da, *_ws(ws), _stream(stream)))
     return descs
 
 
 def dmcr_loss_grad_batched(params, opts: LossOpts, fields, targets, loss_out, grads=None, ws=None, stream=None):
+    Ns, Ks = _batch_lengths(params)
+    fa, ta = _ptr_array(fields, Ns, "fields"), _ptr_array(targets, Ks, "targets")
+    lo = _sized(loss_out, DMCR_OUT_COUNT * len(params), "loss_out", at_least=True)
+    ga = _ptr_array(grads, Ns, "grads")
     ws = batch_workspace(params, fields[0].device) if ws is None else ws
-    _check(load().dmcr_loss_grad_batched(len(params), _params_array(params), ctypes.byref(opts.c()),
-                                         _ptr_array(fields), _ptr_array(targets), _ptr(loss_out), _ptr_array(grads),
-                                         ws.data_ptr(), ws.numel(), _stream(stream)))
+    _check(load().dmcr_loss_grad_batched(len(params), _params_array(params), ctypes.byref(opts.c()), fa, ta, lo, ga,
+                                         *_ws(ws), _stream(stream)))
 
 
 def dmcr_descriptor_vjp_batched(params, fields, grad_descs, grad_fields, ws=None, stream=None):
+    Ns, Ks = _batch_lengths(params)
+    fa, ga = _ptr_array(fields, Ns, "fields"), _ptr_array(grad_descs, Ks, "grad_descs")
+    gf = _ptr_array(grad_fields, Ns, "grad_fields")
     ws = batch_workspace(params, fields[0].device) if ws is None else ws
-    _check(load().dmcr_descriptor_vjp_batched(len(params), _params_array(params), _ptr_array(fields),
-                                              _ptr_array(grad_descs), _ptr_array(grad_fields), ws.data_ptr(),
-                                              ws.numel(), _stream(stream)))
+    _check(load().dmcr_descriptor_vjp_batched(len(params), _params_array(params), fa, ga, gf, *_ws(ws),
+                                              _stream(stream)))
     return grad_fields
 
 
 def dmcr_adam_step_batched(params, opts: ReconOpts, targets, fields, ms, vs, steps, loss_out=None, ws=None,
                            stream=None):
     """One Adam iteration of every instance; returns the new step counts."""
-    ws = batch_workspace(params, fields[0].device) if ws is None else ws
     n = len(params)
-    st = (dmcr_adam_state * n)()
-    for i in range(n):
-        st[i] = dmcr_adam_state(_ptr(ms[i]), _ptr(vs[i]), int(steps[i]))
-    _check(load().dmcr_adam_step_batched(n, _params_array(params), ctypes.byref(opts.c()), _ptr_array(targets),
-                                         _ptr_array(fields), st, _ptr(loss_out), ws.data_ptr(), ws.numel(),
+    Ns, Ks = _batch_lengths(params)
+    ta, fa = _ptr_array(targets, Ks, "targets"), _ptr_array(fields, Ns, "fields")
+    lo = _sized(loss_out, DMCR_OUT_COUNT * n, "loss_out", at_least=True)
+    st = _adam_states(ms, vs, steps, Ns)
+    ws = batch_workspace(params, fields[0].device) if ws is None else ws
+    _check(load().dmcr_adam_step_batched(n, _params_array(params), ctypes.byref(opts.c()), ta, fa, st, lo, *_ws(ws),
                                          _stream(stream)))
     return [st[i].step for i in range(n)]
 
@@ -378,18 +448,21 @@ def dmcr_adam_step_batched(params, opts: ReconOpts, targets, fields, ms, vs, ste
 def dmcr_reconstruct_batched(params, opts, targets, fields, ms, vs, steps, ws=None, stream=None):
     """Graph-captured reconstruction of every instance (synchronous).  ``opts`` is one
     ReconOpts or a list.  Returns (list of report dicts, list of new step counts)."""
-    ws = batch_workspace(params, fields[0].device) if ws is None else ws
     n = len(params)
     if isinstance(opts, ReconOpts):
         opts = [opts] * n
+    if len(opts) != n:
+        raise ValueError("opts: %d entries for %d instances" % (len(opts), n))
+    Ns, Ks = _batch_lengths(params)
+    ta, fa = _ptr_array(targets, Ks, "targets"), _ptr_array(fields, Ns, "fields")
     oa = (dmcr_recon_opts * n)()
-    st = (dmcr_adam_state * n)()
     for i in range(n):
         oa[i] = opts[i].c()
-        st[i] = dmcr_adam_state(_ptr(ms[i]), _ptr(vs[i]), int(steps[i]))
+    st = _adam_states(ms, vs, steps, Ns)
+    ws = batch_workspace(params, fields[0].device) if ws is None else ws
     reps = (dmcr_recon_report * n)()
-    status = load().dmcr_reconstruct_batched(n, _params_array(params), oa, _ptr_array(targets), _ptr_array(fields),
-                                             st, reps, ws.data_ptr(), ws.numel(), _stream(stream))
+    status = load().dmcr_reconstruct_batched(n, _params_array(params), oa, ta, fa, st, reps, *_ws(ws),
+                                             _stream(stream))
     _check(status)
     out = []
     for i in range(n):

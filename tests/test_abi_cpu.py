@@ -120,3 +120,133 @@ def test_validation_of_descriptor_kinds_and_phases(lib, kw, status):
     with pytest.raises(dm.DmcrError) as e:
         dm.dmcr_descriptor_length(dm.Params(**kw))
     assert e.value.status == status
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA float32 tensor in the binding's argument checks (which run
+    before any call into the library); its pointer is never dereferenced."""
+
+    def __init__(self, n):
+        import torch
+        self.n = n
+        self.dtype = torch.float32
+        self.is_cuda = True
+        self.device = "cuda"
+
+    def numel(self):
+        return self.n
+
+    def is_contiguous(self):
+        return True
+
+    def data_ptr(self):
+        return 1 << 40
+
+    def element_size(self):
+        return 4
+
+
+@pytest.mark.parametrize("call", ["descriptor_field", "descriptor_desc", "loss_target", "loss_out", "loss_grad",
+                                  "vjp_grad", "adam_m", "recon_history", "restrict", "prolongate",
+                                  "batched_count", "batched_field", "batched_loss_out", "noalloc"])
+def test_binding_rejects_wrongly_sized_tensors_before_any_launch(lib, call):
+    import paper_2103_09686_gb300 as dm
+    from paper_2103_09686_gb300 import _lib
+    T = _FakeCudaTensor
+    p = dm.Params((32, 24), (4, 3), levels=2)
+    N, K = 32 * 24, dm.dmcr_descriptor_length(p)
+    q = dm.Params((16, 16), (2, 2), phases=2)
+    Nq, Kq = 2 * 256, dm.dmcr_descriptor_length(q)
+    ws = T(1 << 20)
+    calls = {
+        "descriptor_field": lambda: _lib.dmcr_descriptor(p, T(N + 1), T(K), ws),
+        "descriptor_desc": lambda: _lib.dmcr_descriptor(p, T(N), T(K - 1), ws),
+        "loss_target": lambda: _lib.dmcr_loss_grad(p, dm.LossOpts(), T(N), T(2 * K), T(6), None, None, ws),
+        "loss_out": lambda: _lib.dmcr_loss_grad(p, dm.LossOpts(), T(N), T(K), T(5), None, None, ws),
+        "loss_grad": lambda: _lib.dmcr_loss_grad(p, dm.LossOpts(), T(N), T(K), T(6), T(N // 2), None, ws),
+        "vjp_grad": lambda: _lib.dmcr_descriptor_vjp(p, T(N), T(K), T(N - 1), ws),
+        "adam_m": lambda: _lib.dmcr_adam_step(p, dm.ReconOpts(), T(K), T(N), T(N - 1), T(N), 0, None, ws),
+        "recon_history": lambda: _lib.dmcr_reconstruct(p, dm.ReconOpts(max_iters=10), T(K), T(N), T(N), T(N),
+                                                       history=T(29), ws=ws),
+        "restrict": lambda: _lib.dmcr_restrict(_Shaped((32, 24)), T(16 * 12 + 1)),
+        "prolongate": lambda: _lib.dmcr_prolongate(_Shaped((16, 12)), T(32 * 24 - 4)),
+        "batched_count": lambda: _lib.dmcr_descriptor_batched([p, q], [T(N)], [T(K), T(Kq)], ws),
+        "batched_field": lambda: _lib.dmcr_descriptor_batched([p, q], [T(N), T(Nq // 2)], [T(K), T(Kq)], ws),
+        "batched_loss_out": lambda: _lib.dmcr_loss_grad_batched([p, q], dm.LossOpts(), [T(N), T(Nq)], [T(K), T(Kq)],
+                                                                T(11), None, ws),
+        "noalloc": lambda: _lib.dmcr_descriptor_noalloc(q, T(Nq), T(Kq + 1)),
+    }
+    with pytest.raises(ValueError):
+        calls[call]()
+
+
+class _Shaped(_FakeCudaTensor):
+    def __init__(self, shape):
+        n = 1
+        for s in shape:
+            n *= s
+        super().__init__(n)
+        self.shape = shape
+
+    def dim(self):
+        return len(self.shape)
+
+
+class _RecordingLib:
+    """The real library for the host-side queries; every other entry point is recorded
+    and answers DMCR_OK without running."""
+
+    HOST = ("dmcr_descriptor_length", "dmcr_workspace_size", "dmcr_batch_workspace_size", "dmcr_last_error")
+
+    def __init__(self, real):
+        self.real = real
+        self.calls = []
+
+    def __getattr__(self, name):
+        if name in self.HOST:
+            return getattr(self.real, name)
+
+        def record(*args):
+            self.calls.append(name)
+            return 0
+        return record
+
+
+def test_binding_passes_correctly_sized_tensors_through(lib, monkeypatch):
+    import paper_2103_09686_gb300 as dm
+    from paper_2103_09686_gb300 import _lib
+    rec = _RecordingLib(lib)
+    monkeypatch.setattr(_lib, "load", lambda build_if_missing=False: rec)
+    monkeypatch.setattr(_lib, "_stream", lambda stream=None: 0)
+    T = _FakeCudaTensor
+    p = dm.Params((32, 24), (4, 3), levels=2)
+    q = dm.Params((16, 16), (2, 2), phases=2)
+    s3 = dm.Params((16, 16), (3, 3), descriptor=dm.DMCR_DESC_S3)
+    N, K = 32 * 24, dm.dmcr_descriptor_length(p)
+    Nq, Kq = 2 * 256, dm.dmcr_descriptor_length(q)
+    N3, K3 = 256, dm.dmcr_descriptor_length(s3)
+    ws = T(1 << 20)
+    _lib.dmcr_descriptor(p, T(N), T(K), ws)
+    _lib.dmcr_descriptor(q, T(Nq), T(Kq), ws)
+    _lib.dmcr_descriptor(s3, T(N3), T(K3), ws)
+    _lib.dmcr_loss_grad(p, dm.LossOpts(), T(N), T(K), T(6), T(N), None, ws)
+    _lib.dmcr_loss_grad(q, dm.LossOpts(), T(Nq), T(Kq), T(6), None, T(Kq), ws)
+    _lib.dmcr_descriptor_vjp(s3, T(N3), T(K3), T(N3), ws)
+    _lib.dmcr_restrict(_Shaped((32, 24)), T(16 * 12))
+    _lib.dmcr_prolongate(_Shaped((4, 6, 8)), T(8 * 12 * 16))
+    _lib.dmcr_reconstruct(p, dm.ReconOpts(max_iters=10), T(K), T(N), T(N), T(N), history=T(30), ws=ws)
+    _lib.dmcr_reconstruct(q, dm.ReconOpts(max_iters=10), T(Kq), T(Nq), T(Nq), T(Nq), ws=ws)
+    _lib.dmcr_adam_step(p, dm.ReconOpts(), T(K), T(N), T(N), T(N), 0, T(6), ws)
+    _lib.dmcr_descriptor_noalloc(p, T(N), T(K))
+    params = [p, q, s3]
+    Ns, Ks = [N, Nq, N3], [K, Kq, K3]
+    F = lambda sizes: [T(n) for n in sizes]  # noqa: E731
+    _lib.dmcr_descriptor_batched(params, F(Ns), F(Ks), ws)
+    _lib.dmcr_loss_grad_batched(params, dm.LossOpts(), F(Ns), F(Ks), T(18), F(Ns), ws)
+    _lib.dmcr_descriptor_vjp_batched(params, F(Ns), F(Ks), F(Ns), ws)
+    _lib.dmcr_adam_step_batched(params, dm.ReconOpts(), F(Ks), F(Ns), F(Ns), F(Ns), [0, 0, 0], T(18), ws)
+    _lib.dmcr_reconstruct_batched(params, dm.ReconOpts(), F(Ks), F(Ns), F(Ns), F(Ns), [0, 0, 0], ws)
+    assert rec.calls == ["dmcr_descriptor"] * 3 + ["dmcr_loss_grad"] * 2 + [
+        "dmcr_descriptor_vjp", "dmcr_restrict", "dmcr_prolongate", "dmcr_reconstruct", "dmcr_reconstruct",
+        "dmcr_adam_step", "dmcr_descriptor_noalloc", "dmcr_descriptor_batched", "dmcr_loss_grad_batched",
+        "dmcr_descriptor_vjp_batched", "dmcr_adam_step_batched", "dmcr_reconstruct_batched"]
