@@ -298,6 +298,9 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
     for (int a = first; a < 3; ++a) {
         if (n[a] < 1) return fail(DMCR_EINVAL, "field size must be positive");
         if (P[a] < 0) return fail(DMCR_EINVAL, "window must be >= 0");
+        if (n[a] > (1LL << 30)) return fail(DMCR_EINVAL, "field size %lld above 2^30 on axis %d", (long long)n[a], a - first);
+        if (2LL * P[a] > n[a])
+            return fail(DMCR_EINVAL, "window %d exceeds half the size %lld on axis %d", P[a], (long long)n[a], a - first);
         if (n[a] % (1LL << (p->levels - 1)) != 0)
             return fail(DMCR_EINVAL, "size %lld not divisible by 2^(levels-1)", (long long)n[a]);
     }
@@ -343,12 +346,13 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             return fail(DMCR_ENOTSUP, "window too large for the shared-memory tiles of this build");
         pl.w[l] = (float)pow(2.0, we * l);
         pl.off[l] = off;
+        if (pl.desc_kind == DMCR_DESC_S3 && g.Khalf > 16384)
+            return fail(DMCR_ENOTSUP, "three-point descriptor: at most 16384 shifts");
         off += pl.desc_kind == DMCR_DESC_S3 ? g.Khalf * g.Khalf : (int64_t)phases * phases * g.Khalf;
     }
     pl.Ktot = off;
     pl.N1 = pl.g[0].N;
     if (pl.desc_kind == DMCR_DESC_S3) {
-        if (pl.g[0].Khalf > 16384) return fail(DMCR_ENOTSUP, "three-point descriptor: at most 16384 shifts");
         pl.s3Kpad = (pl.g[0].Khalf + 255) / 256 * 256;   // whole 256-wide tiles of the W GEMM
         for (int l = 0; l < pl.levels; ++l) pl.s3Npad[l] = (pl.g[l].N + 127) / 128 * 128;
     }
@@ -377,6 +381,24 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
     }
     // App. A: f(1/2) of the threshold (1/2 for f(x) = x)
     pl.q_tilde = (float)(tc.identity ? 0.5 : 2.0 * pl.fh2);
+    // the workspace, estimated in floating point first: sizes beyond any device are
+    // rejected before the exact layout below could wrap around
+    {
+        const double ph = (double)pl.phases;
+        double est = 4.0 * (double)pl.Ktot;
+        for (int l = 0; l < pl.levels; ++l) {
+            const LevelGeom& g = pl.g[l];
+            const double N = (double)g.N;
+            const double chunks = pl.desc_kind == DMCR_DESC_S3 || g.fft ? (double)g.nChunks
+                                                                        : (double)g.nZc * g.nYc * g.nXc;
+            est += 4.0 * ph * N + 4.0 * ph * ph * chunks * N;
+            if (g.fft) est += 32.0 * N;
+            else if (pl.desc_kind == DMCR_DESC_S3)
+                est += 12.0 * (double)pl.s3Npad[l] * (double)pl.s3Kpad + 4.0 * (double)pl.s3Kpad * (double)pl.s3Kpad;
+            else est += 4.0 * ph * ph * ((double)g.fwdTiles * (double)g.Khalf + (double)gd_floats(g));
+        }
+        if (est > 0x1p50) return fail(DMCR_EINVAL, "the problem needs about %.3g bytes of workspace (more than 2^50)", est);
+    }
     // workspace layout
     size_t o = 0;
     pl.tab_bytes = align_up(table_bound(pl.levels, pl.phases) + table_slack());
@@ -852,6 +874,12 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         P.fin = {push(P.tb, fv), (int)fv.size(), fb};
     }
     if (P.tb.h.size() > cap) return fail(DMCR_ENOMEM, "segment tables (%zu bytes) exceed their region", P.tb.h.size());
+    // every fused launch indexes its blocks with a 1-D grid
+    int64_t most = std::max({P.fwd.blocks, P.red.blocks, P.gco.blocks, P.adj.blocks, P.fin.blocks, P.tmap.blocks});
+    for (const Prepared::R& r : P.restricts) most = std::max(most, r.blocks);
+    if (most > (int64_t)INT32_MAX)
+        return fail(DMCR_ENOTSUP, "a fused launch would need %lld thread blocks (more than 2^31 - 1): split the batch "
+                                  "or shrink the problem", (long long)most);
     return DMCR_OK;
 }
 

@@ -65,6 +65,8 @@ def test_version_and_lengths(lib):
     (dict(shape=(64, 64), window=(4, 4), alpha=float("nan")), 1),
     (dict(shape=(64, 64), window=(4, 4), level_weight_exp=float("inf")), 1),
     (dict(shape=(1 << 18, 1 << 17), window=(1, 1)), 1),   # more than 2^34 elements
+    (dict(shape=(1 << 31, 4), window=(1, 1)), 1),         # an axis above 2^30
+    (dict(shape=(1 << 17, 1 << 17), window=(128, 1 << 16)), 1),   # a workspace above 2^50 bytes
 ])
 def test_argument_validation(lib, kw, status):
     import paper_2103_09686_gb300 as dm
