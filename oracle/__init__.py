@@ -22,6 +22,8 @@ What each function follows (sections and equations of the paper):
   lambda = lambda0 * E.
 * ``loss_grad`` / ``descriptor_vjp`` -- the exact gradient by the chain rule through all
   levels simultaneously (Sec. 3.1, Sec. 3.3).
+* ``round_field`` -- the rounding used to evaluate a reconstruction (Sec. 4.1): values
+  >= 1/2 become phase 1 (the tie goes to phase 1), the rest phase 0.
 * ``adam_step`` / ``reconstruct`` -- Eq. M-update with Adam at the TensorFlow defaults
   (App. B): lr 1e-3, beta1 0.9, beta2 0.999; epsilon 1e-7 (Keras form; the paper does
   not print epsilon).

@@ -363,6 +363,15 @@ def test_adam_two_steps_where_eps_matters():
     np.testing.assert_allclose(M2 - M1, 0.151636162157530 * lr, rtol=1e-12)
 
 
+def test_rounding_for_evaluation():
+    """Sec. 4.1 rounds the relaxed field to phases 0/1; the tie 1/2 goes to phase 1 and
+    values outside [0, 1] round to the nearer phase."""
+    M = np.array([[0.49999999, 0.5, 0.50000001], [-3.0, 7.0, 0.0]])
+    np.testing.assert_array_equal(oracle.round_field(M), [[0, 1, 1], [0, 1, 0]])
+    B = (np.random.default_rng(2).random((9, 7)) < 0.4).astype(np.float64)
+    np.testing.assert_array_equal(oracle.round_field(B), B)     # binary fields are fixed points
+
+
 def test_oracle_reconstruction_lowers_loss_on_small_checkerboard():
     """Flow chart of Sec. 3 on a 16x16 checkerboard: the loss falls."""
     T = synthetic.checkerboard(16, 4)
