@@ -132,6 +132,15 @@ def _stream(stream=None) -> int:
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
+def _check_device(t, what: str = "tensor"):
+    """The library launches on the current CUDA device, so every pointer must belong to it:
+    a tensor on another device would hand foreign addresses to the kernels."""
+    index = getattr(t.device, "index", None)
+    if isinstance(index, int) and index != torch.cuda.current_device():
+        raise ValueError("%s is on cuda:%d but the current device is cuda:%d (make its device current, e.g. "
+                         "with torch.cuda.device(...))" % (what, index, torch.cuda.current_device()))
+
+
 def _ptr(t):
     if t is None:
         return None
@@ -139,6 +148,7 @@ def _ptr(t):
         raise ValueError("tensor must be on a CUDA device")
     if t.dtype != torch.float32 or not t.is_contiguous():
         raise ValueError("tensor must be contiguous float32")
+    _check_device(t)
     return t.data_ptr()
 
 
@@ -159,6 +169,7 @@ def _ws(ws):
     """(pointer, bytes) of a workspace tensor."""
     if not ws.is_cuda or not ws.is_contiguous():
         raise ValueError("workspace must be a contiguous CUDA tensor")
+    _check_device(ws, "workspace")
     return ws.data_ptr(), ws.numel() * ws.element_size()
 
 

@@ -304,7 +304,11 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         if (n[a] % (1LL << (p->levels - 1)) != 0)
             return fail(DMCR_EINVAL, "size %lld not divisible by 2^(levels-1)", (long long)n[a]);
     }
-    if (n[0] * n[1] * n[2] * (p->phases > 1 ? p->phases : 1) > (1LL << 34)) return fail(DMCR_EINVAL, "field too large");
+    // every axis is <= 2^30 here, so the integer product of three axes and the phase count
+    // could pass 2^63; the element count is compared in floating point (exact below 2^53,
+    // and any value that rounds is far above the bound)
+    if ((double)n[0] * (double)n[1] * (double)n[2] * (double)phases > 0x1p34)
+        return fail(DMCR_EINVAL, "field too large: more than 2^34 elements");
     if (!isfinite(p->level_weight_exp)) return fail(DMCR_EINVAL, "level_weight_exp must be finite");
     const double we = p->level_weight_exp < 0.f ? p->ndim / 2.0 : (double)p->level_weight_exp;
     int tune[4] = {p->tune[0], p->tune[1], p->tune[2], p->tune[3]};

@@ -67,6 +67,12 @@ def test_version_and_lengths(lib):
     (dict(shape=(1 << 18, 1 << 17), window=(1, 1)), 1),   # more than 2^34 elements
     (dict(shape=(1 << 31, 4), window=(1, 1)), 1),         # an axis above 2^30
     (dict(shape=(1 << 17, 1 << 17), window=(128, 1 << 16)), 1),   # a workspace above 2^50 bytes
+    # three axes of 2^30 (and two with 16): the product of the axes passes 2^63 or wraps to
+    # 0 in 64-bit integers; the element count must still be rejected as too large
+    (dict(shape=(1 << 30, 1 << 30, 1 << 30), window=(0, 0, 0)), 1),
+    (dict(shape=(1 << 30, 1 << 30, 16), window=(0, 0, 0)), 1),
+    (dict(shape=(1 << 30, 1 << 30, 1 << 30), window=(1, 1, 1), phases=8), 1),
+    (dict(shape=(1 << 12, 1 << 11, 1 << 11), window=(1, 1, 1), phases=3), 1),   # 2^34 cells x 3 phases
 ])
 def test_argument_validation(lib, kw, status):
     import paper_2103_09686_gb300 as dm
@@ -180,6 +186,32 @@ def test_binding_rejects_wrongly_sized_tensors_before_any_launch(lib, call):
     }
     with pytest.raises(ValueError):
         calls[call]()
+
+
+class _Dev:
+    def __init__(self, index):
+        self.index = index
+
+
+def test_binding_rejects_tensors_on_another_device(lib, monkeypatch):
+    """A tensor on a device other than the current one is rejected on the host: the library
+    launches on the current device and would otherwise receive a foreign pointer."""
+    import torch
+    import paper_2103_09686_gb300 as dm
+    from paper_2103_09686_gb300 import _lib
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    p = dm.Params((32, 24), (4, 3))
+    N, K = 32 * 24, dm.dmcr_descriptor_length(p)
+    here, there = _FakeCudaTensor(N), _FakeCudaTensor(N)
+    here.device, there.device = _Dev(0), _Dev(1)
+    desc = _FakeCudaTensor(K)
+    desc.device = _Dev(0)
+    ws = _FakeCudaTensor(1 << 20)
+    ws.device = _Dev(1)
+    with pytest.raises(ValueError, match="cuda:1"):
+        _lib.dmcr_descriptor(p, there, desc)
+    with pytest.raises(ValueError, match="workspace"):
+        _lib.dmcr_descriptor(p, here, desc, ws)
 
 
 class _Shaped(_FakeCudaTensor):
