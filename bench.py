@@ -568,6 +568,25 @@ def oracle_sample_mp(shape, window, levels, nph, field, budget_s: float, seed: i
             s, K, "x".join(map(str, shape)), nph, q, N1, nph * nph, levels)
 
 
+PIPE_NAMES = ("rcp", "ex2", "tanh", "lg2", "ffma", "ffma2_lanes", "adjoint_pairs", "forward_pairs")
+
+
+def measure_pipe_rates() -> dict:
+    """Measured throughput per SM per clock (libdmcr_pipes.so, csrc/pipes.cu): MUFU rcp /
+    ex2 / tanh / lg2 operations, FFMA, FFMA2 lane operations, and the pair rates of the
+    adjoint's and the forward's per-pair arithmetic held in registers."""
+    import ctypes
+    from paper_2103_09686_gb300 import _build
+    _build.build()
+    lib = ctypes.CDLL(_build.PIPES_LIB)
+    lib.dmcr_bench_pipe_rates.restype = ctypes.c_int
+    r = (ctypes.c_double * 8)()
+    st = lib.dmcr_bench_pipe_rates(r)
+    if st != 0:
+        raise RuntimeError("pipe-rate probe failed with CUDA error %d" % st)
+    return {k: float(r[i]) for i, k in enumerate(PIPE_NAMES)}
+
+
 def cores_used() -> int:
     try:
         return int(os.environ.get("OMP_NUM_THREADS", "")) or os.cpu_count()
@@ -600,13 +619,8 @@ def main():
                     help="Fig. checerboardreconstructions: checkerboards of 64..512 with the multigrid scheme")
     args = ap.parse_args()
     if args.pipes:
-        import ctypes
-        import paper_2103_09686_gb300 as dm
-        lib = dm.load()
-        r = (ctypes.c_double * 5)()
-        st = lib.dmcr_pipe_rates(r)
-        print(json.dumps({"metric": "pipe rates", "unit": "ops/SM/clk", "status": st,
-                          "rcp": r[0], "ex2": r[1], "tanh": r[2], "lg2": r[3], "ffma": r[4]}))
+        rates = measure_pipe_rates()
+        print(json.dumps({"metric": "pipe rates", "unit": "per SM per clock", **rates}))
         return 0
     if args.serve:
         return main_serve(args)

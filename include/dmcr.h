@@ -314,14 +314,6 @@ dmcr_status dmcr_profile_read(int index, char* name, int name_len, double* total
 #define DMCR_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 dmcr_status dmcr_descriptor_noalloc(const dmcr_params* p, const float* field, float* desc, void* stream);
 
-/*
- * dmcr_pipe_rates -- diagnostic: measured throughput, in operations per SM per clock, of
- *   rates[0] MUFU reciprocal, [1] MUFU exp2, [2] MUFU tanh, [3] MUFU log2, [4] FP32 FMA
- *   (independent chains at full occupancy, clock64-timed).  The roofline peaks of the
- *   correlation kernels are derived from these unit rates and the SM count and clock.
- *   SYNCHRONOUS; allocates a few bytes of device memory.  No counterpart in the paper.
- */
-dmcr_status dmcr_pipe_rates(double rates[5]);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,8 @@ What each function follows (sections and equations of the paper):
 * ``loss`` -- Sec. 3.1, Eq. L_func_dMCR: E = ||D - D_des||_2, E_bc with H(0)=0,
   lambda = lambda0 * E.
 * ``loss_grad`` / ``descriptor_vjp`` -- the exact gradient by the chain rule through all
-  levels simultaneously (Sec. 3.1, Sec. 3.3).
+  levels simultaneously (Sec. 3.1, Sec. 3.3); ``vjp_at`` the same gradient at sampled
+  finest positions (gather form, for full-size problems).
 * ``round_field`` -- the rounding used to evaluate a reconstruction (Sec. 4.1): values
   >= 1/2 become phase 1 (the tie goes to phase 1), the rest phase 0.
 * ``adam_step`` / ``reconstruct`` -- Eq. M-update with Adam at the TensorFlow defaults
@@ -350,6 +351,29 @@ def descriptor_vjp(M, p: Params, grad_D) -> np.ndarray:
         gl = level_vjp(pyr[l], p, w[l] * np.asarray(grad_D[l * K:(l + 1) * K], dtype=np.float64))
         g = gl if g is None else gl + prolongate_adjoint(g)
     return g
+
+
+def vjp_at(M, p: Params, grad_D, positions) -> np.ndarray:
+    """``descriptor_vjp`` at sampled finest positions (flat indices), in gather form: the
+    finest position x receives, from every level l, the level-l gradient of its ancestor
+    (coordinates x >> l, the cell that pools x at level l, Sec. 3.3) times 2^{-d l}, the
+    product of the l pooling transposes on the way down (each gives a child 1/2^d of its
+    parent).  O(levels * K_half) pair evaluations per position, so it serves full-size
+    problems where the scatter form of ``descriptor_vjp`` would be too slow."""
+    M = np.asarray(M, dtype=np.float64)
+    d = M.ndim
+    K = half_window(p.ndim, p.window).shape[0]
+    pyr = pyramid(M, p.levels)
+    w = p.weights()
+    coords = np.stack(np.unravel_index(np.asarray(positions, dtype=np.int64), M.shape), axis=1)
+    out = np.zeros(coords.shape[0])
+    for l in range(p.levels):
+        n_l = np.array(pyr[l].shape, dtype=np.int64)
+        anc = coords >> l
+        flat = np.ravel_multi_index(tuple(anc.T), tuple(n_l))
+        G = w[l] * np.asarray(grad_D[l * K:(l + 1) * K], dtype=np.float64)
+        out += level_vjp(pyr[l], p, G, flat) / float(2 ** (d * l))
+    return out
 
 
 def loss_grad(M, D_des, p: Params, mode: str = "norm", lambda0: float | None = None, bc: bool = True):

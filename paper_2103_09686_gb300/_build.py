@@ -12,7 +12,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libdmcr.so")
 BUILD_DIR = os.path.join(PKG, "_build")
-SOURCES = ["corr.cu", "aux.cu", "fft.cu", "gram.cu", "api.cu", "probe.cu"]
+SOURCES = ["corr.cu", "aux.cu", "fft.cu", "gram.cu", "api.cu"]
+# the benchmark's pipe-rate microbenchmark: a library of its own, not part of the C ABI
+PIPES_SRC = "pipes.cu"
+PIPES_LIB = os.path.join(PKG, "libdmcr_pipes.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -42,11 +45,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
     stamp = os.path.join(BUILD_DIR, "stamp")
     dig = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
+    if (not force and os.path.exists(LIB) and os.path.exists(PIPES_LIB) and os.path.exists(stamp)
+            and open(stamp).read() == dig):
         return LIB
     nvcc = _nvcc()
     procs = []
     objs = []
+    pipes_obj = os.path.join(BUILD_DIR, PIPES_SRC.replace(".cu", ".o"))
+    cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, PIPES_SRC), "-o", pipes_obj]
+    procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for src in SOURCES:
         obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
         objs.append(obj)
@@ -63,10 +70,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(out.decode(errors="replace"), file=sys.stderr)
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    for out, ins in ((LIB, objs), (PIPES_LIB, [pipes_obj])):
+        tmp = out + ".tmp.%d" % os.getpid()
+        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *ins])
+        os.replace(tmp, out)
     with open(stamp, "w") as f:
         f.write(dig)
     return LIB

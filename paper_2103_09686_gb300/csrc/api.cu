@@ -1180,18 +1180,14 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
         }
         if (st) break;
         for (int i = 0; i < count; ++i) {
-            dmcr_recon_report& r = reports[i];
-            memset(&r, 0, sizeof(r));
-            r.iterations = (int)(hs[i].adam_step - states[i].step);
-            r.converged = hs[i].done == 1;
-            for (int k = 0; k < DMCR_OUT_COUNT; ++k) r.loss[k] = hs[i].loss[k];
-            r.status = hs[i].err ? DMCR_ETIMEOUT : (hs[i].done == 2 ? DMCR_ENONFINITE : DMCR_OK);
+            memset(&reports[i], 0, sizeof(reports[i]));
+            fill_report(hs[i], states[i].step, &reports[i]);
             states[i].step = hs[i].adam_step;
-            if (hs[i].err && !per_instance_status)
-                st = fail(DMCR_ETIMEOUT, "a bounded tensor-core wait timed out in instance %d", i);
-            else if (hs[i].done == 2 && !per_instance_status)
-                st = fail(DMCR_ENONFINITE, "loss became non-finite in instance %d", i);
         }
+        int bad = 0;
+        st = call_status(hs.data(), count, per_instance_status, &bad);
+        if (st == DMCR_ETIMEOUT) st = fail(st, "a bounded tensor-core wait timed out in instance %d", bad);
+        else if (st == DMCR_ENONFINITE) st = fail(st, "loss became non-finite in instance %d", bad);
         if (st) break;
         // one more evaluation, of the returned fields rounded to phases 0/1 (Sec. 4.1) where
         // asked for: a rounded field goes to its first level's adjoint partials, which no

@@ -211,39 +211,40 @@ __global__ void __launch_bounds__(NPEN_BLOCKS) loss_kernel(const LossSeg* __rest
     const DF t2s = block_sum_df(get(1), sh);
     const DF x2s = block_sum_df(get(2), sh);
     if (threadIdx.x != 0) return;
-    // the scalars in FP32 (FP64 division and square root are slow on this part); the sums
-    // arrive as double-floats, rounded once here
-    const float E2 = e2s.hi + e2s.lo;
-    const float T2 = t2s.hi + t2s.lo;
-    const float ex2 = x2s.hi + x2s.lo;
-    const float N = (float)lp.N;
-    const float lam0 = lp.bc_on ? lp.lambda0 : 0.f;
-    const float E = sqrtf(E2);
-    const float Ebc = ex2 / (N * N);
-    const float phi = lp.mode == 0 ? E : E2;
-    const float lam = lam0 * phi;
-    const float L = phi + lam * Ebc;
-    const float rel = T2 > 0.f ? E / sqrtf(T2) : INFINITY;
-    const float out[6] = {E, E2, Ebc, lam, L, rel};
+    // the scalars in FP64 on this one thread (a few dozen FP64 operations once per
+    // evaluation): the double-float sums keep about 48 bits, and the square roots and
+    // quotients below keep them, so E, rel_err and L reach the output rounded once to FP32
+    const double E2 = (double)e2s.hi + (double)e2s.lo;
+    const double T2 = (double)t2s.hi + (double)t2s.lo;
+    const double ex2 = (double)x2s.hi + (double)x2s.lo;
+    const double N = (double)lp.N;
+    const double lam0 = lp.bc_on ? (double)lp.lambda0 : 0.0;
+    const double E = sqrt(E2);
+    const double Ebc = ex2 / (N * N);
+    const double phi = lp.mode == 0 ? E : E2;
+    const double lam = lam0 * phi;
+    const double L = phi + lam * Ebc;
+    const double rel = T2 > 0.0 ? E / sqrt(T2) : (double)INFINITY;
+    const float out[6] = {(float)E, (float)E2, (float)Ebc, (float)lam, (float)L, (float)rel};
     for (int i = 0; i < 6; ++i) sc->loss[i] = out[i];
     if (loss_out != nullptr)
         for (int i = 0; i < 6; ++i) loss_out[i] = out[i];
     // dL/dD = phi'(E) (1 + lam0 E_bc) dE/dD ;  dL/dM (penalty) = lam0 phi dE_bc/dM
-    float gs;
-    if (lp.mode == 0) gs = E > 0.f ? (1.f + lam0 * Ebc) / E : 0.f;
-    else gs = 2.f * (1.f + lam0 * Ebc);
-    sc->gscale = gs;
-    sc->pen_coef = 2.f * lam0 * phi / (N * N);
+    double gs;
+    if (lp.mode == 0) gs = E > 0.0 ? (1.0 + lam0 * Ebc) / E : 0.0;
+    else gs = 2.0 * (1.0 + lam0 * Ebc);
+    sc->gscale = (float)gs;
+    sc->pen_coef = (float)(2.0 * lam0 * phi / (N * N));
     if (!lp.recon) return;
     const int it = sc->iter;
     if (history != nullptr && it < lp.max_iters) {
-        history[3 * it + 0] = E;
-        history[3 * it + 1] = L;
-        history[3 * it + 2] = rel;
+        history[3 * it + 0] = out[0];
+        history[3 * it + 1] = out[4];
+        history[3 * it + 2] = out[5];
     }
     sc->iter = it + 1;
-    if (!isfinite(L)) { sc->done = 2; return; }
-    if (lp.tol_rel > 0.f && (it % lp.check_every) == 0 && rel < lp.tol_rel) { sc->done = 1; return; }
+    if (!isfinite(out[4])) { sc->done = 2; return; }
+    if (lp.tol_rel > 0.f && (it % lp.check_every) == 0 && out[5] < lp.tol_rel) { sc->done = 1; return; }
     if (it + 1 > lp.max_iters) { sc->done = 3; return; }
     sc->adam_step = sc->adam_step + 1;
     // beta^t products stay FP64: they are multiplied once per step over many steps
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(NPEN_BLOCKS) loss_kernel(const LossSeg* __rest
     const double b2t = sc->b2t * (double)lp.beta2;
     sc->b1t = b1t;
     sc->b2t = b2t;
-    sc->lr_t = lp.lr * sqrtf((float)(1.0 - b2t)) / (float)(1.0 - b1t);
+    sc->lr_t = (float)((double)lp.lr * sqrt(1.0 - b2t) / (1.0 - b1t));
 }
 
 void launch_loss(const LossSeg* segs, int nseg, cudaStream_t s) {

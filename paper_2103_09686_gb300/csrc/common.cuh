@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "scalars.h"
+
 namespace dmcr {
 
 constexpr int T = 8;            // shifts per thread (forward) / positions per strip (adjoint)
@@ -93,19 +95,6 @@ struct ThreshConst {
     float lim;       // product form when |kappa M| <= lim everywhere in a block
     float beta;      // c3 / c1: f = c1 (s + beta)
     int identity;    // f(x) = x
-};
-
-// Device-side scalars of one evaluation / reconstruction.
-struct Scalars {
-    float loss[6];        // E, E2, Ebc, lambda, L, rel_err
-    float gscale;         // dL/dD = gscale * rho
-    float pen_coef;       // penalty gradient coefficient: pen_coef * ex * dex
-    float lr_t;           // Adam step size of the current iteration
-    int done;             // 0 running, 1 converged, 2 non-finite loss
-    int iter;             // iterations evaluated in this call
-    int64_t adam_step;    // Adam steps taken (global, for bias correction)
-    double b1t, b2t;      // beta1^adam_step, beta2^adam_step (running products)
-    int err;              // set when a bounded tensor-core wait timed out
 };
 
 struct LossParams {

@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(GemmShape<BN>::THREADS, 1) tc_gemm_kernel(cons
     uint64_t* empty = full + GSTAGES;
     uint64_t* tfull = empty + GSTAGES;
     uint64_t* tempty = tfull + 2;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint64_t* mdone = tempty + 2;   // every MMA of this CTA finished (the last commit)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tilesM = g.M / GM, tilesN = g.N / GN;
     int bm, bn;
@@ -272,6 +273,7 @@ __global__ void __launch_bounds__(GemmShape<BN>::THREADS, 1) tc_gemm_kernel(cons
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], EPI_WARPS * 32);
         }
+        mbar_init(mdone, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == EPI_WARPS + 1) tmem_alloc(tslot, TMEM_COLS);
@@ -286,6 +288,7 @@ __global__ void __launch_bounds__(GemmShape<BN>::THREADS, 1) tc_gemm_kernel(cons
     if (warp == EPI_WARPS) {
         // ---- TMA producer
         if (lane == 0) {
+            int issued = 0;   // stages whose copies were started
             for (int kb = 0; kb < nk; ++kb) {
                 const int s = kb % GSTAGES;
                 if (kb >= GSTAGES) ok = mbar_wait(&empty[s], ((kb / GSTAGES) - 1) & 1);
@@ -297,10 +300,14 @@ __global__ void __launch_bounds__(GemmShape<BN>::THREADS, 1) tc_gemm_kernel(cons
                 tma_load_2d(st + A_TILE, &g.ta_lo, k0, bm * GM, &full[s]);
                 tma_load_2d(st + 2 * A_TILE, &g.tb_hi, k0, bn * GN, &full[s]);
                 tma_load_2d(st + 2 * A_TILE + B_TILE, &g.tb_lo, k0, bn * GN, &full[s]);
+                issued = kb + 1;
             }
-            // no copy may still be in flight at exit: the last stages' bytes have landed
-            for (int kb = nk > GSTAGES ? nk - GSTAGES : 0; kb < nk; ++kb)
-                mbar_wait(&full[kb % GSTAGES], (kb / GSTAGES) & 1);
+            // no copy of this CTA may still be in flight when it exits, after a give-up as
+            // well: wait (bounded) for the bytes of the stages it actually started.  Each
+            // stage's barrier has begun no phase after the one waited on here, so the
+            // parity is unambiguous.
+            for (int kb = issued > GSTAGES ? issued - GSTAGES : 0; kb < issued; ++kb)
+                if (!mbar_wait(&full[kb % GSTAGES], (kb / GSTAGES) & 1)) ok = false;
         }
         __syncwarp();
     } else if (warp == EPI_WARPS + 1) {
@@ -332,6 +339,11 @@ __global__ void __launch_bounds__(GemmShape<BN>::THREADS, 1) tc_gemm_kernel(cons
                 mma_commit(&empty[s]);
                 if (kb % FLUSH == FLUSH - 1 || kb == nk - 1) mma_commit(&tfull[buf]);
             }
+            // TMEM is freed below: first every MMA issued above (all of them, also after a
+            // give-up of this thread or of another role) must have finished writing it.  A
+            // commit tracks every earlier tcgen05 operation of this thread.
+            mma_commit(mdone);
+            if (!mbar_wait(mdone, 0)) ok = false;
         }
         __syncwarp();
     } else {
@@ -387,6 +399,8 @@ __global__ void __launch_bounds__(GemmShape<BN>::THREADS, 1) tc_gemm_kernel(cons
         }
     }
     if (!ok && g.err != nullptr) atomicExch(g.err, 1);
+    // the MMA issuer reaches this barrier only after its last commit arrived (or its bounded
+    // wait for it ran out), and the epilogue warps after their last TMEM read
     tc_fence_before();
     __syncthreads();
     if (warp == EPI_WARPS + 1) tmem_dealloc(tmem, TMEM_COLS);

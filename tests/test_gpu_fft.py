@@ -60,7 +60,7 @@ def test_fft_equals_direct_identity(cuda_lib):
         out[path] = (d, *dm.loss_grad(M, d, p))
     (d1, l1, g1), (d2, l2, g2) = out[dm.DMCR_PATH_DIRECT], out[dm.DMCR_PATH_FFT]
     np.testing.assert_allclose(d2.cpu().numpy(), d1.cpu().numpy(), rtol=1e-5, atol=1e-9)
-    np.testing.assert_allclose(l2.cpu().numpy(), l1.cpu().numpy(), rtol=1e-4)
+    np.testing.assert_allclose(l2.cpu().numpy(), l1.cpu().numpy(), rtol=1e-5)
     assert float(torch.linalg.norm(g2 - g1) / torch.linalg.norm(g1)) < 1e-5
 
 

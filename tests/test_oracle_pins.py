@@ -328,6 +328,36 @@ def test_vjp_linear_in_upstream_and_sampled_positions():
     assert abs(np.dot(G1, Jv) - np.sum(g1 * v)) < 1e-7 * (1 + abs(np.dot(G1, Jv)))
 
 
+@pytest.mark.parametrize("case", ["2d_3lev", "3d_2lev", "2d_identity_2lev"])
+def test_sampled_gather_vjp_through_every_level(case):
+    """``vjp_at`` (the gradient through every level at sampled finest positions, Sec. 3.3)
+    against FP64 central differences of <G, D(M)> at those positions, and against the
+    scatter form ``descriptor_vjp`` at every position."""
+    rng = np.random.default_rng(31)
+    if case == "2d_3lev":
+        p = oracle.Params(ndim=2, window=(2, 3), levels=3)
+        M = rng.uniform(-0.2, 1.2, (16, 24))
+    elif case == "3d_2lev":
+        p = oracle.Params(ndim=3, window=(1, 2, 1), levels=2)
+        M = rng.uniform(-0.2, 1.2, (4, 8, 6))
+    else:
+        p = oracle.Params(ndim=2, window=(3, 1), levels=2, threshold="identity")
+        M = rng.uniform(-0.2, 1.2, (12, 8))
+    G = rng.standard_normal(oracle.descriptor(M, p).size)
+    pos = rng.choice(M.size, size=10, replace=False)
+    got = oracle.vjp_at(M, p, G, pos)
+    h = 1e-5
+    fd = np.zeros(pos.size)
+    for i, q in enumerate(pos):
+        e = np.zeros(M.size)
+        e[q] = h
+        fd[i] = (np.dot(G, oracle.descriptor(M + e.reshape(M.shape), p)) -
+                 np.dot(G, oracle.descriptor(M - e.reshape(M.shape), p))) / (2 * h)
+    assert np.linalg.norm(got - fd) / np.linalg.norm(fd) < 1e-7
+    full = oracle.descriptor_vjp(M, p, G).ravel()
+    np.testing.assert_allclose(oracle.vjp_at(M, p, G, np.arange(M.size)), full, rtol=1e-12, atol=1e-15)
+
+
 # --------------------------------------------------------------------------- optimiser
 
 def test_adam_constant_gradient_steps_by_lr():
