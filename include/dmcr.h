@@ -89,7 +89,7 @@ typedef struct {
     float alpha;             /* soft-threshold slope; the paper uses 10 */
     float level_weight_exp;  /* w_l = 2^(level_weight_exp (l-1)); <0 selects ndim/2 (2^(l-1) in 2-D); must be finite */
     int path;                /* DMCR_PATH_AUTO, DMCR_PATH_DIRECT or DMCR_PATH_FFT */
-    int tune[4];             /* launch shape (0 = built-in choice): forward tile rows {8,16,32},
+    int tune[4];             /* launch shape (0 = built-in choice): forward tile rows {2,4,8,16,32},
                                 adjoint ry rows per shift chunk (1..16), adjoint chunk target
                                 limit (1..64), adjoint rx blocks of 8 shifts per chunk at most
                                 (1..32).  Results agree to rounding across shapes. */

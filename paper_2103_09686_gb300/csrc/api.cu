@@ -184,11 +184,18 @@ int64_t gd_floats(const LevelGeom& g) { return (int64_t)(2 * g.P[0] + 1) * (2 * 
 
 // Forward tile rows for the whole problem (all levels share one fused launch): the tallest
 // tile (fewest halo rows per output row) that still gives ~8 blocks per SM summed over levels.
+// A small forward (below 2^24 pair evaluations, where the launch is latency bound) may go down
+// to tiles of 4 or 2 rows: more blocks, at the price of taller halos relative to the tile.
 int forward_rows(const int64_t n[3], const int P[3], int levels, int ndim) {
     const int64_t groups = ceil_div(
         (int64_t)(P[1] + 1) * ceil_div(2 * P[2] + 1, T) + (int64_t)P[0] * (2 * P[1] + 1) * ceil_div(2 * P[2] + 1, T),
         FWD_THREADS);
-    for (int TY = 32; TY > 8; TY /= 2) {
+    int64_t pairs = 0;
+    const int64_t khalf = ((int64_t)(2 * P[0] + 1) * (2 * P[1] + 1) * (2 * P[2] + 1) + 1) / 2;
+    for (int l = 0; l < levels; ++l)
+        pairs += (ndim == 2 ? 1 : n[0] >> l) * (n[1] >> l) * (n[2] >> l) * khalf;
+    const int smallest = pairs < (1LL << 24) ? 2 : 8;
+    for (int TY = 32; TY > smallest; TY /= 2) {
         int64_t blocks = 0;
         for (int l = 0; l < levels; ++l) {
             const int64_t n0 = ndim == 2 ? 1 : n[0] >> l;
@@ -196,13 +203,13 @@ int forward_rows(const int64_t n[3], const int P[3], int levels, int ndim) {
         }
         if (blocks >= 1216) return TY;
     }
-    return 8;
+    return smallest;
 }
 
 // tune: {forward tile rows (8/16/32; 0 is taken as forward_rows()), adjoint ry rows per
 // chunk (0 = auto, else 1..16), adjoint chunk target limit (0 = auto, else 1..64), adjoint rx
 // blocks of 8 shifts per chunk at most (0 = auto, else 1..32)}
-void plan_level(LevelGeom& g, const int tune[4]) {
+void plan_level(LevelGeom& g, const int tune[4], int phases) {
     g.N = g.n[0] * g.n[1] * g.n[2];
     g.NB = (int)ceil_div(2 * g.P[2] + 1, T);
     g.NG = (int64_t)(g.P[1] + 1) * g.NB + (int64_t)g.P[0] * (2 * g.P[1] + 1) * g.NB;
@@ -240,20 +247,35 @@ void plan_level(LevelGeom& g, const int tune[4]) {
     g.NBc = (int)ceil_div(g.NB, g.nXc);
     int cap = 16;
     while (cap > 1) {
-        g.RY = cap;
+        g.RYS = cap;
         if (adj_smem_bytes(g) <= 56 * 1024) break;
         --cap;
     }
-    const int64_t chunk_cap = tune[2] > 0 ? tune[2] : 32;
+    // a level of fewer than 8 tiles (a small field) may take up to 64 chunks
+    const int64_t chunk_cap = tune[2] > 0 ? tune[2] : (g.adjTiles < 8 ? 64 : 32);
     const int64_t want = std::min<int64_t>(chunk_cap, std::max<int64_t>(1, ceil_div(rows_target, g.adjTiles)));
     const int64_t perX = ceil_div(want, (int64_t)g.nXc);
     const int nZc = (int)std::min<int64_t>(wz, perX);
     g.RY = (int)std::min<int64_t>(ceil_div(wy, ceil_div(perX, nZc)), cap);
     if (tune[1] > 0) g.RY = std::min(tune[1], cap);
+    // several phase fields: every ordered pair is a segment of the same launch, so a chunk
+    // can cover up to phases^2 times as many ry rows (staged in rounds of at most `cap`
+    // rows): fewer chunks, and phases^2 times fewer adjoint partials to write and read back
+    if (phases > 1 && tune[1] == 0) g.RY = std::min<int64_t>((int64_t)g.RY * phases * phases, wy);
     g.RY = std::min(g.RY, wy);
+    g.RYS = std::min(g.RY, cap);
     g.nYc = (int)ceil_div(wy, g.RY);
     g.RZ = (int)ceil_div(wz, nZc);
     g.nZc = (int)ceil_div(wz, g.RZ);
+    // a small field (fewer than 8 tiles) whose rz and ry splits fall short of the chunk
+    // target splits the rx blocks further
+    if (tune[3] == 0 && g.adjTiles < 8 && (int64_t)g.nZc * g.nYc * g.nXc < want && g.NB > g.nXc) {
+        const int nx = (int)std::min<int64_t>(g.NB, ceil_div(want, (int64_t)g.nZc * g.nYc));
+        if (nx > g.nXc) {
+            g.NBc = (int)ceil_div(g.NB, nx);
+            g.nXc = (int)ceil_div(g.NB, g.NBc);
+        }
+    }
     g.nChunks = g.nZc * g.nYc * g.nXc;
 }
 
@@ -266,9 +288,10 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
         return fail(DMCR_EINVAL, "unknown threshold %d", p->threshold);
     if (p->path != DMCR_PATH_AUTO && p->path != DMCR_PATH_DIRECT && p->path != DMCR_PATH_FFT)
         return fail(DMCR_EINVAL, "unknown path %d", p->path);
-    if (!(p->tune[0] == 0 || p->tune[0] == 8 || p->tune[0] == 16 || p->tune[0] == 32) || p->tune[1] < 0 ||
+    if (!(p->tune[0] == 0 || p->tune[0] == 2 || p->tune[0] == 4 || p->tune[0] == 8 || p->tune[0] == 16 ||
+          p->tune[0] == 32) || p->tune[1] < 0 ||
         p->tune[1] > 16 || p->tune[2] < 0 || p->tune[2] > 64 || p->tune[3] < 0 || p->tune[3] > 32)
-        return fail(DMCR_EINVAL, "tune = {0|8|16|32, 0..16, 0..64, 0..32} expected");
+        return fail(DMCR_EINVAL, "tune = {0|2|4|8|16|32, 0..16, 0..64, 0..32} expected");
     if (p->threshold == DMCR_SOFT && !(p->alpha > 0.f && isfinite(p->alpha)))
         return fail(DMCR_EINVAL, "alpha must be positive and finite");
     if (p->descriptor != DMCR_DESC_S2 && p->descriptor != DMCR_DESC_S3 && p->descriptor != DMCR_DESC_S2_TILDE)
@@ -325,7 +348,7 @@ dmcr_status validate_and_plan(const dmcr_params* p, Plan& pl) {
             if (2LL * P[a] > g.n[a])
                 return fail(DMCR_EINVAL, "window %d exceeds half the level-%d size %lld on axis %d", P[a], l + 1,
                             (long long)g.n[a], a - first);
-        plan_level(g, tune);
+        plan_level(g, tune, phases);
         const bool fft_sizes = fft_size_ok(g.n[0]) && fft_size_ok(g.n[1]) && fft_size_ok(g.n[2]);
         if (p->path == DMCR_PATH_FFT) {
             if (!fft_sizes)
@@ -938,17 +961,21 @@ void fft_twiddles(const Prepared::FftJob& j, cudaStream_t s) {
     }
 }
 
+// X = DFT(M) stays in the workspace; the power spectrum and its inverse go to H
 void fft_descriptor(const Prepared::FftJob& j, cudaStream_t s) {
     fft_twiddles(j, s);
     fft_grid(j, j.X, j.field, -1, s);
-    launch_fft_power(j.X, j.g.N, s);
-    fft_grid(j, j.X, nullptr, +1, s);
-    launch_fft_sample(j.g, j.X, j.weight, j.mode, j.fh2, j.desc, s);
+    launch_fft_power(j.X, j.H, j.g.N, s);
+    fft_grid(j, j.H, nullptr, +1, s);
+    launch_fft_sample(j.g, j.H, j.weight, j.mode, j.fh2, j.desc, s);
 }
 
-void fft_vjp(const Prepared::FftJob& j, cudaStream_t s) {
-    fft_twiddles(j, s);
-    fft_grid(j, j.X, j.field, -1, s);
+// x_ready: the descriptor of the same call left X = DFT(M) (and the twiddles) in place
+void fft_vjp(const Prepared::FftJob& j, bool x_ready, cudaStream_t s) {
+    if (!x_ready) {
+        fft_twiddles(j, s);
+        fft_grid(j, j.X, j.field, -1, s);
+    }
     launch_fft_embed(j.g, j.Gd, j.H, s);
     fft_grid(j, j.H, nullptr, -1, s);
     launch_fft_dc(j.H, j.dc, s);
@@ -1017,7 +1044,7 @@ void run(const Prepared& P, cudaStream_t s) {
         }
         if (!P.fftb.empty()) {
             ProfScope ps("fft_vjp", -1, s);
-            for (const Prepared::FftJob& j : P.fftb) fft_vjp(j, s);
+            for (const Prepared::FftJob& j : P.fftb) fft_vjp(j, (P.flags & F_FWD) != 0, s);
         }
         if (!P.s3b.empty()) {
             ProfScope ps("s3_adjoint", -1, s);
@@ -1266,6 +1293,153 @@ void recon_inst(Inst& x, const dmcr_recon_opts* o, const float* target, float* f
     x.step = st->step;
 }
 
+// ---------------------------------------------------------------------------- cached iteration graphs
+//
+// dmcr_adam_step(_batched) is called once per iteration with the same arguments over and
+// over; for small problems its ten launches, the planning and the table building cost more
+// than the arithmetic.  The first call with a given set of arguments therefore captures the
+// iteration (table upload + every kernel) into a CUDA graph on a private stream and keeps
+// the instantiated graph; a later call with the same arguments launches one small kernel
+// that sets the Adam step scalars of this call (passed by value) and the graph.  The key is
+// every argument that shapes the launch sequence or that the tables point to: the params
+// and options field by field, all pointers, the workspace size and the device.  Calls made
+// while the stream is being captured by the caller, or while the library's per-kernel
+// timers are on, take the direct launches.
+struct KeyBuf {
+    std::string b;
+    template <typename V>
+    void add(const V& v) { b.append(reinterpret_cast<const char*>(&v), sizeof(V)); }
+};
+
+void key_params(KeyBuf& k, const dmcr_params& p) {
+    k.add(p.ndim);
+    for (int a = 0; a < 3; ++a) k.add(p.n[a]), k.add(p.window[a]);
+    k.add(p.levels), k.add(p.threshold), k.add(p.alpha), k.add(p.level_weight_exp), k.add(p.path);
+    for (int a = 0; a < 4; ++a) k.add(p.tune[a]);
+    k.add(p.descriptor), k.add(p.phases);
+}
+
+void key_adam_opts(KeyBuf& k, const dmcr_recon_opts& o) {
+    k.add(o.lr), k.add(o.beta1), k.add(o.beta2), k.add(o.eps), k.add(o.loss.mode), k.add(o.loss.lambda0),
+        k.add(o.loss.bc_on);
+}
+
+struct StepGraph {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<Scalars*> sc;       // per instance
+    float beta1 = 0.9f, beta2 = 0.999f;
+    uint64_t used = 0;
+};
+
+constexpr size_t GRAPH_CACHE = 16;
+std::mutex g_graph_mu;
+// never freed: the graphs live until the process exits (a destructor at exit could run
+// after the CUDA context is gone)
+std::vector<StepGraph>& graph_cache() {
+    static std::vector<StepGraph>* c = new std::vector<StepGraph>();
+    return *c;
+}
+uint64_t g_graph_clock = 0;
+
+bool graphs_usable(cudaStream_t s) {
+    {
+        ProfState& p = prof();
+        std::lock_guard<std::mutex> lk(p.mu);
+        if (p.on) return false;        // per-kernel event timers need the direct launches
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusNone;
+}
+
+// Launch the cached graph of `key` for Adam steps steps[i] + 1; false if there is none.
+bool replay_step_graph(const std::string& key, const int64_t* steps, cudaStream_t s, dmcr_status* st) {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<InitSeg> init;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (StepGraph& g : graph_cache())
+            if (g.key == key) {
+                exec = g.exec;
+                g.used = ++g_graph_clock;
+                for (size_t i = 0; i < g.sc.size(); ++i)
+                    init.push_back({g.sc[i], steps[i], pow((double)g.beta1, (double)steps[i]),
+                                    pow((double)g.beta2, (double)steps[i])});
+                break;
+            }
+    }
+    if (exec == nullptr) return false;
+    launch_scalars_set(init.data(), (int)init.size(), s);
+    *st = cuda_check(cudaGetLastError(), "scalars set");
+    if (*st == DMCR_OK) *st = cuda_check(cudaGraphLaunch(exec, s), "cudaGraphLaunch (cached iteration)");
+    return true;
+}
+
+// Capture the prepared iteration (tables + kernels, no scalar initialisation) into a graph
+// and store it under `key`.  Returns false (and leaves no error pending) if anything fails.
+bool capture_step_graph(const std::string& key, const Prepared& P, const std::vector<Inst>& in) {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        upload(P, cs);
+        run(P, cs);
+        ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && graph != nullptr;
+    }
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    cudaGetLastError();
+    if (!ok) {
+        if (exec) cudaGraphExecDestroy(exec);
+        return false;
+    }
+    StepGraph g;
+    g.key = key;
+    g.exec = exec;
+    for (const Inst& x : in) g.sc.push_back(x.sc);
+    g.beta1 = in[0].beta1;
+    g.beta2 = in[0].beta2;
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    std::vector<StepGraph>& c = graph_cache();
+    g.used = ++g_graph_clock;
+    if (c.size() >= GRAPH_CACHE) {
+        auto lru = std::min_element(c.begin(), c.end(), [](const StepGraph& a, const StepGraph& b) { return a.used < b.used; });
+        cudaGraphExecDestroy(lru->exec);
+        *lru = g;
+    } else {
+        c.push_back(g);
+    }
+    return true;
+}
+
+// One Adam iteration of the instances: from the cache when possible, else prepared here
+// (and captured for the next call when graphs are usable).
+dmcr_status adam_iteration(const std::string& key, std::vector<Inst>& in, char* tab, size_t tab_cap,
+                           cudaStream_t s, const char* what) {
+    const bool graphs = graphs_usable(s);
+    std::vector<int64_t> steps;
+    for (const Inst& x : in) steps.push_back(x.step);
+    dmcr_status st = DMCR_OK;
+    if (graphs && replay_step_graph(key, steps.data(), s, &st)) return st;
+    if (graphs) {
+        Prepared P;
+        DMCR_TRY(prepare(in, F_FWD | F_LOSS | F_BACK | F_ADAM, tab, tab_cap, P));
+        if (capture_step_graph(key, P, in) && replay_step_graph(key, steps.data(), s, &st)) return st;
+    }
+    Prepared P;
+    DMCR_TRY(prepare(in, F_INIT | F_FWD | F_LOSS | F_BACK | F_ADAM, tab, tab_cap, P));
+    upload(P, s);
+    run(P, s);
+    return cuda_check(cudaGetLastError(), what);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------- C ABI
@@ -1376,23 +1550,36 @@ dmcr_status dmcr_init_uniform(float* field, int64_t count, uint64_t seed, void* 
 
 dmcr_status dmcr_adam_step(const dmcr_params* p, const dmcr_recon_opts* o, const float* target_desc, float* field,
                            dmcr_adam_state* state, float* loss_out, void* ws, size_t ws_bytes, void* stream) {
+    if (p == nullptr || o == nullptr || target_desc == nullptr || field == nullptr || state == nullptr ||
+        state->m == nullptr || state->v == nullptr)
+        return fail(DMCR_EINVAL, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    DMCR_TRY(cuda_check(cudaGetDevice(&dev), "cudaGetDevice"));
+    KeyBuf k;
+    k.add(dev);
+    k.add(1);
+    key_params(k, *p);
+    key_adam_opts(k, *o);
+    k.add(target_desc), k.add(field), k.add(state->m), k.add(state->v), k.add(loss_out), k.add(ws), k.add(ws_bytes);
+    dmcr_status st = DMCR_OK;
+    if (graphs_usable(s) && replay_step_graph(k.b, &state->step, s, &st)) {
+        if (st == DMCR_OK) state->step += 1;
+        return st;
+    }
     Plan pl;
     DMCR_TRY(validate_and_plan(p, pl));
-    if (o == nullptr || target_desc == nullptr || field == nullptr || state == nullptr || state->m == nullptr ||
-        state->v == nullptr)
-        return fail(DMCR_EINVAL, "NULL argument");
     DMCR_TRY(check_loss_opts(&o->loss));
     DMCR_TRY(check_ws(pl, ws, ws_bytes));
     DMCR_TRY(prepare_device());
-    Inst x = single(pl, ws);
+    std::vector<Inst> in{single(pl, ws)};
     dmcr_recon_opts one = *o;
     one.max_iters = 1;
     one.tol_rel = 0.f;
     one.check_every = 1;
-    recon_inst(x, &one, target_desc, field, state, nullptr);
-    x.loss_out = loss_out;
-    DMCR_TRY(exec_single(x, F_INIT | F_FWD | F_LOSS | F_BACK | F_ADAM, static_cast<cudaStream_t>(stream),
-                         "dmcr_adam_step launch"));
+    recon_inst(in[0], &one, target_desc, field, state, nullptr);
+    in[0].loss_out = loss_out;
+    DMCR_TRY(adam_iteration(k.b, in, table_region(pl, ws), pl.tab_bytes, s, "dmcr_adam_step launch"));
     state->step += 1;
     return DMCR_OK;
 }
@@ -1490,10 +1677,34 @@ dmcr_status dmcr_descriptor_vjp_batched(int count, const dmcr_params* params, co
 dmcr_status dmcr_adam_step_batched(int count, const dmcr_params* params, const dmcr_recon_opts* opts,
                                    const float* const* targets, float* const* fields, dmcr_adam_state* states,
                                    float* loss_out, void* ws, size_t ws_bytes, void* stream) {
+    if (count < 1) return fail(DMCR_EINVAL, "count must be >= 1");
+    if (params == nullptr || opts == nullptr || targets == nullptr || fields == nullptr || states == nullptr)
+        return fail(DMCR_EINVAL, "NULL argument");
+    for (int i = 0; i < count; ++i)
+        if (targets[i] == nullptr || fields[i] == nullptr || states[i].m == nullptr || states[i].v == nullptr)
+            return fail(DMCR_EINVAL, "NULL pointer in instance %d", i);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    DMCR_TRY(cuda_check(cudaGetDevice(&dev), "cudaGetDevice"));
+    KeyBuf k;
+    k.add(dev);
+    k.add(count);
+    key_adam_opts(k, *opts);
+    for (int i = 0; i < count; ++i) {
+        key_params(k, params[i]);
+        k.add(targets[i]), k.add(fields[i]), k.add(states[i].m), k.add(states[i].v);
+    }
+    k.add(loss_out), k.add(ws), k.add(ws_bytes);
+    std::vector<int64_t> steps(count);
+    for (int i = 0; i < count; ++i) steps[i] = states[i].step;
+    dmcr_status st = DMCR_OK;
+    if (graphs_usable(s) && replay_step_graph(k.b, steps.data(), s, &st)) {
+        if (st == DMCR_OK)
+            for (int i = 0; i < count; ++i) states[i].step += 1;
+        return st;
+    }
     BatchLayout B;
     DMCR_TRY(batch_layout(count, params, B));
-    if (opts == nullptr || targets == nullptr || fields == nullptr || states == nullptr)
-        return fail(DMCR_EINVAL, "NULL argument");
     DMCR_TRY(check_loss_opts(&opts->loss));
     DMCR_TRY(batch_ws(B, ws, ws_bytes));
     DMCR_TRY(prepare_device());
@@ -1503,13 +1714,11 @@ dmcr_status dmcr_adam_step_batched(int count, const dmcr_params* params, const d
     one.tol_rel = 0.f;
     one.check_every = 1;
     for (int i = 0; i < count; ++i) {
-        if (targets[i] == nullptr || fields[i] == nullptr || states[i].m == nullptr || states[i].v == nullptr)
-            return fail(DMCR_EINVAL, "NULL pointer in instance %d", i);
         recon_inst(in[i], &one, targets[i], fields[i], &states[i], nullptr);
         in[i].loss_out = loss_out != nullptr ? loss_out + (size_t)DMCR_OUT_COUNT * i : nullptr;
     }
-    DMCR_TRY(exec_batch(B, ws, in, F_INIT | F_FWD | F_LOSS | F_BACK | F_ADAM, static_cast<cudaStream_t>(stream),
-                        "dmcr_adam_step_batched launch"));
+    DMCR_TRY(adam_iteration(k.b, in, static_cast<char*>(ws) + B.o_tab, B.tab_bytes, s,
+                            "dmcr_adam_step_batched launch"));
     for (int i = 0; i < count; ++i) states[i].step += 1;
     return DMCR_OK;
 }

@@ -317,25 +317,54 @@ void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, cudaStream_t s
     final_kernel<<<(unsigned)blocks, ELEM_TH, 0, s>>>(segs, nseg);
 }
 
-__global__ void scalars_init_kernel(const InitSeg* __restrict__ segs, int nseg) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nseg) return;
-    Scalars* sc = segs[i].sc;
+__device__ __forceinline__ void scalars_init_one(const InitSeg& g) {
+    Scalars* sc = g.sc;
     for (int k = 0; k < 6; ++k) sc->loss[k] = 0.f;
     sc->gscale = 0.f;
     sc->pen_coef = 0.f;
     sc->lr_t = 0.f;
     sc->done = 0;
     sc->iter = 0;
-    sc->adam_step = segs[i].step;
-    sc->b1t = segs[i].b1t;
-    sc->b2t = segs[i].b2t;
+    sc->adam_step = g.step;
+    sc->b1t = g.b1t;
+    sc->b2t = g.b2t;
     sc->err = 0;
+}
+
+__global__ void scalars_init_kernel(const InitSeg* __restrict__ segs, int nseg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nseg) return;
+    scalars_init_one(segs[i]);
 }
 
 void launch_scalars_init(const InitSeg* segs, int nseg, cudaStream_t s) {
     if (nseg <= 0) return;
     scalars_init_kernel<<<(nseg + 127) / 128, 128, 0, s>>>(segs, nseg);
+}
+
+// The same initialisation with the segments passed by value (no table in device memory):
+// used before a replay of a cached iteration graph, whose captured tables cannot carry the
+// Adam step count of the current call.
+constexpr int SET_MAX = 960;
+struct InitBatch {
+    int n;
+    InitSeg seg[SET_MAX];
+};
+
+__global__ void scalars_set_kernel(const InitBatch b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n) return;
+    scalars_init_one(b.seg[i]);
+}
+
+void launch_scalars_set(const InitSeg* segs, int nseg, cudaStream_t s) {
+    static thread_local InitBatch b;
+    for (int off = 0; off < nseg; off += SET_MAX) {
+        const int k = nseg - off < SET_MAX ? nseg - off : SET_MAX;
+        b.n = k;
+        memcpy(b.seg, segs + off, (size_t)k * sizeof(InitSeg));
+        scalars_set_kernel<<<(k + 127) / 128, 128, 0, s>>>(b);
+    }
 }
 
 // Writes up to BLOB_BYTES of host data, passed by value as a kernel parameter, to device

@@ -79,6 +79,7 @@ struct LevelGeom {
     int adjTilesY, adjTilesX;
     int64_t adjTiles;  // n[0] * adjTilesY * adjTilesX
     int nZc, nYc, RZ, RY;   // shift chunks over rz and ry
+    int RYS;                // ry rows staged in shared memory at a time (RY may be larger: rounds)
     int nXc, NBc;           // shift chunks over the rx blocks: NBc blocks of T per chunk
     int nChunks;
     int fft;          // 1: this level runs on the FFT path (identity threshold / binary target)
@@ -282,6 +283,7 @@ void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, cudaStream_t s
 void launch_init_uniform(float* field, int64_t count, uint64_t seed, cudaStream_t s);
 void launch_round_field(const float* src, float* dst, int64_t count, cudaStream_t s);
 void launch_scalars_init(const InitSeg* segs, int nseg, cudaStream_t s);
+void launch_scalars_set(const InitSeg* host_segs, int nseg, cudaStream_t s);   // segments by value
 void set_kernel_attributes();
 void set_gram_attributes();
 size_t gemm_smem_bytes();
@@ -293,7 +295,7 @@ size_t fft_smem_bytes(int len, int L);
 int fft_lines_per_block(int len);
 void launch_fft_pass(const FftPass& p, cudaStream_t s);
 void launch_fft_twiddles(double2* tw, int len, cudaStream_t s);
-void launch_fft_power(double2* X, int64_t N, cudaStream_t s);
+void launch_fft_power(const double2* X, double2* P, int64_t N, cudaStream_t s);
 void launch_fft_xcorr(const double2* X, double2* H, int64_t N, cudaStream_t s);
 void launch_fft_sample(const LevelGeom& g, const double2* X, float weight, int mode, double fh2, float* desc,
                        cudaStream_t s);

@@ -615,15 +615,15 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     const int rzB = min(rzA + g.RZ, g.P[0] + 1);
     const int ryA = -g.P[1] + yc * g.RY;
     const int ryB = min(ryA + g.RY, g.P[1] + 1);
-    const int ryN = ryB - ryA;
     const int bbA = xc * g.NBc;
     const int nbb = min(g.NBc, g.NB - bbA);
     const int lastValid = bbA + nbb == g.NB ? 2 * g.P[2] + 1 - T * (g.NB - 1) : T;
     const int colsH = T * nbb + 4 * T;      // read extent: 8 strip + 8 bb + 16 columns
     const int strideP = stride_4mod32(2 * colsH);
-    const int pairRows = 32 + ryN - 1;      // pair row i holds halo rows i and i + 32
+    // the chunk's ry rows are staged in rounds of at most RYS rows (pair row i of a round
+    // holds halo rows i and i + 32); the accumulators carry over the rounds
     float* ys = smem;
-    float* Gs = smem + pairRows * strideP;
+    float* Gs = smem + (32 + g.RYS - 1) * strideP;
     const int64_t hx0 = x0 - g.P[2] + (int64_t)T * bbA;
 
     // own positions: rows y0 + lane and y0 + lane + 32, columns x0 + 8 strip + k
@@ -646,13 +646,16 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
     const int rowG = nbb * GBLOCK;          // coefficient floats of one ry row of the chunk
     const int warp = threadIdx.x >> 5;
     constexpr int NW = ADJ_THREADS / 32;
-    for (int rz = rzA; rz < rzB; ++rz) {
+    for (int rz = rzA; rz < rzB; ++rz)
+    for (int ryS = ryA; ryS < ryB; ryS += g.RYS) {
+        const int ryN = min(g.RYS, ryB - ryS);
+        const int pairRows = 32 + ryN - 1;
         __syncthreads();
         const int64_t gz = wrap1(z + rz, n0);
         // raw halo (pair rows i, i + 32) and the chunk's coefficient rows, copied asynchronously
         for (int i = warp; i < pairRows; i += NW) {
-            const float* srcA = tipf + (gz * n1 + wrap1(y0 + ryA + i, n1)) * n2;
-            const float* srcB = tipf + (gz * n1 + wrap1(y0 + ryA + i + 32, n1)) * n2;
+            const float* srcA = tipf + (gz * n1 + wrap1(y0 + ryS + i, n1)) * n2;
+            const float* srcB = tipf + (gz * n1 + wrap1(y0 + ryS + i + 32, n1)) * n2;
             float* dst = ys + i * strideP;
             int64_t gx = wrap1(hx0 + lane, n2);
             for (int c = lane; c < colsH; c += 32) {
@@ -662,7 +665,7 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
                 while (gx >= n2) gx -= n2;
             }
         }
-        const float* grow0 = Gd + (((int64_t)(rz + g.P[0]) * (2 * g.P[1] + 1) + (ryA + g.P[1])) * g.NB + bbA) * GBLOCK;
+        const float* grow0 = Gd + (((int64_t)(rz + g.P[0]) * (2 * g.P[1] + 1) + (ryS + g.P[1])) * g.NB + bbA) * GBLOCK;
         for (int i = threadIdx.x; i < ryN * (rowG / 4); i += ADJ_THREADS) {
             const int r = i / (rowG / 4), c = i - r * (rowG / 4);
             cp_async16(Gs + r * rowG + 4 * c, grow0 + (int64_t)r * g.NB * GBLOCK + 4 * c);
@@ -684,8 +687,8 @@ corr_adj_kernel(const AdjSeg* __restrict__ segs, int nseg, ThreshConst tc) {
         const int slow = __syncthreads_or(rc);
         if (!IDENT && slow) {
             for (int i = warp; i < pairRows; i += NW) {
-                const float* srcA = tipf + (gz * n1 + wrap1(y0 + ryA + i, n1)) * n2;
-                const float* srcB = tipf + (gz * n1 + wrap1(y0 + ryA + i + 32, n1)) * n2;
+                const float* srcA = tipf + (gz * n1 + wrap1(y0 + ryS + i, n1)) * n2;
+                const float* srcB = tipf + (gz * n1 + wrap1(y0 + ryS + i + 32, n1)) * n2;
                 float* dst = ys + i * strideP;
                 int64_t gx = wrap1(hx0 + lane, n2);
                 for (int c = lane; c < colsH; c += 32) {
@@ -810,9 +813,9 @@ void launch_fwd_reduce(const RedSeg* segs, int nseg, int64_t blocks, cudaStream_
 }
 
 size_t adj_smem_bytes(const LevelGeom& g) {
-    const int pairRows = 32 + g.RY - 1;
+    const int pairRows = 32 + g.RYS - 1;
     const int colsH = T * g.NBc + 4 * T;
-    return (size_t)(pairRows * stride_4mod32(2 * colsH) + g.RY * g.NBc * GBLOCK) * sizeof(float);
+    return (size_t)(pairRows * stride_4mod32(2 * colsH) + g.RYS * g.NBc * GBLOCK) * sizeof(float);
 }
 
 void launch_corr_adj(const AdjSeg* segs, int nseg, int64_t blocks, size_t smem, const ThreshConst& tc,

@@ -57,6 +57,59 @@ __device__ __forceinline__ LineMap line_of(const FftPass& p, int l) {
     return m;
 }
 
+// One Stockham stage of radix R over the L lines in shared memory (src -> dst): every
+// butterfly reads R values n/R apart, multiplies by the twiddles of its offset k within the
+// current sub-transform length Ns, and writes R values Ns apart.  R is a template parameter so
+// that the butterfly's values stay in registers.
+template <int R>
+__device__ __forceinline__ void fft_stage(const FftPass& p, const double2* __restrict__ src, double2* __restrict__ dst,
+                                          int Ns) {
+    const int n = p.len, L = p.L;
+    const int nR = n / R;
+    const int tstep = n / (Ns * R);
+    for (int t = threadIdx.x; t < L * nR; t += blockDim.x) {
+        const int l = t / nR, j = t - l * nR;
+        const int k = j % Ns;
+        const double2* in = src + l * n;
+        double2 v[R];
+        v[0] = in[j];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            double2 w = p.tw[(k * r) * tstep];
+            if (p.sign > 0) w.y = -w.y;
+            v[r] = cmul(in[j + r * nR], w);
+        }
+        double2 V[R];
+        if (R == 2) {
+            V[0] = cadd(v[0], v[1]);
+            V[1] = csub(v[0], v[1]);
+        } else if (R == 4) {
+            const double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+            const double2 c = cadd(v[1], v[3]), d = mul_i(csub(v[1], v[3]), p.sign);
+            V[0] = cadd(a, c);
+            V[1] = cadd(b, d);
+            V[2] = csub(a, c);
+            V[3] = csub(b, d);
+        } else {
+            // radix 3 and 5: V[q] = sum_r v[r] omega^(r q),  omega = exp(sign 2 pi i / R)
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                double2 acc = v[0];
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    double2 w = R == 3 ? p.om3[(r * q) % 3] : p.om5[(r * q) % 5];
+                    if (p.sign > 0) w.y = -w.y;
+                    acc = cadd(acc, cmul(v[r], w));
+                }
+                V[q] = acc;
+            }
+        }
+        double2* out = dst + l * n + (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) out[q * Ns] = V[q];
+    }
+}
+
 __global__ void __launch_bounds__(256) fft_pass_kernel(FftPass p) {
     extern __shared__ __align__(16) double2 sbuf[];
     const int n = p.len, L = p.L;
@@ -79,45 +132,12 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(FftPass p) {
     int Ns = 1;
     for (int s = 0; s < p.nrad; ++s) {
         const int R = p.rad[s];
-        const int nR = n / R;
-        const int tstep = n / (Ns * R);
         __syncthreads();
-        for (int t = threadIdx.x; t < L * nR; t += blockDim.x) {
-            const int l = t / nR, j = t - l * nR;
-            const int k = j % Ns;
-            const double2* in = src + l * n;
-            double2 v[5];
-            for (int r = 0; r < R; ++r) {
-                double2 w = p.tw[(k * r) * tstep];
-                if (p.sign > 0) w.y = -w.y;
-                v[r] = r == 0 ? in[j] : cmul(in[j + r * nR], w);
-            }
-            double2 V[5];
-            if (R == 2) {
-                V[0] = cadd(v[0], v[1]);
-                V[1] = csub(v[0], v[1]);
-            } else if (R == 4) {
-                const double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-                const double2 c = cadd(v[1], v[3]), d = mul_i(csub(v[1], v[3]), p.sign);
-                V[0] = cadd(a, c);
-                V[1] = cadd(b, d);
-                V[2] = csub(a, c);
-                V[3] = csub(b, d);
-            } else {
-                // radix 3 and 5: V[q] = sum_r v[r] omega^(r q),  omega = exp(sign 2 pi i / R)
-                const double2* om = R == 3 ? p.om3 : p.om5;
-                for (int q = 0; q < R; ++q) {
-                    double2 acc = v[0];
-                    for (int r = 1; r < R; ++r) {
-                        double2 w = om[(r * q) % R];
-                        if (p.sign > 0) w.y = -w.y;
-                        acc = cadd(acc, cmul(v[r], w));
-                    }
-                    V[q] = acc;
-                }
-            }
-            double2* out = dst + l * n + (j / Ns) * Ns * R + k;
-            for (int q = 0; q < R; ++q) out[q * Ns] = V[q];
+        switch (R) {
+            case 2: fft_stage<2>(p, src, dst, Ns); break;
+            case 3: fft_stage<3>(p, src, dst, Ns); break;
+            case 4: fft_stage<4>(p, src, dst, Ns); break;
+            default: fft_stage<5>(p, src, dst, Ns); break;
         }
         double2* tmp = src;
         src = dst;
@@ -149,12 +169,12 @@ void launch_fft_pass(const FftPass& p, cudaStream_t s) {
     fft_pass_kernel<<<(unsigned)blocks, 256, fft_smem_bytes(p.len, p.L), s>>>(p);
 }
 
-// X <- |X|^2
-__global__ void fft_power_kernel(double2* __restrict__ X, int64_t N) {
+// P <- |X|^2 (X is kept: the adjoint of the same call reuses the transform of the field)
+__global__ void fft_power_kernel(const double2* __restrict__ X, double2* __restrict__ P, int64_t N) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double2 v = X[i];
-    X[i] = make_double2(v.x * v.x + v.y * v.y, 0.0);
+    P[i] = make_double2(v.x * v.x + v.y * v.y, 0.0);
 }
 
 // H <- X conj(H)
@@ -253,8 +273,8 @@ void launch_fft_twiddles(double2* tw, int len, cudaStream_t s) {
     fft_twiddle_kernel<<<(len + 255) / 256, 256, 0, s>>>(tw, len);
 }
 
-void launch_fft_power(double2* X, int64_t N, cudaStream_t s) {
-    fft_power_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(X, N);
+void launch_fft_power(const double2* X, double2* P, int64_t N, cudaStream_t s) {
+    fft_power_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(X, P, N);
 }
 void launch_fft_xcorr(const double2* X, double2* H, int64_t N, cudaStream_t s) {
     fft_xcorr_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(X, H, N);

@@ -4,7 +4,8 @@
 //   0 MUFU reciprocal (rcp.approx.ftz), 1 MUFU exp2, 2 MUFU tanh, 3 MUFU log2,
 //   4 FP32 FFMA, 5 FP32 FFMA2 (lane operations: two per instruction),
 //   6 the adjoint's pair arithmetic held in registers (pairs per SM per clock),
-//   7 the forward's pair arithmetic held in registers (pairs per SM per clock).
+//   7 the forward's pair arithmetic held in registers (pairs per SM per clock),
+//   8 FP64 DFMA (the FFT path's arithmetic).
 // Every thread runs many independent chains (no chain waits on another), as many CTAs of
 // 256 threads as fit on an SM at once (all resident together, so each CTA's cycle count
 // spans the concurrent run), and each loop iteration carries at least 64 operations so the
@@ -23,17 +24,21 @@ __device__ __forceinline__ float p_tanh(float x) { float y; asm volatile("tanh.a
 __device__ __forceinline__ float p_lg2(float x) { float y; asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
 
 // operations per chain step counted by the host, per op kind
-__host__ __device__ constexpr int chains(int op) { return op == 4 ? 32 : (op == 5 ? 16 : (op >= 6 ? 8 : 16)); }
+__host__ __device__ constexpr int chains(int op) {
+    return op == 4 ? 32 : (op == 5 ? 16 : (op == 8 ? 16 : (op >= 6 ? 8 : 16)));
+}
 
 template <int OP>
 __global__ void __launch_bounds__(256) pipe_kernel(float* out, long long* cyc, float seed) {
     constexpr int CH = chains(OP);
     float r[CH];
     float2 q[CH];
+    double dq[OP == 8 ? CH : 1];
 #pragma unroll
     for (int i = 0; i < CH; ++i) {
         r[i] = seed + 0.01f * i + 1e-6f * threadIdx.x;
         q[i] = make_float2(r[i], r[i] + 0.5f);
+        if (OP == 8) dq[i] = (double)r[i];
     }
     const float2 a2 = make_float2(0.999f, 0.998f), b2 = make_float2(0.001f, 0.002f);
     const float2 one2 = make_float2(1.f, 1.f);
@@ -78,6 +83,11 @@ __global__ void __launch_bounds__(256) pipe_kernel(float* out, long long* cyc, f
                 h = __ffma2_rn(h, s, a2);
                 q[i] = __ffma2_rn(h, s, q[i]);
             }
+        } else if (OP == 8) {
+#pragma unroll
+            for (int rep = 0; rep < 4; ++rep)
+#pragma unroll
+                for (int i = 0; i < CH; ++i) dq[i] = fma(dq[i], 0.999, 0.001);
         } else {
             // forward: d, shared reciprocal, u = s + beta, acc += u^2
 #pragma unroll
@@ -92,30 +102,32 @@ __global__ void __launch_bounds__(256) pipe_kernel(float* out, long long* cyc, f
     const long long t1 = clock64();
     float s = 0.f;
     for (int i = 0; i < CH; ++i) s += r[i] + q[i].x + q[i].y;
+    if (OP == 8)
+        for (int i = 0; i < CH; ++i) s += (float)dq[i];
     if (s == 12345.f) out[0] = s;
     if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
 }
 
 // operations one thread counts per loop iteration
 constexpr double ops_per_iter(int op) {
-    return op <= 3 ? 4.0 * 16 : (op == 4 ? 2.0 * 32 : (op == 5 ? 4.0 * 16 * 2 : 8.0 * 2));
+    return op <= 3 ? 4.0 * 16 : (op == 4 ? 2.0 * 32 : (op == 5 ? 4.0 * 16 * 2 : (op == 8 ? 4.0 * 16 : 8.0 * 2)));
 }
 
 }  // namespace
 
-// rates[0..7] as listed at the top (ops, lane operations or pairs per SM per clock);
+// rates[0..8] as listed at the top (ops, lane operations or pairs per SM per clock);
 // returns 0, or a CUDA error code.  Synchronous; allocates a few bytes of device memory.
-extern "C" int dmcr_bench_pipe_rates(double rates[8]) {
+extern "C" int dmcr_bench_pipe_rates(double rates[9]) {
     int dev = 0, sms = 0;
     if (rates == nullptr) return 1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return (int)e;
-    const void* kern[8] = {(const void*)pipe_kernel<0>, (const void*)pipe_kernel<1>, (const void*)pipe_kernel<2>,
+    const void* kern[9] = {(const void*)pipe_kernel<0>, (const void*)pipe_kernel<1>, (const void*)pipe_kernel<2>,
                            (const void*)pipe_kernel<3>, (const void*)pipe_kernel<4>, (const void*)pipe_kernel<5>,
-                           (const void*)pipe_kernel<6>, (const void*)pipe_kernel<7>};
-    int per_sm[8];
-    for (int op = 0; op < 8 && e == cudaSuccess; ++op) {
+                           (const void*)pipe_kernel<6>, (const void*)pipe_kernel<7>, (const void*)pipe_kernel<8>};
+    int per_sm[9];
+    for (int op = 0; op < 9 && e == cudaSuccess; ++op) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[op], kern[op], 256, 0);
         if (e == cudaSuccess && per_sm[op] < 1) e = cudaErrorInvalidConfiguration;
     }
@@ -129,7 +141,7 @@ extern "C" int dmcr_bench_pipe_rates(double rates[8]) {
         return (int)e;
     }
     long long* h = new long long[blocks_max];
-    for (int op = 0; op < 8 && e == cudaSuccess; ++op) {
+    for (int op = 0; op < 9 && e == cudaSuccess; ++op) {
         const int blocks = sms * (per_sm[op] < 8 ? per_sm[op] : 8);
         for (int rep = 0; rep < 2; ++rep) {   // the first launch warms up
             switch (op) {
@@ -140,7 +152,8 @@ extern "C" int dmcr_bench_pipe_rates(double rates[8]) {
                 case 4: pipe_kernel<4><<<blocks, 256>>>(out, cyc, 0.7f); break;
                 case 5: pipe_kernel<5><<<blocks, 256>>>(out, cyc, 0.7f); break;
                 case 6: pipe_kernel<6><<<blocks, 256>>>(out, cyc, 0.7f); break;
-                default: pipe_kernel<7><<<blocks, 256>>>(out, cyc, 0.7f); break;
+                case 7: pipe_kernel<7><<<blocks, 256>>>(out, cyc, 0.7f); break;
+                default: pipe_kernel<8><<<blocks, 256>>>(out, cyc, 0.7f); break;
             }
         }
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) break;

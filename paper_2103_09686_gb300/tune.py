@@ -22,7 +22,7 @@ import torch
 
 from . import _lib
 
-FWD_ROWS = (8, 16, 32)
+FWD_ROWS = (4, 8, 16, 32)
 ADJ_ROWS = (0, 2, 4, 8, 12, 16)
 ADJ_CHUNKS = (0, 8, 16, 64)
 ADJ_XBLOCKS = (0, 3, 5, 12, 32)

@@ -111,7 +111,9 @@ def test_lengths_of_the_other_descriptors(lib):
     assert dm.dmcr_descriptor_length(dm.Params((64, 64), (16, 16), phases=1)) == 545
     one = dm.dmcr_workspace_size(dm.Params((256, 256), (16, 16), levels=2))
     three = dm.dmcr_workspace_size(dm.Params((256, 256), (16, 16), levels=2, phases=3))
-    assert three > 3 * one
+    # nine forward-partial and coefficient blocks per level; the adjoint partials grow less
+    # than nine-fold (a chunk of a multi-phase problem covers up to 9 times the ry rows)
+    assert three > 2 * one
 
 
 @pytest.mark.parametrize("kw,status", [
