@@ -49,12 +49,11 @@ RCP_PER_PAIR = {"corr_fwd": 0.5, "corr_adj": 4.0 / 8.0 * 0.5 + 4.0 / 8.0}
 ALGORITHMIC_FP32_OPS_PER_PAIR = 5.0
 # the probe's measured pair rate of each kernel's own instruction mix held in registers
 MIX_KEY = {"corr_fwd": "forward_pairs", "corr_adj": "adjoint_pairs"}
-# DRAM bytes (read + write) per launch of the current kernels on the 512^2, +-64, 3-level
-# workload, from the ncu full-set capture summarised in profiles/corr_kernels_grf512_w64_L3.md
-# (None whenever the kernels changed since the last capture).
-NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2707968 + 28416, ("grf512", "corr_fwd"): 1452032 + 768,
+# DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (None
+# whenever a kernel changed since its last capture).
+NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): None, ("grf512", "corr_fwd"): None,
                      # profiles/launches_mp3_512_w64_L3.md
-                     ("mp3_512", "corr_adj"): 16447744 + 259444224, ("mp3_512", "corr_fwd"): 4369152 + 42389504}
+                     ("mp3_512", "corr_adj"): 15905024 + 50688, ("mp3_512", "corr_fwd"): 4216832 + 45588480}
 
 WORKLOADS = {
     "grf512": dict(shape=(512, 512), window=(64, 64), levels=3,
@@ -109,6 +108,12 @@ def serve_jobs(n_jobs: int, rate: float, seed: int, dm, serve):
 
 
 SERVE_CLASS_CAPS = (1.5e8, 1e9, 1e10, float("inf"))   # voxel-shifts per iteration of each cost class
+# most active jobs per class: the two heavy classes (2-D 1024^2 and 3-D jobs) serve one job
+# at a time in arrival order; equal stream priorities.  On the first 64 arrivals at 80% load
+# this gave p50 1.96 s / p99 25.7 s against 2.73 s / 28.9 s with no class limits and
+# cheap-first priorities, and 3.87 s / 30.0 s for the plain form.
+SERVE_CLASS_SLOTS = (None, None, 1, 1)
+SERVE_PRIORITIES = "equal"
 
 
 def main_serve(args):
@@ -127,7 +132,8 @@ def main_serve(args):
 
     def both(n_jobs, rate):
         jobs = serve_jobs(n_jobs, rate, 5000, dm, serve)
-        served = serve.run_trace(jobs, "serve", max_slots=args.slots, tick_iters=50, class_caps=SERVE_CLASS_CAPS)
+        served = serve.run_trace(jobs, "serve", max_slots=args.slots, tick_iters=50, class_caps=SERVE_CLASS_CAPS,
+                                 class_slots=SERVE_CLASS_SLOTS, priorities=SERVE_PRIORITIES)
         units = sum(j.iters_done * serve.iteration_units(j.params) for j in jobs)
         plain_jobs = serve_jobs(n_jobs, rate, 5000, dm, serve)
         plain = serve.run_trace(plain_jobs, "plain")
@@ -149,8 +155,10 @@ def main_serve(args):
                                    "80%% of the measured served capacity; jobs 2D GRF {128,256,512,1024}^2 +-16 with "
                                    "levels down to 64^2, one in six 3D GRF {64,80,96,128,160}^3 +-8 (3 levels from "
                                    "96, else 2), l = n/32, vf U[0.1,0.5], each to rel_err < 1e-3 (at most 5000 "
-                                   "iterations); slots %d, tick 50 iterations, cost classes %s"
-                                   % (args.jobs, args.jobs2, args.slots, list(SERVE_CLASS_CAPS))},
+                                   "iterations); slots %d, tick 50 iterations, cost classes %s with at most %s "
+                                   "active jobs each, %s stream priorities"
+                                   % (args.jobs, args.jobs2, args.slots, list(SERVE_CLASS_CAPS),
+                                      list(SERVE_CLASS_SLOTS), SERVE_PRIORITIES)},
             "overload": over, "at_80pct_capacity": at80, "clocks": clocks}
     print(json.dumps(line))
     return 0

@@ -157,13 +157,13 @@ bool fft_size_ok(int64_t n) {
 
 // Identity threshold, AUTO path: the FFT when its estimated cost is lower.  Both costs are
 // fitted (relative error) to GB300 measurements of descriptor + gradient on 64^3 and 128^3
-// (P = 1..24): the FFT path is ~1.15 ns per grid point + 0.18 ms; the direct kernels
-// ~0.149 ps per voxel-shift + 0.14 ns per point + 0.13 ms.  Measured crossovers: P = 10 on
-// both grids (at P = 8 the direct path is ahead by 13% on 64^3 and 9% on 128^3).
+// (P = 1..24): the FFT path is ~0.758 ns per grid point + 0.157 ms; the direct kernels
+// ~0.148 ps per voxel-shift + 0.127 ns per point + 0.151 ms.  Measured crossovers: P = 8 on
+// both grids (at P = 6 the direct path is ahead by 23% on 64^3 and 29% on 128^3).
 bool fft_cheaper(const LevelGeom& g) {
     const double kfull = (double)(2 * g.P[0] + 1) * (2 * g.P[1] + 1) * (2 * g.P[2] + 1);
-    const double t_direct = (double)g.N * kfull * 1.49e-13 + (double)g.N * 1.35e-10 + 1.31e-4;
-    const double t_fft = (double)g.N * 1.148e-9 + 1.77e-4;
+    const double t_direct = (double)g.N * kfull * 1.481e-13 + (double)g.N * 1.266e-10 + 1.506e-4;
+    const double t_fft = (double)g.N * 7.577e-10 + 1.568e-4;
     return t_fft < t_direct;
 }
 
@@ -1154,6 +1154,79 @@ dmcr_status exec_batch(const BatchLayout& B, void* ws, std::vector<Inst>& in, un
     return cuda_check(cudaGetLastError(), what);
 }
 
+// Instantiated graphs of reconstruction iterations, keyed by everything the captured launch
+// sequence depends on: the table bytes and where they live, every launch count and grid, the
+// FFT and three-point jobs, and the device.  A server ticking the same set of jobs, or a
+// caller running a reconstruction in chunks, then captures each iteration once.  The tables
+// themselves are uploaded by every call (outside the graph): other calls may have reused
+// the workspace in between.
+struct ReconGraph {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t used = 0;
+};
+constexpr size_t RECON_GRAPH_CACHE = 32;
+std::mutex g_recon_mu;
+uint64_t g_recon_clock = 0;
+std::vector<ReconGraph>& recon_cache() {
+    static std::vector<ReconGraph>* c = new std::vector<ReconGraph>();   // lives until exit
+    return *c;
+}
+
+std::string prepared_key(const Prepared& P) {
+    std::string k;
+    auto add = [&k](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+    int dev = 0;
+    cudaGetDevice(&dev);
+    add(&dev, sizeof dev);
+    add(&P.tab, sizeof P.tab);
+    add(&P.flags, sizeof P.flags);
+    add(&P.tc, sizeof P.tc);
+    for (const Prepared::R& r : P.restricts) add(&r, sizeof r);
+    for (const Prepared::R* r : {&P.fwd, &P.red, &P.pen, &P.loss, &P.gco, &P.adj, &P.fin, &P.init, &P.tmap, &P.tsum})
+        add(r, sizeof *r);
+    add(&P.smem_fwd, sizeof P.smem_fwd);
+    add(&P.smem_adj, sizeof P.smem_adj);
+    for (const auto* v : {&P.fftf, &P.fftb}) {
+        const size_t n = v->size();
+        add(&n, sizeof n);
+        if (n) add(v->data(), n * sizeof((*v)[0]));
+    }
+    for (const auto* v : {&P.s3f, &P.s3b}) {
+        const size_t n = v->size();
+        add(&n, sizeof n);
+        if (n) add(v->data(), n * sizeof((*v)[0]));
+    }
+    add(P.tb.h.data(), P.tb.h.size());
+    return k;
+}
+
+cudaGraphExec_t recon_graph_find(const std::string& key) {
+    std::lock_guard<std::mutex> lk(g_recon_mu);
+    for (ReconGraph& g : recon_cache())
+        if (g.key == key) {
+            g.used = ++g_recon_clock;
+            return g.exec;
+        }
+    return nullptr;
+}
+
+void recon_graph_store(const std::string& key, cudaGraphExec_t exec) {
+    std::lock_guard<std::mutex> lk(g_recon_mu);
+    std::vector<ReconGraph>& c = recon_cache();
+    ReconGraph g;
+    g.key = key;
+    g.exec = exec;
+    g.used = ++g_recon_clock;
+    if (c.size() >= RECON_GRAPH_CACHE) {
+        auto lru = std::min_element(c.begin(), c.end(), [](const ReconGraph& a, const ReconGraph& b) { return a.used < b.used; });
+        cudaGraphExecDestroy(lru->exec);
+        *lru = g;
+    } else {
+        c.push_back(g);
+    }
+}
+
 // Graph-captured reconstruction of every instance (each stops on its own device flag).
 dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, Scalars* scal_base,
                               const std::vector<int>& max_iters, int poll_every, dmcr_recon_report* reports,
@@ -1184,17 +1257,25 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
         Prepared P;
         if ((st = prepare(in, F_FWD | F_LOSS | F_BACK | F_ADAM, tab, tab_cap, P))) break;
         upload(P, s);
-        if ((st = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "BeginCapture"))) break;
-        run(P, s);
-        if ((st = cuda_check(cudaStreamEndCapture(s, &graph), "EndCapture"))) break;
-        if ((st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "GraphInstantiate"))) break;
+        const std::string key = prepared_key(P);
+        cudaGraphExec_t cached = recon_graph_find(key);
+        if (cached == nullptr) {
+            if ((st = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "BeginCapture"))) break;
+            run(P, s);
+            if ((st = cuda_check(cudaStreamEndCapture(s, &graph), "EndCapture"))) break;
+            if ((st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "GraphInstantiate"))) break;
+            recon_graph_store(key, exec);          // the cache owns it from here
+            cached = exec;
+            exec = nullptr;
+        }
+        cudaGraphExec_t run_exec = cached;
         int most = 0;
         for (int k : max_iters) most = std::max(most, k);
         // iteration max_iters evaluates the final field and sets the done flag
         int launched = 0;
         while (launched <= most) {
             const int k = std::min(poll_every, most + 1 - launched);
-            for (int i = 0; i < k && !st; ++i) st = cuda_check(cudaGraphLaunch(exec, s), "GraphLaunch");
+            for (int i = 0; i < k && !st; ++i) st = cuda_check(cudaGraphLaunch(run_exec, s), "GraphLaunch");
             if (st) break;
             launched += k;
             if ((st = cuda_check(cudaMemcpyAsync(hs.data(), scal_base, count * sizeof(Scalars), cudaMemcpyDeviceToHost,

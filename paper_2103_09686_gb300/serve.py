@@ -8,8 +8,11 @@ and level of the class, replayed as a captured CUDA graph) of at most ``tick_ite
 iterations.  Jobs are grouped in cost classes by their work per iteration; in threaded
 mode every class ticks on its own host thread and CUDA stream, so cheap, latency-bound
 jobs are not held to the iteration time of expensive ones and the classes' kernels
-overlap on the device.  Between ticks, finished jobs retire (result copied to the host)
-and waiting jobs are admitted while a slot and the HBM budget allow.  Because the
+overlap on the device.  A class may cap how many of its jobs are active at once: jobs
+large enough to fill the device each are then served one after another in arrival order,
+which finishes each sooner than sharing the device among them.  Between ticks, finished
+jobs retire (result copied to the host) and waiting jobs are admitted while a slot and the
+HBM budget allow.  Because the
 per-instance arithmetic of a batched call equals that of a single call bitwise, and a tick
 boundary only re-evaluates the loss of the current field, a job's result is the same
 alone and in any mix (tested).
@@ -71,8 +74,9 @@ def iteration_units(params: _lib.Params) -> int:
 
 
 class _Class:
-    def __init__(self, cap):
+    def __init__(self, cap, slots):
         self.cap = cap
+        self.slots = slots        # most jobs of this class active at once
         self.pending: collections.deque[Job] = collections.deque()
         self.active: list[Job] = []
         self.stream = None
@@ -82,14 +86,26 @@ class _Class:
 
 class Server:
     def __init__(self, device="cuda", hbm_budget_bytes: int = 150 << 30, max_slots: int = 64, tick_iters: int = 50,
-                 class_caps=(float("inf"),), clock=time.perf_counter):
+                 class_caps=(float("inf"),), class_slots=None, priorities: str = "cheap_first",
+                 clock=time.perf_counter):
         self.dev = torch.device(device)
         self.budget = int(hbm_budget_bytes)
         self.max_slots = int(max_slots)
         self.tick_iters = int(tick_iters)
         self.clock = clock
         self.t0 = None
-        self.classes = [_Class(c) for c in sorted(class_caps)]
+        # class_slots[i]: most active jobs of the class with cap class_caps[i] (None: only the
+        # server-wide max_slots).  Jobs of one class that could each fill the device run better
+        # one after another in arrival order than side by side: sharing the device delays all
+        # of them, while serial service finishes the first at full speed.
+        slots = [None] * len(class_caps) if class_slots is None else list(class_slots)
+        if len(slots) != len(class_caps):
+            raise ValueError("class_slots needs one entry per class cap")
+        self.classes = [_Class(c, n if n is not None else self.max_slots)
+                        for c, n in sorted(zip(class_caps, slots), key=lambda cs: cs[0])]
+        if priorities not in ("cheap_first", "equal"):
+            raise ValueError("priorities: 'cheap_first' or 'equal'")
+        self.priorities = priorities
         self.done: list[Job] = []
         self.in_use = 0
         self.ticks = 0
@@ -127,7 +143,8 @@ class Server:
     def _admit(self, cls):
         new = []
         with self._lock:
-            while cls.pending and sum(len(c.active) for c in self.classes) + len(new) < self.max_slots:
+            while (cls.pending and sum(len(c.active) for c in self.classes) + len(new) < self.max_slots
+                   and len(cls.active) + len(new) < cls.slots):
                 job = cls.pending[0]
                 need = job.bytes_estimate()
                 if self.in_use + need > self.budget:
@@ -206,11 +223,13 @@ class Server:
         if self.t0 is None:
             self.t0 = self.clock()
         self._stop = False
-        # cheaper classes get higher stream priority: their short kernels are scheduled
-        # ahead of the long-running blocks of expensive classes as SMs free up
+        # "cheap_first": cheaper classes get higher stream priority, so their short kernels are
+        # scheduled ahead of the long-running blocks of expensive classes as SMs free up;
+        # "equal": every class stream has the default priority
         lo, hi = torch.cuda.Stream.priority_range()      # least, greatest (numerically lower = higher)
         for i, c in enumerate(self.classes):
-            c.stream = torch.cuda.Stream(device=self.dev, priority=min(lo, hi + i))
+            prio = min(lo, hi + i) if self.priorities == "cheap_first" else 0
+            c.stream = torch.cuda.Stream(device=self.dev, priority=prio)
             t = threading.Thread(target=self._worker, args=(c,), daemon=True)
             t.start()
             self._threads.append(t)

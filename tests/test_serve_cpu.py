@@ -142,3 +142,22 @@ def test_tick_iters_must_be_a_multiple_of_check_every(fake):
     job.opts = dataclasses.replace(job.opts, check_every=7)
     with pytest.raises(ValueError):
         srv.submit(job)
+
+
+def test_class_slots_serve_heavy_jobs_one_at_a_time(fake):
+    """A class limited to one active job serves its jobs in arrival order, one per tick set,
+    while a cheap class keeps several active."""
+    small = [_job(i, shape=(64, 64), window=(4, 4)) for i in range(3)]
+    large = [_job(10 + i, shape=(256, 256), window=(32, 32), levels=2) for i in range(3)]
+    fake.need.update({j.job_id: 100 for j in small + large})
+    cap = serve.iteration_units(small[0].params) * 10
+    srv = serve.Server(device="cpu", max_slots=64, tick_iters=50, class_caps=(float("inf"), cap),
+                       class_slots=(1, None))
+    _run(srv, fake, small + large)
+    heavy = [ids for ids, _ in fake.calls if ids and ids[0] >= 10]
+    assert all(len(ids) == 1 for ids in heavy)
+    assert [ids[0] for ids in heavy] == [10, 10, 11, 11, 12, 12]        # arrival order, 2 ticks each
+    assert max(len(ids) for ids, _ in fake.calls if ids[0] < 10) == 3
+    assert len(srv.done) == 6
+    with pytest.raises(ValueError):
+        serve.Server(device="cpu", class_caps=(1.0, 2.0), class_slots=(1,))
