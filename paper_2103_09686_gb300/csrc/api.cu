@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "dmcr.h"
 
@@ -76,11 +78,13 @@ void prof_collect(ProfState& p) {
     }
     p.pending.clear();
 }
-// Records an event pair around the launches of its scope when profiling is on and the
+// Names the launches of its scope with an NVTX range (for nsys and similar tools; a no-op
+// without one attached), and records an event pair around them when profiling is on and the
 // stream is not being captured into a graph.
 class ProfScope {
   public:
     ProfScope(const char* name, int level, cudaStream_t s) : s_(s) {
+        nvtxRangePushA(name);
         ProfState& p = prof();
         if (!p.on) return;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -96,6 +100,7 @@ class ProfScope {
         active_ = true;
     }
     ~ProfScope() {
+        nvtxRangePop();
         if (!active_) return;
         ProfState& p = prof();
         std::lock_guard<std::mutex> lk(p.mu);
@@ -883,7 +888,7 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
                 f.a.m = slice(fs.a.m);
                 f.a.v = slice(fs.a.v);
                 f.blockStart = fb;
-                fb += ceil_div(N1, ELEM_TH);
+                fb += ceil_div(N1, FIN_POS);
                 fv.push_back(f);
             }
         }
@@ -1164,6 +1169,7 @@ struct ReconGraph {
     std::string key;
     cudaGraphExec_t exec = nullptr;
     uint64_t used = 0;
+    int in_use = 0;     // calls launching it now: never evicted while in use
 };
 constexpr size_t RECON_GRAPH_CACHE = 32;
 std::mutex g_recon_mu;
@@ -1201,30 +1207,51 @@ std::string prepared_key(const Prepared& P) {
     return k;
 }
 
-cudaGraphExec_t recon_graph_find(const std::string& key) {
+// Takes the cached graph of `key` for this call (marked in use until recon_graph_release).
+cudaGraphExec_t recon_graph_acquire(const std::string& key) {
     std::lock_guard<std::mutex> lk(g_recon_mu);
     for (ReconGraph& g : recon_cache())
         if (g.key == key) {
             g.used = ++g_recon_clock;
+            ++g.in_use;
             return g.exec;
         }
     return nullptr;
 }
 
-void recon_graph_store(const std::string& key, cudaGraphExec_t exec) {
+// The call that acquired (or stored) `exec` is done with it: its stream has been synchronized,
+// so no launch of it is pending.
+void recon_graph_release(cudaGraphExec_t exec) {
+    std::lock_guard<std::mutex> lk(g_recon_mu);
+    for (ReconGraph& g : recon_cache())
+        if (g.exec == exec && g.in_use > 0) {
+            --g.in_use;
+            return;
+        }
+}
+
+// Stores a new graph, marked in use by the storing call.  Returns false (the caller keeps
+// and destroys the graph) when every cached graph is in use.  An evicted graph has no
+// pending launch: its last user synchronized before releasing it.
+bool recon_graph_store(const std::string& key, cudaGraphExec_t exec) {
     std::lock_guard<std::mutex> lk(g_recon_mu);
     std::vector<ReconGraph>& c = recon_cache();
     ReconGraph g;
     g.key = key;
     g.exec = exec;
     g.used = ++g_recon_clock;
-    if (c.size() >= RECON_GRAPH_CACHE) {
-        auto lru = std::min_element(c.begin(), c.end(), [](const ReconGraph& a, const ReconGraph& b) { return a.used < b.used; });
-        cudaGraphExecDestroy(lru->exec);
-        *lru = g;
-    } else {
+    g.in_use = 1;
+    if (c.size() < RECON_GRAPH_CACHE) {
         c.push_back(g);
+        return true;
     }
+    ReconGraph* lru = nullptr;
+    for (ReconGraph& e : c)
+        if (e.in_use == 0 && (lru == nullptr || e.used < lru->used)) lru = &e;
+    if (lru == nullptr) return false;
+    cudaGraphExecDestroy(lru->exec);
+    *lru = g;
+    return true;
 }
 
 // Graph-captured reconstruction of every instance (each stops on its own device flag).
@@ -1235,7 +1262,8 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec = nullptr;      // a graph of this call only (the cache was full of graphs in use)
+    cudaGraphExec_t cached = nullptr;    // the cache's graph, in use by this call
     dmcr_status st = DMCR_OK;
     std::vector<Scalars> hs(count);
     do {
@@ -1258,17 +1286,18 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
         if ((st = prepare(in, F_FWD | F_LOSS | F_BACK | F_ADAM, tab, tab_cap, P))) break;
         upload(P, s);
         const std::string key = prepared_key(P);
-        cudaGraphExec_t cached = recon_graph_find(key);
+        cached = recon_graph_acquire(key);
         if (cached == nullptr) {
             if ((st = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "BeginCapture"))) break;
             run(P, s);
             if ((st = cuda_check(cudaStreamEndCapture(s, &graph), "EndCapture"))) break;
             if ((st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "GraphInstantiate"))) break;
-            recon_graph_store(key, exec);          // the cache owns it from here
-            cached = exec;
-            exec = nullptr;
+            if (recon_graph_store(key, exec)) {    // the cache owns it from here
+                cached = exec;
+                exec = nullptr;
+            }
         }
-        cudaGraphExec_t run_exec = cached;
+        cudaGraphExec_t run_exec = cached != nullptr ? cached : exec;
         int most = 0;
         for (int k : max_iters) most = std::max(most, k);
         // iteration max_iters evaluates the final field and sets the done flag
@@ -1332,12 +1361,11 @@ dmcr_status reconstruct_insts(std::vector<Inst>& in, char* tab, size_t tab_cap, 
         if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
         for (int i : rid) reports[i].rounded_rel_err = hs[i].err ? NAN : hs[i].loss[5];
     } while (0);
+    if (s) cudaStreamSynchronize(s);     // no launch of either graph is pending past here
+    if (cached) recon_graph_release(cached);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    if (s) {
-        cudaStreamSynchronize(s);
-        cudaStreamDestroy(s);
-    }
+    if (s) cudaStreamDestroy(s);
     if (ev) cudaEventDestroy(ev);
     return st;
 }
@@ -1408,6 +1436,7 @@ void key_adam_opts(KeyBuf& k, const dmcr_recon_opts& o) {
 struct StepGraph {
     std::string key;
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;     // recorded after every replay: eviction waits for it
     std::vector<Scalars*> sc;       // per instance
     float beta1 = 0.9f, beta2 = 0.999f;
     uint64_t used = 0;
@@ -1437,27 +1466,25 @@ bool graphs_usable(cudaStream_t s) {
     return cs == cudaStreamCaptureStatusNone;
 }
 
-// Launch the cached graph of `key` for Adam steps steps[i] + 1; false if there is none.
+// Launch the cached graph of `key` for Adam steps steps[i] + 1; false if there is none.  The
+// launches are enqueued under the cache's lock (no other thread can evict the graph
+// meanwhile), followed by an event that an eviction waits for.
 bool replay_step_graph(const std::string& key, const int64_t* steps, cudaStream_t s, dmcr_status* st) {
-    cudaGraphExec_t exec = nullptr;
-    std::vector<InitSeg> init;
-    {
-        std::lock_guard<std::mutex> lk(g_graph_mu);
-        for (StepGraph& g : graph_cache())
-            if (g.key == key) {
-                exec = g.exec;
-                g.used = ++g_graph_clock;
-                for (size_t i = 0; i < g.sc.size(); ++i)
-                    init.push_back({g.sc[i], steps[i], pow((double)g.beta1, (double)steps[i]),
-                                    pow((double)g.beta2, (double)steps[i])});
-                break;
-            }
-    }
-    if (exec == nullptr) return false;
-    launch_scalars_set(init.data(), (int)init.size(), s);
-    *st = cuda_check(cudaGetLastError(), "scalars set");
-    if (*st == DMCR_OK) *st = cuda_check(cudaGraphLaunch(exec, s), "cudaGraphLaunch (cached iteration)");
-    return true;
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (StepGraph& g : graph_cache())
+        if (g.key == key) {
+            g.used = ++g_graph_clock;
+            std::vector<InitSeg> init;
+            for (size_t i = 0; i < g.sc.size(); ++i)
+                init.push_back({g.sc[i], steps[i], pow((double)g.beta1, (double)steps[i]),
+                                pow((double)g.beta2, (double)steps[i])});
+            launch_scalars_set(init.data(), (int)init.size(), s);
+            *st = cuda_check(cudaGetLastError(), "scalars set");
+            if (*st == DMCR_OK) *st = cuda_check(cudaGraphLaunch(g.exec, s), "cudaGraphLaunch (cached iteration)");
+            if (*st == DMCR_OK) *st = cuda_check(cudaEventRecord(g.done, s), "cudaEventRecord (cached iteration)");
+            return true;
+        }
+    return false;
 }
 
 // Capture the prepared iteration (tables + kernels, no scalar initialisation) into a graph
@@ -1474,6 +1501,8 @@ bool capture_step_graph(const std::string& key, const Prepared& P, const std::ve
         ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && graph != nullptr;
     }
     if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    cudaEvent_t done = nullptr;
+    if (ok) ok = cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess;
     if (graph) cudaGraphDestroy(graph);
     if (cs) cudaStreamDestroy(cs);
     cudaGetLastError();
@@ -1484,6 +1513,7 @@ bool capture_step_graph(const std::string& key, const Prepared& P, const std::ve
     StepGraph g;
     g.key = key;
     g.exec = exec;
+    g.done = done;
     for (const Inst& x : in) g.sc.push_back(x.sc);
     g.beta1 = in[0].beta1;
     g.beta2 = in[0].beta2;
@@ -1492,7 +1522,10 @@ bool capture_step_graph(const std::string& key, const Prepared& P, const std::ve
     g.used = ++g_graph_clock;
     if (c.size() >= GRAPH_CACHE) {
         auto lru = std::min_element(c.begin(), c.end(), [](const StepGraph& a, const StepGraph& b) { return a.used < b.used; });
+        // its last replay may still be queued: wait for it before the graph is destroyed
+        cudaEventSynchronize(lru->done);
         cudaGraphExecDestroy(lru->exec);
+        cudaEventDestroy(lru->done);
         *lru = g;
     } else {
         c.push_back(g);

@@ -120,17 +120,45 @@ __global__ void stats_kernel(const PenSeg* __restrict__ segs) {
         comp = (t - sum) - y;
         sum = t;
     };
-    for (int64_t k = i0; k < sg.K; k += stride) {
+    // the terms of this thread in order; their loads issued four at a time (the same sums)
+    int64_t k = i0;
+    for (; k + 3 * stride < sg.K; k += 4 * stride) {
+        float tv[4], dv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            tv[u] = sg.target[k + u * stride];
+            dv[u] = sg.desc[k + u * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float r = dv[u] - tv[u];
+            kahan(r2, r2c, r * r);
+            kahan(t2, t2c, tv[u] * tv[u]);
+        }
+    }
+    for (; k < sg.K; k += stride) {
         const float t = sg.target[k];
         const float r = sg.desc[k] - t;
         kahan(r2, r2c, r * r);
         kahan(t2, t2c, t * t);
     }
-    if (sg.field != nullptr)
-        for (int64_t i = i0; i < sg.N; i += stride) {
+    if (sg.field != nullptr) {
+        int64_t i = i0;
+        for (; i + 3 * stride < sg.N; i += 4 * stride) {
+            float fv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) fv[u] = sg.field[i + u * stride];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float e = box_excess(fv[u]);
+                kahan(e2, e2c, e * e);
+            }
+        }
+        for (; i < sg.N; i += stride) {
             const float e = box_excess(sg.field[i]);
             kahan(e2, e2c, e * e);
         }
+    }
     // Kahan's (sum, comp) stands for sum - comp
     const DF R2 = block_sum_df(df_two_sum(r2, -r2c), sh);
     const DF T2 = block_sum_df(df_two_sum(t2, -t2c), sh);
@@ -263,16 +291,24 @@ void launch_loss(const LossSeg* segs, int nseg, cudaStream_t s) {
 // --------------------------------------------------------------------- gradient + Adam
 
 // g(y) = sum_l 2^{-d(l-1)} sum_chunks part_l[chunk][ancestor_l(y)]  (+ penalty gradient),
-// then either written out, or used for one Adam step (Keras form) on the field.
+// then either written out, or used for one Adam step (Keras form) on the field.  FIN_SUB
+// consecutive threads share a position: thread q sums the chunks c = q (mod FIN_SUB) in
+// order, and the FIN_SUB partial sums are combined by a fixed butterfly (every thread of the
+// group ends with the same bits: floating-point addition is commutative); thread 0 of the
+// group writes.
 __global__ void final_kernel(const FinalSeg* __restrict__ segs, int nseg) {
     const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
     const FinalSeg& sg = segs[si];
     if (sg.done != nullptr && *sg.done) return;
     const FinalArgs& a = sg.a;
     const int64_t N1 = a.n1[0] * a.n1[1] * a.n1[2];
-    const int64_t i = ((int64_t)blockIdx.x - sg.blockStart) * ELEM_TH + threadIdx.x;
-    if (i >= N1) return;
-    const int64_t x = i % a.n1[2], y = (i / a.n1[2]) % a.n1[1], z = i / (a.n1[1] * a.n1[2]);
+    const int q = threadIdx.x % FIN_SUB;
+    const int64_t i = ((int64_t)blockIdx.x - sg.blockStart) * FIN_POS + threadIdx.x / FIN_SUB;
+    // a block never straddles positions of two segments, but its last group may lie past N1:
+    // it computes on position 0 (every lane takes part in the shuffles) and writes nothing
+    const bool valid = i < N1;
+    const int64_t ii = valid ? i : 0;
+    const int64_t x = ii % a.n1[2], y = (ii / a.n1[2]) % a.n1[1], z = ii / (a.n1[1] * a.n1[2]);
     float g = 0.f;
     float scale = 1.f;
     const float step = a.ndim == 2 ? 0.25f : 0.125f;
@@ -280,22 +316,25 @@ __global__ void final_kernel(const FinalSeg* __restrict__ segs, int nseg) {
         const int64_t lz = a.ndim == 2 ? 0 : (z >> l);
         const int64_t li = (lz * a.nl[l][1] + (y >> l)) * a.nl[l][2] + (x >> l);
         float s = 0.f;
-        const float* p = a.parts[l] + li;
-        // the chunks in order, their loads issued eight at a time
-        const int nc = a.nChunks[l];
         const int64_t stride = a.Nl[l];
-        int c = 0;
-        for (; c + 8 <= nc; c += 8) {
-            float v[8];
+        const float* p = a.parts[l] + li + (int64_t)q * stride;
+        // this thread's chunks q, q + FIN_SUB, ... in order, their loads issued four at a time
+        const int nc = a.nChunks[l];
+        int c = q;
+        for (; c + 3 * FIN_SUB < nc; c += 4 * FIN_SUB, p += 4 * FIN_SUB * stride) {
+            float v[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = p[(int64_t)(c + u) * stride];
+            for (int u = 0; u < 4; ++u) v[u] = p[(int64_t)u * FIN_SUB * stride];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) s += v[u];
+            for (int u = 0; u < 4; ++u) s += v[u];
         }
-        for (; c < nc; ++c) s += p[(int64_t)c * stride];
+        for (; c < nc; c += FIN_SUB, p += FIN_SUB * stride) s += *p;
+#pragma unroll
+        for (int o = 1; o < FIN_SUB; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         g = fmaf(scale, s, g);
         scale *= step;
     }
+    if (!valid || q != 0) return;
     if (a.sc != nullptr && a.field != nullptr) {
         const float M = a.field[i];
         const float ex = box_excess(M);

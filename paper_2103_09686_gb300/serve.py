@@ -103,8 +103,8 @@ class Server:
             raise ValueError("class_slots needs one entry per class cap")
         self.classes = [_Class(c, n if n is not None else self.max_slots)
                         for c, n in sorted(zip(class_caps, slots), key=lambda cs: cs[0])]
-        if priorities not in ("cheap_first", "equal"):
-            raise ValueError("priorities: 'cheap_first' or 'equal'")
+        if priorities not in ("cheap_first", "equal", "heavy_first"):
+            raise ValueError("priorities: 'cheap_first', 'equal' or 'heavy_first'")
         self.priorities = priorities
         self.done: list[Job] = []
         self.in_use = 0
@@ -225,10 +225,17 @@ class Server:
         self._stop = False
         # "cheap_first": cheaper classes get higher stream priority, so their short kernels are
         # scheduled ahead of the long-running blocks of expensive classes as SMs free up;
-        # "equal": every class stream has the default priority
+        # "heavy_first": the reverse -- the longest jobs run at nearly full speed and the cheap
+        # classes fill the SMs they leave; "equal": every class stream has the default priority
         lo, hi = torch.cuda.Stream.priority_range()      # least, greatest (numerically lower = higher)
+        last = len(self.classes) - 1
         for i, c in enumerate(self.classes):
-            prio = min(lo, hi + i) if self.priorities == "cheap_first" else 0
+            if self.priorities == "cheap_first":
+                prio = min(lo, hi + i)
+            elif self.priorities == "heavy_first":
+                prio = min(lo, hi + (last - i))
+            else:
+                prio = 0
             c.stream = torch.cuda.Stream(device=self.dev, priority=prio)
             t = threading.Thread(target=self._worker, args=(c,), daemon=True)
             t.start()

@@ -77,3 +77,48 @@ def test_cached_graph_batched_steps_equal_direct_steps(cuda_lib):
 
     for x, y in zip(run(False), run(True)):
         assert torch.equal(x, y)
+
+
+def test_graph_caches_evict_and_recapture(cuda_lib):
+    """More argument sets than the caches hold (16 step graphs, 32 reconstruction graphs):
+    the least recently used graphs are evicted (after their last replay has run) and a later
+    call with evicted arguments captures again; every result equals the direct launches."""
+    dm = cuda_lib
+    p = dm.Params(shape=(32, 32), window=(4, 4))
+    D = dm.descriptor(torch.tensor((np.random.default_rng(2).random((32, 32)) < 0.4).astype(np.float32),
+                                   device="cuda"), p)
+
+    def fresh(k):
+        f = torch.tensor(synthetic.uniform_field((32, 32), 100 + k), dtype=torch.float32, device="cuda")
+        return f, torch.zeros_like(f), torch.zeros_like(f)
+
+    def steps(k, direct, n=3):
+        f, m, v = fresh(k)
+        dm.dmcr_profile_enable(direct)
+        try:
+            st = 0
+            for _ in range(n):
+                st = dm.dmcr_adam_step(p, dm.ReconOpts(lr=1e-2), D, f, m, v, st, None, wss[k])
+        finally:
+            dm.dmcr_profile_enable(False)
+            dm.dmcr_profile_reset()
+        return f
+
+    wss = [dm.workspace(p) for _ in range(20)]       # distinct workspaces: distinct argument sets
+    graph = [steps(k, False) for k in range(20)] + [steps(0, False)]      # set 0 evicted by now
+    direct = [steps(k, True) for k in range(20)] + [steps(0, True)]
+    for a, b in zip(graph, direct):
+        assert torch.equal(a, b)
+
+    rws = [dm.workspace(p) for _ in range(40)]     # 40 table addresses: 40 distinct launch sequences
+
+    def recon(k):
+        f, m, v = fresh(k)
+        rep, _ = dm.dmcr_reconstruct(p, dm.ReconOpts(max_iters=3 + k % 4, lr=1e-2, check_every=1), D, f, m, v,
+                                     ws=rws[k])
+        return f, rep["iterations"]
+
+    first = [recon(k) for k in range(40)]          # more than the 32 cached: evictions
+    again = [recon(k) for k in (0, 1, 39)]
+    for (fa, ia), (fb, ib) in zip([first[0], first[1], first[39]], again):
+        assert ia == ib and torch.equal(fa, fb)
