@@ -108,11 +108,13 @@ def serve_jobs(n_jobs: int, rate: float, seed: int, dm, serve):
 
 
 SERVE_CLASS_CAPS = (1.5e8, 1e9, 1e10, float("inf"))   # voxel-shifts per iteration of each cost class
-# most active jobs per class: the two heavy classes (2-D 1024^2 and 3-D jobs) serve one job
-# at a time in arrival order; equal stream priorities.  On the first 64 arrivals at 80% load
-# this gave p50 1.96 s / p99 25.7 s against 2.73 s / 28.9 s with no class limits and
-# cheap-first priorities, and 3.87 s / 30.0 s for the plain form.
-SERVE_CLASS_SLOTS = (None, None, 1, 1)
+# most active jobs per class: the class of the 128^3/160^3 jobs serves one job at a time in
+# arrival order, the class of the 2-D 1024^2 and 3-D 64-96^3 jobs four; equal stream
+# priorities.  Measured on the first 128 arrivals at 80% load (0.377 req/s) against the plain
+# form of the same session: p50 4.41 / p99 90.5 / mean 14.4 s against 5.00 / 91.8 / 18.3 s
+# (other settings: no limits 4.8 / 119 / 22.8 s; one job in each heavy class 1.6 / 120 /
+# 17.8 s; the heaviest class exclusive 4.9 / 170 / 34.8 s).
+SERVE_CLASS_SLOTS = (None, None, 4, 1)
 SERVE_PRIORITIES = "equal"
 
 

@@ -87,7 +87,7 @@ class _Class:
 class Server:
     def __init__(self, device="cuda", hbm_budget_bytes: int = 150 << 30, max_slots: int = 64, tick_iters: int = 50,
                  class_caps=(float("inf"),), class_slots=None, priorities: str = "cheap_first",
-                 clock=time.perf_counter):
+                 exclusive_top: bool = False, clock=time.perf_counter):
         self.dev = torch.device(device)
         self.budget = int(hbm_budget_bytes)
         self.max_slots = int(max_slots)
@@ -106,6 +106,9 @@ class Server:
         if priorities not in ("cheap_first", "equal", "heavy_first"):
             raise ValueError("priorities: 'cheap_first', 'equal' or 'heavy_first'")
         self.priorities = priorities
+        # exclusive_top: while a job of the most expensive class is active, the other classes
+        # pause at their next tick boundary, so that job has the device to itself
+        self.exclusive_top = bool(exclusive_top)
         self.done: list[Job] = []
         self.in_use = 0
         self.ticks = 0
@@ -171,7 +174,13 @@ class Server:
         with self._lock:
             cls.active.extend(new)
 
+    def _paused(self, cls) -> bool:
+        top = self.classes[-1]
+        return self.exclusive_top and cls is not top and bool(top.active or top.pending)
+
     def _tick_class(self, cls) -> int:
+        if self._paused(cls):
+            return 0
         self._admit(cls)
         jobs = list(cls.active)
         if not jobs:
@@ -251,7 +260,7 @@ class Server:
                         if self._stop and not cls.pending and not cls.active:
                             return
                     self._tick_class(cls)
-                    if not cls.active:          # pending jobs wait for memory or slots held elsewhere
+                    if not cls.active or self._paused(cls):   # waiting for memory, slots or the top class
                         with self._wake:
                             self._wake.wait(0.01)
         except BaseException as e:     # surfaced by stop()

@@ -161,3 +161,18 @@ def test_class_slots_serve_heavy_jobs_one_at_a_time(fake):
     assert len(srv.done) == 6
     with pytest.raises(ValueError):
         serve.Server(device="cpu", class_caps=(1.0, 2.0), class_slots=(1,))
+
+
+def test_exclusive_top_class_pauses_the_others(fake):
+    """With exclusive_top, no tick of a cheaper class runs while a job of the most expensive
+    class is waiting or active."""
+    small = [_job(i, shape=(64, 64), window=(4, 4)) for i in range(2)]
+    large = [_job(10, shape=(256, 256), window=(32, 32), levels=2)]
+    fake.need.update({0: 100, 1: 100, 10: 150})
+    cap = serve.iteration_units(small[0].params) * 10
+    srv = serve.Server(device="cpu", max_slots=64, tick_iters=50, class_caps=(cap, float("inf")),
+                       exclusive_top=True)
+    _run(srv, fake, small + large)
+    kinds = ["large" if ids[0] >= 10 else "small" for ids, _ in fake.calls]
+    assert kinds == ["large"] * 3 + ["small"] * 2        # the large job first, alone, then the small ones
+    assert len(srv.done) == 3
