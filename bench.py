@@ -51,7 +51,8 @@ ALGORITHMIC_FP32_OPS_PER_PAIR = 5.0
 MIX_KEY = {"corr_fwd": "forward_pairs", "corr_adj": "adjoint_pairs"}
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (None
 # whenever a kernel changed since its last capture).
-NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): None, ("grf512", "corr_fwd"): None,
+NCU_TRAFFIC_BYTES = {# profiles/corr_kernels_grf512_w64_L3.md
+                     ("grf512", "corr_adj"): 2714880 + 12544, ("grf512", "corr_fwd"): 1451520 + 768,
                      # profiles/launches_mp3_512_w64_L3.md
                      ("mp3_512", "corr_adj"): 15905024 + 50688, ("mp3_512", "corr_fwd"): 4216832 + 45588480}
 

@@ -291,50 +291,52 @@ void launch_loss(const LossSeg* segs, int nseg, cudaStream_t s) {
 // --------------------------------------------------------------------- gradient + Adam
 
 // g(y) = sum_l 2^{-d(l-1)} sum_chunks part_l[chunk][ancestor_l(y)]  (+ penalty gradient),
-// then either written out, or used for one Adam step (Keras form) on the field.  FIN_SUB
-// consecutive threads share a position: thread q sums the chunks c = q (mod FIN_SUB) in
-// order, and the FIN_SUB partial sums are combined by a fixed butterfly (every thread of the
-// group ends with the same bits: floating-point addition is commutative); thread 0 of the
-// group writes.
-__global__ void final_kernel(const FinalSeg* __restrict__ segs, int nseg) {
+// then either written out, or used for one Adam step (Keras form) on the field.  A block
+// covers FIN_POS positions with FIN_SUB threads each: thread (q, p) -- q = threadIdx.x /
+// FIN_POS, so a warp reads FIN_POS consecutive positions of the same chunk (coalesced) --
+// sums the chunks c = q (mod FIN_SUB) of every level in order into its own partial gradient;
+// the FIN_SUB partials are added in a fixed order through shared memory and thread (0, p)
+// writes.
+__global__ void __launch_bounds__(ELEM_TH) final_kernel(const FinalSeg* __restrict__ segs, int nseg) {
     const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
     const FinalSeg& sg = segs[si];
     if (sg.done != nullptr && *sg.done) return;
+    __shared__ float part[FIN_SUB][FIN_POS];
     const FinalArgs& a = sg.a;
     const int64_t N1 = a.n1[0] * a.n1[1] * a.n1[2];
-    const int q = threadIdx.x % FIN_SUB;
-    const int64_t i = ((int64_t)blockIdx.x - sg.blockStart) * FIN_POS + threadIdx.x / FIN_SUB;
-    // a block never straddles positions of two segments, but its last group may lie past N1:
-    // it computes on position 0 (every lane takes part in the shuffles) and writes nothing
+    const int q = threadIdx.x / FIN_POS, pl = threadIdx.x % FIN_POS;
+    const int64_t i = ((int64_t)blockIdx.x - sg.blockStart) * FIN_POS + pl;
     const bool valid = i < N1;
-    const int64_t ii = valid ? i : 0;
-    const int64_t x = ii % a.n1[2], y = (ii / a.n1[2]) % a.n1[1], z = ii / (a.n1[1] * a.n1[2]);
     float g = 0.f;
-    float scale = 1.f;
-    const float step = a.ndim == 2 ? 0.25f : 0.125f;
-    for (int l = 0; l < a.levels; ++l) {
-        const int64_t lz = a.ndim == 2 ? 0 : (z >> l);
-        const int64_t li = (lz * a.nl[l][1] + (y >> l)) * a.nl[l][2] + (x >> l);
-        float s = 0.f;
-        const int64_t stride = a.Nl[l];
-        const float* p = a.parts[l] + li + (int64_t)q * stride;
-        // this thread's chunks q, q + FIN_SUB, ... in order, their loads issued four at a time
-        const int nc = a.nChunks[l];
-        int c = q;
-        for (; c + 3 * FIN_SUB < nc; c += 4 * FIN_SUB, p += 4 * FIN_SUB * stride) {
-            float v[4];
+    if (valid) {
+        const int64_t x = i % a.n1[2], y = (i / a.n1[2]) % a.n1[1], z = i / (a.n1[1] * a.n1[2]);
+        float scale = 1.f;
+        const float step = a.ndim == 2 ? 0.25f : 0.125f;
+        for (int l = 0; l < a.levels; ++l) {
+            const int64_t lz = a.ndim == 2 ? 0 : (z >> l);
+            const int64_t li = (lz * a.nl[l][1] + (y >> l)) * a.nl[l][2] + (x >> l);
+            float s = 0.f;
+            const int64_t stride = a.Nl[l];
+            const float* p = a.parts[l] + li + (int64_t)q * stride;
+            // this thread's chunks q, q + FIN_SUB, ... in order, their loads issued four at a time
+            const int nc = a.nChunks[l];
+            int c = q;
+            for (; c + 3 * FIN_SUB < nc; c += 4 * FIN_SUB, p += 4 * FIN_SUB * stride) {
+                float v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = p[(int64_t)u * FIN_SUB * stride];
+                for (int u = 0; u < 4; ++u) v[u] = p[(int64_t)u * FIN_SUB * stride];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s += v[u];
+                for (int u = 0; u < 4; ++u) s += v[u];
+            }
+            for (; c < nc; c += FIN_SUB, p += FIN_SUB * stride) s += *p;
+            g = fmaf(scale, s, g);
+            scale *= step;
         }
-        for (; c < nc; c += FIN_SUB, p += FIN_SUB * stride) s += *p;
-#pragma unroll
-        for (int o = 1; o < FIN_SUB; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        g = fmaf(scale, s, g);
-        scale *= step;
     }
+    part[q][pl] = g;
+    __syncthreads();
     if (!valid || q != 0) return;
+    g = (part[0][pl] + part[1][pl]) + (part[2][pl] + part[3][pl]);
     if (a.sc != nullptr && a.field != nullptr) {
         const float M = a.field[i];
         const float ex = box_excess(M);

@@ -310,7 +310,8 @@ float gcoef_scale(const LevelGeom& g, const ThreshConst& tc, float weight);
 constexpr int RED_K = 32;      // shifts per fwd_reduce block
 constexpr int GCOEF_TH = 256;  // entries per gcoef block
 constexpr int ELEM_TH = 256;   // pixels per restrict block; threads per final block
-constexpr int FIN_SUB = 4;     // gradient assembly: threads per position (each sums every 4th chunk)
+constexpr int FIN_SUB = 4;     // gradient assembly: threads per position (each sums every 4th chunk; the
+                               // combine adds exactly four partials)
 constexpr int FIN_POS = ELEM_TH / FIN_SUB;   // positions per final block
 
 // Segment of linear block b: the last segment whose blockStart <= b.
