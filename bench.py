@@ -49,11 +49,10 @@ RCP_PER_PAIR = {"corr_fwd": 0.5, "corr_adj": 4.0 / 8.0 * 0.5 + 4.0 / 8.0}
 ALGORITHMIC_FP32_OPS_PER_PAIR = 5.0
 # the probe's measured pair rate of each kernel's own instruction mix held in registers
 MIX_KEY = {"corr_fwd": "forward_pairs", "corr_adj": "adjoint_pairs"}
-# DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (None
-# whenever a kernel changed since its last capture).
-NCU_TRAFFIC_BYTES = {# profiles/corr_kernels_grf512_w64_L3.md
-                     ("grf512", "corr_adj"): 2714880 + 12544, ("grf512", "corr_fwd"): 1451520 + 768,
-                     # profiles/launches_mp3_512_w64_L3.md
+# DRAM bytes (read + write) per launch of each correlation kernel, from one ncu capture of the
+# bench's own command per workload (dram__bytes_read.sum + dram__bytes_write.sum); None
+# whenever a kernel changed since its last capture.
+NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2714880 + 12544, ("grf512", "corr_fwd"): 1451520 + 768,
                      ("mp3_512", "corr_adj"): 15905024 + 50688, ("mp3_512", "corr_fwd"): 4216832 + 45588480}
 
 WORKLOADS = {

@@ -229,7 +229,10 @@ dmcr_status dmcr_init_uniform(float* field, int64_t count, uint64_t seed, void* 
  *   history: max_iters * 3 floats (device: E, L, rel_err per iteration) or NULL.
  *   SYNCHRONOUS: returns after the run, with `report` (host) filled in; report.loss is the
  *   loss of the returned field.  The graph runs on a private stream created with the
- *   priority of `stream` (so a high-priority caller stream keeps its priority).
+ *   priority of `stream` (so a high-priority caller stream keeps its priority).  The
+ *   library keeps the 32 most recently captured iteration graphs (of this call and the
+ *   batched one), keyed by their whole launch sequence, so a later call with the same
+ *   arguments and options captures nothing.
  */
 dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* opts,
                              const float* target_desc, float* field_inout, dmcr_adam_state* state,
@@ -243,6 +246,12 @@ dmcr_status dmcr_reconstruct(const dmcr_params* p, const dmcr_recon_opts* opts,
  *   state->step + 1).  Uses opts->lr, beta1, beta2, eps and opts->loss; ignores the
  *   stopping fields.  Asynchronous on `stream`; state->step is incremented on return.
  *   A non-finite loss leaves the field unchanged (check loss_out).
+ *   The first call with a given set of arguments (params, the options above, every pointer,
+ *   ws_bytes, the current device) captures the iteration into a CUDA graph that the library
+ *   keeps (the 16 most recently used sets); a later call with the same arguments launches
+ *   one small kernel with this call's step count and replays the graph, with the same
+ *   results bit for bit.  While `stream` is being captured by the caller, or while the
+ *   dmcr_profile timers are on, the kernels are launched directly instead.
  */
 dmcr_status dmcr_adam_step(const dmcr_params* p, const dmcr_recon_opts* opts, const float* target_desc,
                            float* field, dmcr_adam_state* state, float* loss_out, void* ws, size_t ws_bytes,
