@@ -553,7 +553,7 @@ struct Prepared {
     };
     std::vector<R> restricts;
     R fwd{0, 0, 0}, red{0, 0, 0}, pen{0, 0, 0}, loss{0, 0, 0}, gco{0, 0, 0}, adj{0, 0, 0}, fin{0, 0, 0},
-        init{0, 0, 0}, tmap{0, 0, 0}, tsum{0, 0, 0};
+        fin_small{0, 0, 0}, init{0, 0, 0}, tmap{0, 0, 0}, tsum{0, 0, 0};
     size_t smem_fwd = 0, smem_adj = 0;
     struct FftJob {
         LevelGeom g;
@@ -783,8 +783,11 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         std::vector<Item> items;
         std::vector<GSeg> gv;
         std::vector<TildeSeg> tsv;
-        std::vector<FinalSeg> fv;
-        int64_t gb = 0, fb = 0;
+        // gradient assembly: a small field has few positions for many chunk partials and its
+        // segments go to the launch with FIN_SUB threads per position; the others to the one
+        // with one thread per position
+        std::vector<FinalSeg> fv, fvs;
+        int64_t gb = 0, fb = 0, fbs = 0;
         const bool vjp = !(flags & F_LOSS);
         for (const Inst& x : in) {
             const int nph = x.pl->phases;
@@ -887,9 +890,15 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
                 f.a.M = slice(fs.a.M);
                 f.a.m = slice(fs.a.m);
                 f.a.v = slice(fs.a.v);
-                f.blockStart = fb;
-                fb += ceil_div(N1, FIN_POS);
-                fv.push_back(f);
+                if (N1 < FIN_SUB_BELOW) {
+                    f.blockStart = fbs;
+                    fbs += ceil_div(N1, ELEM_TH / FIN_SUB);
+                    fvs.push_back(f);
+                } else {
+                    f.blockStart = fb;
+                    fb += ceil_div(N1, ELEM_TH);
+                    fv.push_back(f);
+                }
             }
         }
         std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.work > b.work; });
@@ -904,10 +913,12 @@ dmcr_status prepare(std::vector<Inst>& in, unsigned flags, char* tab, size_t cap
         P.tsum = {push(P.tb, tsv), (int)tsv.size(), (int64_t)tsv.size()};
         P.adj = {push(P.tb, av), (int)av.size(), ab};
         P.fin = {push(P.tb, fv), (int)fv.size(), fb};
+        P.fin_small = {push(P.tb, fvs), (int)fvs.size(), fbs};
     }
     if (P.tb.h.size() > cap) return fail(DMCR_ENOMEM, "segment tables (%zu bytes) exceed their region", P.tb.h.size());
     // every fused launch indexes its blocks with a 1-D grid
-    int64_t most = std::max({P.fwd.blocks, P.red.blocks, P.gco.blocks, P.adj.blocks, P.fin.blocks, P.tmap.blocks});
+    int64_t most = std::max({P.fwd.blocks, P.red.blocks, P.gco.blocks, P.adj.blocks, P.fin.blocks, P.fin_small.blocks,
+                             P.tmap.blocks});
     for (const Prepared::R& r : P.restricts) most = std::max(most, r.blocks);
     if (most > (int64_t)INT32_MAX)
         return fail(DMCR_ENOTSUP, "a fused launch would need %lld thread blocks (more than 2^31 - 1): split the batch "
@@ -1056,7 +1067,8 @@ void run(const Prepared& P, cudaStream_t s) {
             for (const S3Job& j : P.s3b) launch_s3_backward(j, P.tc, j.err, s);
         }
         ProfScope ps((P.flags & F_ADAM) ? "grad_adam" : "grad_assemble", -1, s);
-        launch_final(P.at<FinalSeg>(P.fin.off), P.fin.nseg, P.fin.blocks, s);
+        launch_final(P.at<FinalSeg>(P.fin.off), P.fin.nseg, P.fin.blocks, 1, s);
+        launch_final(P.at<FinalSeg>(P.fin_small.off), P.fin_small.nseg, P.fin_small.blocks, FIN_SUB, s);
     }
 }
 
@@ -1189,7 +1201,8 @@ std::string prepared_key(const Prepared& P) {
     add(&P.flags, sizeof P.flags);
     add(&P.tc, sizeof P.tc);
     for (const Prepared::R& r : P.restricts) add(&r, sizeof r);
-    for (const Prepared::R* r : {&P.fwd, &P.red, &P.pen, &P.loss, &P.gco, &P.adj, &P.fin, &P.init, &P.tmap, &P.tsum})
+    for (const Prepared::R* r : {&P.fwd, &P.red, &P.pen, &P.loss, &P.gco, &P.adj, &P.fin, &P.fin_small, &P.init,
+                                   &P.tmap, &P.tsum})
         add(r, sizeof *r);
     add(&P.smem_fwd, sizeof P.smem_fwd);
     add(&P.smem_adj, sizeof P.smem_adj);

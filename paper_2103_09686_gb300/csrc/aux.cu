@@ -291,52 +291,69 @@ void launch_loss(const LossSeg* segs, int nseg, cudaStream_t s) {
 // --------------------------------------------------------------------- gradient + Adam
 
 // g(y) = sum_l 2^{-d(l-1)} sum_chunks part_l[chunk][ancestor_l(y)]  (+ penalty gradient),
-// then either written out, or used for one Adam step (Keras form) on the field.  A block
-// covers FIN_POS positions with FIN_SUB threads each: thread (q, p) -- q = threadIdx.x /
-// FIN_POS, so a warp reads FIN_POS consecutive positions of the same chunk (coalesced) --
-// sums the chunks c = q (mod FIN_SUB) of every level in order into its own partial gradient;
-// the FIN_SUB partials are added in a fixed order through shared memory and thread (0, p)
-// writes.
+// then either written out, or used for one Adam step (Keras form) on the field.  Position i's
+// chunk sums for the chunks c = q (mod SUB) of every level, each level's chunks in order,
+// their loads issued eight at a time.
+template <int SUB>
+__device__ __forceinline__ float chunk_sums(const FinalArgs& a, int64_t i, int q) {
+    const int64_t x = i % a.n1[2], y = (i / a.n1[2]) % a.n1[1], z = i / (a.n1[1] * a.n1[2]);
+    float g = 0.f, scale = 1.f;
+    const float step = a.ndim == 2 ? 0.25f : 0.125f;
+    for (int l = 0; l < a.levels; ++l) {
+        const int64_t lz = a.ndim == 2 ? 0 : (z >> l);
+        const int64_t li = (lz * a.nl[l][1] + (y >> l)) * a.nl[l][2] + (x >> l);
+        const int64_t jump = SUB * a.Nl[l];
+        const float* p = a.parts[l] + li + q * a.Nl[l];
+        const int nc = a.nChunks[l];
+        float s = 0.f;
+        int c = q;
+        for (; c + 7 * SUB < nc; c += 8 * SUB) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u, p += jump) v[u] = *p;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+        for (; c < nc; c += SUB, p += jump) s += *p;
+        g = fmaf(scale, s, g);
+        scale *= step;
+    }
+    return g;
+}
+
+// A block covers ELEM_TH / SUB positions with SUB threads each.  SUB = 1 (a large field):
+// one thread per position, a warp reads 32 consecutive positions of a chunk.  SUB = FIN_SUB
+// (a small field: few positions for many chunk partials): thread (q, p) -- q = threadIdx.x /
+// positions, so a warp still reads consecutive positions of one chunk -- sums the chunks
+// c = q (mod FIN_SUB) and the FIN_SUB partials are added in a fixed order through shared
+// memory.  Two instantiations, so that SUB = 1 keeps the 32 registers with which 8 blocks
+// stay resident per SM (a 512^2 field is one wave).
+template <int SUB>
 __global__ void __launch_bounds__(ELEM_TH) final_kernel(const FinalSeg* __restrict__ segs, int nseg) {
     const int si = find_segment(segs, nseg, (int64_t)blockIdx.x);
     const FinalSeg& sg = segs[si];
     if (sg.done != nullptr && *sg.done) return;
-    __shared__ float part[FIN_SUB][FIN_POS];
     const FinalArgs& a = sg.a;
     const int64_t N1 = a.n1[0] * a.n1[1] * a.n1[2];
-    const int q = threadIdx.x / FIN_POS, pl = threadIdx.x % FIN_POS;
-    const int64_t i = ((int64_t)blockIdx.x - sg.blockStart) * FIN_POS + pl;
-    const bool valid = i < N1;
-    float g = 0.f;
-    if (valid) {
-        const int64_t x = i % a.n1[2], y = (i / a.n1[2]) % a.n1[1], z = i / (a.n1[1] * a.n1[2]);
-        float scale = 1.f;
-        const float step = a.ndim == 2 ? 0.25f : 0.125f;
-        for (int l = 0; l < a.levels; ++l) {
-            const int64_t lz = a.ndim == 2 ? 0 : (z >> l);
-            const int64_t li = (lz * a.nl[l][1] + (y >> l)) * a.nl[l][2] + (x >> l);
-            float s = 0.f;
-            const int64_t stride = a.Nl[l];
-            const float* p = a.parts[l] + li + (int64_t)q * stride;
-            // this thread's chunks q, q + FIN_SUB, ... in order, their loads issued four at a time
-            const int nc = a.nChunks[l];
-            int c = q;
-            for (; c + 3 * FIN_SUB < nc; c += 4 * FIN_SUB, p += 4 * FIN_SUB * stride) {
-                float v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = p[(int64_t)u * FIN_SUB * stride];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) s += v[u];
-            }
-            for (; c < nc; c += FIN_SUB, p += FIN_SUB * stride) s += *p;
-            g = fmaf(scale, s, g);
-            scale *= step;
-        }
+    const int64_t b = (int64_t)blockIdx.x - sg.blockStart;
+    int64_t i;
+    float g;
+    if constexpr (SUB == 1) {
+        i = b * ELEM_TH + threadIdx.x;
+        if (i >= N1) return;
+        g = chunk_sums<1>(a, i, 0);
+    } else {
+        static_assert(SUB == 4, "the combine below adds four partials");
+        constexpr int NPOS = ELEM_TH / SUB;
+        __shared__ float part[SUB][NPOS];
+        const int q = threadIdx.x / NPOS, pl = threadIdx.x % NPOS;
+        i = b * NPOS + pl;
+        const bool valid = i < N1;
+        part[q][pl] = valid ? chunk_sums<SUB>(a, i, q) : 0.f;
+        __syncthreads();
+        if (q != 0 || !valid) return;
+        g = (part[0][pl] + part[1][pl]) + (part[2][pl] + part[3][pl]);
     }
-    part[q][pl] = g;
-    __syncthreads();
-    if (!valid || q != 0) return;
-    g = (part[0][pl] + part[1][pl]) + (part[2][pl] + part[3][pl]);
     if (a.sc != nullptr && a.field != nullptr) {
         const float M = a.field[i];
         const float ex = box_excess(M);
@@ -353,9 +370,12 @@ __global__ void __launch_bounds__(ELEM_TH) final_kernel(const FinalSeg* __restri
     }
 }
 
-void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, cudaStream_t s) {
+void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, int sub, cudaStream_t s) {
     if (blocks <= 0) return;
-    final_kernel<<<(unsigned)blocks, ELEM_TH, 0, s>>>(segs, nseg);
+    if (sub == 1)
+        final_kernel<1><<<(unsigned)blocks, ELEM_TH, 0, s>>>(segs, nseg);
+    else
+        final_kernel<FIN_SUB><<<(unsigned)blocks, ELEM_TH, 0, s>>>(segs, nseg);
 }
 
 __device__ __forceinline__ void scalars_init_one(const InitSeg& g) {

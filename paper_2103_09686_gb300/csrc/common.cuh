@@ -279,7 +279,8 @@ void launch_tilde_map(const TildeSeg* segs, int nseg, int64_t blocks, cudaStream
 void launch_tilde_sum(const TildeSeg* segs, int nseg, cudaStream_t s);
 void launch_corr_adj(const AdjSeg* segs, int nseg, int64_t blocks, size_t smem, const ThreshConst& tc,
                      cudaStream_t s);
-void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, cudaStream_t s);
+// sub = threads per position: 1, or FIN_SUB for segments of fields below FIN_SUB_BELOW positions
+void launch_final(const FinalSeg* segs, int nseg, int64_t blocks, int sub, cudaStream_t s);
 void launch_init_uniform(float* field, int64_t count, uint64_t seed, cudaStream_t s);
 void launch_round_field(const float* src, float* dst, int64_t count, cudaStream_t s);
 void launch_scalars_init(const InitSeg* segs, int nseg, cudaStream_t s);
@@ -310,9 +311,9 @@ float gcoef_scale(const LevelGeom& g, const ThreshConst& tc, float weight);
 constexpr int RED_K = 32;      // shifts per fwd_reduce block
 constexpr int GCOEF_TH = 256;  // entries per gcoef block
 constexpr int ELEM_TH = 256;   // pixels per restrict block; threads per final block
-constexpr int FIN_SUB = 4;     // gradient assembly: threads per position (each sums every 4th chunk; the
-                               // combine adds exactly four partials)
-constexpr int FIN_POS = ELEM_TH / FIN_SUB;   // positions per final block
+constexpr int FIN_SUB = 4;     // gradient assembly of a small field: threads per position (each sums
+                               // every 4th chunk; the combine adds exactly four partials)
+constexpr int64_t FIN_SUB_BELOW = 1 << 16;   // fields of fewer positions use FIN_SUB threads each
 
 // Segment of linear block b: the last segment whose blockStart <= b.
 template <typename S>
