@@ -53,7 +53,7 @@ MIX_KEY = {"corr_fwd": "forward_pairs", "corr_adj": "adjoint_pairs"}
 # bench's own command per workload (dram__bytes_read.sum + dram__bytes_write.sum); None
 # whenever a kernel changed since its last capture.
 NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2714880 + 12544, ("grf512", "corr_fwd"): 1451520 + 768,
-                     ("mp3_512", "corr_adj"): 15905024 + 50688, ("mp3_512", "corr_fwd"): 4216832 + 45588480}
+                     ("mp3_512", "corr_adj"): 16121344 + 45945088, ("mp3_512", "corr_fwd"): 4216832 + 45588480}
 
 WORKLOADS = {
     "grf512": dict(shape=(512, 512), window=(64, 64), levels=3,

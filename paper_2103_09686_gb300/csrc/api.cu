@@ -264,9 +264,11 @@ void plan_level(LevelGeom& g, const int tune[4], int phases) {
     g.RY = (int)std::min<int64_t>(ceil_div(wy, ceil_div(perX, nZc)), cap);
     if (tune[1] > 0) g.RY = std::min(tune[1], cap);
     // several phase fields: every ordered pair is a segment of the same launch, so a chunk
-    // can cover up to phases^2 times as many ry rows (staged in rounds of at most `cap`
-    // rows): fewer chunks, and phases^2 times fewer adjoint partials to write and read back
-    if (phases > 1 && tune[1] == 0) g.RY = std::min<int64_t>((int64_t)g.RY * phases * phases, wy);
+    // covers `phases` times as many ry rows (staged in rounds of at most `cap` rows): fewer
+    // adjoint partials to write and read back.  phases^2 times as many kept the partials of
+    // three 512^2 fields in L2 but made blocks so long that the launch's tail idled: 3.4%
+    // slower adjoint; one times spilled the partials: 2x the gradient assembly's time
+    if (phases > 1 && tune[1] == 0) g.RY = std::min<int64_t>((int64_t)g.RY * phases, wy);
     g.RY = std::min(g.RY, wy);
     g.RYS = std::min(g.RY, cap);
     g.nYc = (int)ceil_div(wy, g.RY);
