@@ -52,7 +52,7 @@ MIX_KEY = {"corr_fwd": "forward_pairs", "corr_adj": "adjoint_pairs"}
 # DRAM bytes (read + write) per launch of each correlation kernel, from one ncu capture of the
 # bench's own command per workload (dram__bytes_read.sum + dram__bytes_write.sum); None
 # whenever a kernel changed since its last capture.
-NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2714880 + 12544, ("grf512", "corr_fwd"): 1451520 + 768,
+NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2780160 + 256, ("grf512", "corr_fwd"): 1457152 + 1024,
                      ("mp3_512", "corr_adj"): 16121344 + 45945088, ("mp3_512", "corr_fwd"): 4216832 + 45588480}
 
 WORKLOADS = {
