@@ -259,7 +259,8 @@ void plan_level(LevelGeom& g, const int tune[4], int phases, int level) {
     // a level of fewer than 8 tiles (a small field) may take up to 64 chunks.  A coarser level
     // of a multigrid problem may take up to 128: its blocks come last in the fused launch
     // (heaviest first), and shorter last blocks leave the SMs less idle time at its end
-    // (512^2, +-64, 3 levels: the 128^2 level in 86 chunks instead of 30, adjoint 1.1% faster)
+    // (512^2, +-64, 3 levels: the 256^2 and 128^2 levels in 38 and 86 chunks instead of 30
+    // and 30, adjoint 1.1% faster)
     const int64_t chunk_cap = tune[2] > 0 ? tune[2] : (g.adjTiles < 8 ? 64 : (level > 0 ? 128 : 32));
     const int64_t want = std::min<int64_t>(chunk_cap, std::max<int64_t>(1, ceil_div(rows_target, g.adjTiles)));
     const int64_t perX = ceil_div(want, (int64_t)g.nXc);
