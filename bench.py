@@ -53,7 +53,10 @@ MIX_KEY = {"corr_fwd": "forward_pairs", "corr_adj": "adjoint_pairs"}
 # bench's own command per workload (dram__bytes_read.sum + dram__bytes_write.sum); None
 # whenever a kernel changed since its last capture.
 NCU_TRAFFIC_BYTES = {("grf512", "corr_adj"): 2780160 + 256, ("grf512", "corr_fwd"): 1457152 + 1024,
-                     ("mp3_512", "corr_adj"): 16121344 + 45945088, ("mp3_512", "corr_fwd"): 4216832 + 45588480}
+                     ("mp3_512", "corr_adj"): 16121344 + 45945088, ("mp3_512", "corr_fwd"): 4216832 + 45588480,
+                     ("grf128_3d", "corr_adj"): 17604096 + 51608320, ("grf128_3d", "corr_fwd"): 39135744 + 242014464,
+                     ("grf64", "corr_adj"): 114688 + 0, ("grf64", "corr_fwd"): 93440 + 0,
+                     ("batch256", "corr_adj"): 135313408 + 1368981248, ("batch256", "corr_fwd"): 86752256 + 615229184}
 
 WORKLOADS = {
     "grf512": dict(shape=(512, 512), window=(64, 64), levels=3,
